@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 registration hot path.
+
+One step = one full Gauss-Newton-Krylov solve (Algorithm 1 of arXiv
+2008.12820) of the 256^3 synthetic blob workload: N_t = 4, beta = 1e-2,
+gamma = 1, inverse-A preconditioner, stop at 5e-2 relative gradient
+reduction, started from v = 0.  Every row of the hot path runs inside it:
+RK2 foot points, cubic interpolation, state / adjoint / incremental transport,
+spectral gradient / divergence / regularization / preconditioner, PCG with FP64
+dots, Armijo line search.  The inputs are resident in HBM before the timed
+region; the working set (~5 GB) is far larger than the 129 MB L2.
+
+value = voxels registered per second (N / solve time, Gvoxel/s), summed over
+ranks.  With torchrun (N > 1) every rank solves its own replica (no
+collective on the data path; "replicas only").
+
+Extra keys: Hessian-matvec throughput, the solve report, a roofline entry for
+the dominant kernel class (algorithmic bytes / CUDA-event time, live), an
+end-to-end number through the C ABI with host buffers, a CPU baseline of the
+FP64 oracle, the error against the oracle, clocks sampled during the timed
+region.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+method has; the paper's code is not available) on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Hessian matvec Gvoxel/s and GN solve time @256³; % of HBM roofline; "
+          "err vs FP64")
+UNIT = "Gvoxel/s"
+WORKLOAD = "blob256"
+WORKLOAD_DESC = ("256^3 synthetic brain-like blob images (12 ellipsoids, sigma 2 voxels), "
+                 "reference warped by a band-limited displacement (|k|<=6, max 4 voxels); "
+                 "nt=4, beta=1e-2, gamma=1, cubic SL, spectral ops, PC InvA, "
+                 "full GN-Krylov solve to 5e-2 from v=0")
+CPU_SAMPLE_N = 64        # oracle solves the same generator on a 64^3 grid
+ERR_CHECK_N = 128        # GPU vs oracle gradient / matvec on a 128^3 instance
+
+KCLASS = ["footpoint", "state", "adjoint", "incstate", "incadj", "bodyforce", "fft_r2c",
+          "fft_c2c", "fft_mul", "fft_c2r", "reduce", "vector", "interp"]
+# kernel function name regex of each class (for the ncu summaries)
+KNAMES = {"footpoint": "k_footpoints|k_adjoint_factor", "state": "k_state_step",
+          "adjoint": "k_adjoint_step", "incstate": "k_incstate_step",
+          "incadj": "k_adjoint_step", "bodyforce": "k_bodyforce", "fft_r2c": "k_r2c_x3",
+          "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1", "fft_c2r": "k_c2r_x3",
+          "reduce": "k_reduce2|k_finalize", "vector": "k_pcg|k_axpby|k_sub|k_inc",
+          "interp": "k_interp"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kclass, bytes_per_launch, n_vox):
+    """DRAM traffic per launch from the committed ncu summary of this kernel,
+    scaled by voxels; null if the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kclass)
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else None
+    if h != e.get("source_sha256_16"):
+        return None
+    return e["dram_bytes_per_voxel"] * n_vox * e.get("voxels_per_launch_factor", 1.0)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    __graft_entry__.build()
+    from paper_2008_12820_gb300 import claire, synth
+
+    w = synth.workload(args.workload)
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    N = int(np.prod(shape))
+    m0 = torch.from_numpy(w["m0"]).cuda()
+    m1 = torch.from_numpy(w["m1"]).cuda()
+    v = torch.zeros((3,) + shape, device="cuda")
+    reg = claire.Registration(shape, nt, beta, gamma)
+    reg.set_images(m0, m1)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        v.zero_()
+        return reg.solve(v)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        rep = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region ----------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    reg.profile_enable(True)
+    launches0 = reg.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reports = []
+    for _ in range(args.steps):
+        reports.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = reg.launch_count() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    prof = {k: reg.profile_read(i) for i, k in enumerate(KCLASS)}
+    reg.profile_enable(False)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N / (ms * 1e-3) / 1e9
+    rep = reports[-1]
+
+    # ---- Hessian matvec throughput at the solution (own events loop) -------
+    reg.linearize(v)
+    vt = torch.from_numpy(synth.smooth_direction(shape, 7)).cuda()
+    Hv = torch.empty_like(vt)
+    for _ in range(3):
+        reg.hess_matvec(None, vt, out=Hv)
+    torch.cuda.synchronize()
+    nmv = 20
+    e0.record(stream)
+    for _ in range(nmv):
+        reg.hess_matvec(None, vt, out=Hv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1) / nmv
+    mv_gvox = N / (mv_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel class ----------------------------
+    peak, peak_src = read_peaks()
+    dom = max(prof, key=lambda k: prof[k][1])
+    nl, kms, kby = prof[dom]
+    achieved = (kby / nl) / ((kms / nl) * 1e-3) / 1e9 if nl else 0.0
+    breakdown = {k: {"launches": n_, "ms_per_step": round(t_ / args.steps, 4),
+                     "GBps": round(b_ / (t_ * 1e-3) / 1e9, 1) if t_ > 0 else None}
+                 for k, (n_, t_, b_) in prof.items() if n_}
+    roofline = {"bound": "hbm", "kernel": dom, "kernels": KNAMES[dom],
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": traffic_for(dom, kby / nl if nl else 0, N),
+                "bytes_per_launch": kby / nl if nl else 0}
+
+    out = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "grid": list(shape), "nt": nt, "beta": beta,
+                   "gamma": gamma, "precond": "InvA", "eps_n": 5e-2,
+                   "l2": "inputs larger than L2 (working set ~5 GB)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "gn_solve_time_s": round(ms * 1e-3, 5),
+        "hess_matvec_gvoxel_s": round(mv_gvox, 4), "hess_matvec_ms": round(mv_ms, 4),
+        "solve": {"n_gn": rep.n_gn, "n_pcg": rep.n_pcg, "n_matvec": rep.n_matvec,
+                  "n_ls": rep.n_ls, "grel": rep.grel, "mismatch_rel": rep.mismatch_rel,
+                  "J": rep.J, "t_hess_ms": round(rep.t_hess_ms, 3),
+                  "t_grad_ms": round(rep.t_grad_ms, 3), "t_pc_ms": round(rep.t_pc_ms, 3),
+                  "t_obj_ms": round(rep.t_obj_ms, 3)},
+        "roofline": roofline, "kernel_breakdown": breakdown,
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    if not args.no_e2e:
+        hm0 = torch.from_numpy(w["m0"]).pin_memory()
+        hm1 = torch.from_numpy(w["m1"]).pin_memory()
+        hv0 = torch.zeros((3,) + shape).pin_memory()
+        hv = torch.empty((3,) + shape).pin_memory()
+        dm0, dm1 = torch.empty_like(m0), torch.empty_like(m1)
+
+        def e2e_step():
+            dm0.copy_(hm0, non_blocking=True)
+            dm1.copy_(hm1, non_blocking=True)
+            v.copy_(hv0, non_blocking=True)
+            reg.set_images(dm0, dm1)
+            r = reg.solve(v)
+            hv.copy_(v, non_blocking=True)
+            return r
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / args.steps
+        out["e2e"] = {"value": round(ws * N / (e_ms * 1e-3) / 1e9, 5), "unit": UNIT,
+                      "ms_per_step": round(e_ms, 3), "h2d_bytes_per_step": 5 * 4 * N,
+                      "d2h_bytes_per_step": 3 * 4 * N}
+
+    # ---- CPU baseline (FP64 oracle) and error vs FP64, rank 0 at N = 1 ------
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sample()
+        out["err_vs_fp64"] = error_vs_oracle(claire, synth)
+    reg.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline_sample(steps=1):
+    """Time the FP64 oracle's full solve of the same generator on a 64^3 grid
+    (host cores, OpenMP over all of them).  Reported per voxel, like value."""
+    import numpy as np
+
+    import oracle
+    from paper_2008_12820_gb300 import synth
+    oracle.build()
+    n = CPU_SAMPLE_N
+    w = synth.workload(WORKLOAD, shape=(n, n, n))
+    P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        _, rep = P.solve(np.zeros((3, n, n, n)))
+        times.append(time.perf_counter() - t)
+    t = min(times)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n ** 3 / t / 1e9, 7), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"full FP64 GN-Krylov solve of the same blob generator on a {n}^3 grid "
+                      f"({rep.n_gn} GN, {rep.n_pcg} PCG), {t:.2f} s; voxels/s",
+            "seconds": round(t, 3)}
+
+
+def error_vs_oracle(claire, synth):
+    """Relative L2 error of the GPU gradient, objective and Hessian matvec
+    against the FP64 oracle on the 128^3 instance of the same generator."""
+    import numpy as np
+    import torch
+
+    import oracle
+    n = ERR_CHECK_N
+    w = synth.workload(WORKLOAD, shape=(n, n, n))
+    v = (0.5 * w["v_true"]).astype(np.float32)
+    vt = synth.smooth_direction((n, n, n), 7)
+    P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
+    go, Jo = P.gradient(v)
+    Ho = P.matvec(vt)
+    with claire.Registration((n, n, n), w["nt"], w["beta"], w["gamma"]) as reg:
+        reg.set_images(torch.from_numpy(w["m0"]).cuda(), torch.from_numpy(w["m1"]).cuda())
+        g, J = reg.gradient(torch.from_numpy(v).cuda())
+        H = reg.hess_matvec(None, torch.from_numpy(vt).cuda())
+        torch.cuda.synchronize()
+        g, H = g.cpu().numpy().astype(np.float64), H.cpu().numpy().astype(np.float64)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return {"grid": [n, n, n], "gradient": rel(g, go), "hess_matvec": rel(H, Ho),
+            "objective": abs(J - Jo) / abs(Jo)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """The oracle as the reference arm: each step is a full FP64 solve of the
+    same generator on a 64^3 grid (a bounded sample of the 256^3 workload)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2008_12820_gb300 import synth
+    oracle.build()
+    n = CPU_SAMPLE_N
+    w = synth.workload(WORKLOAD, shape=(n, n, n))
+    P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
+    for _ in range(args.warmup):
+        P.solve(np.zeros((3, n, n, n)))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, rep = P.solve(np.zeros((3, n, n, n)))
+    t = (time.perf_counter() - t0) / args.steps
+    value = n ** 3 / t / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 7), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "grid": [256, 256, 256], "nt": 4, "beta": 1e-2,
+                   "gamma": 1.0, "precond": "InvA", "eps_n": 5e-2},
+        "cpu_baseline": {"value": round(value, 7), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"full FP64 GN-Krylov solve of the same generator on a "
+                                   f"{n}^3 grid ({rep.n_gn} GN, {rep.n_pcg} PCG); voxels/s"},
+        "e2e": {"value": round(value, 7), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * claire.h -- C ABI of the GB300 (sm_103a) Gauss-Newton-Krylov diffeomorphic
+ * registration library, after Brunn, Himthani, Biros, Mehl and Mang,
+ * "Multi-Node Multi-GPU Diffeomorphic Image Registration for Large-Scale
+ * Imaging Problems" (arXiv 2008.12820).
+ *
+ * The problem (paper Section 2.1, Eq. 2.1): find a stationary velocity v on
+ * the periodic domain Omega = [0, 2*pi)^3 minimizing
+ *     J(v) = 1/2 ||m(., 1) - m1||^2_{L2} + 1/2 <beta*A v, v>_{L2}
+ * subject to the transport equation d_t m + v . grad m = 0, m(., 0) = m0.
+ * beta*A is the vector Laplacian (H1 seminorm) augmented with a divergence
+ * penalty: beta*A = -beta * Laplace - gamma * grad div.
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * Grid: nx * ny * nz points, x_ijk = (i*hx, j*hy, k*hz), h = 2*pi/n per axis.
+ *   A scalar field is float[nx][ny][nz] (z contiguous); a vector field is
+ *   three scalar fields one after another, float[3][nx][ny][nz].  Velocities
+ *   are in domain units per unit time.  N = nx*ny*nz.
+ * Memory: every field pointer is DEVICE memory owned by the caller, 4-byte
+ *   aligned (16-byte alignment is faster), never retained past the call
+ *   (claire_set_images copies).  The context owns all workspace (allocated in
+ *   claire_create with cudaMalloc) and a cached linearization at the last v
+ *   given to claire_gradient / claire_linearize.
+ * Streams: all work is ordered on the context's stream (claire_set_stream;
+ *   default: the legacy default stream).  A call that returns a host scalar
+ *   synchronizes that stream before returning; other calls return as soon as
+ *   the work is enqueued.
+ * Errors: every call returns a claire_status.  On error the outputs are
+ *   unspecified, the context stays usable, and claire_last_error() gives a
+ *   message.  No C++ exception crosses this boundary.
+ * Threads: a context may be used by one host thread at a time.
+ * Inner products: <a, b>_{L2} is the sum over grid points times hx*hy*hz.
+ *   g below is the L2 (Riesz) gradient; the Euclidean gradient of the
+ *   discrete J is hx*hy*hz * g.
+ */
+#ifndef CLAIRE_H
+#define CLAIRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct claire_ctx claire_ctx;
+
+typedef enum {
+    CLAIRE_OK = 0,
+    CLAIRE_ERR_ARG = 1,          /* invalid argument (size, null pointer, parameter) */
+    CLAIRE_ERR_OOM = 2,          /* device allocation failed */
+    CLAIRE_ERR_CUDA = 3,         /* a CUDA call or kernel launch failed */
+    CLAIRE_ERR_STATE = 4,        /* call order violated (e.g. no images set) */
+    CLAIRE_ERR_NONFINITE = 5,    /* NaN/Inf detected in a gradient, objective or PCG scalar */
+    CLAIRE_ERR_LINESEARCH = 6,   /* Armijo line search found no acceptable step */
+    CLAIRE_ERR_PCG_BREAKDOWN = 7,/* PCG curvature p.Hp <= 0 (reported, not fatal in solve) */
+    CLAIRE_ERR_TIMEOUT = 8       /* a bounded device wait gave up */
+} claire_status;
+
+/* Create a context for an nx*ny*nz grid with nt semi-Lagrangian time steps
+ * (dt = 1/nt), regularization weight beta > 0 and divergence penalty
+ * gamma >= 0 (paper Section 2.1, Eq. 2.1; Section 3 "Discretization").
+ * Each n must be in [4, 1024] and a product of powers of 2, 3 and 5 (the
+ * pencil FFT radices); nt in [1, 256].  Allocates all device workspace on the
+ * current device.  *out receives the context or NULL on error. */
+int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, claire_ctx **out);
+
+/* Release the context and its device memory (NULL is a no-op). */
+int claire_destroy(claire_ctx *ctx);
+
+/* Order all later work of ctx on `stream` (a cudaStream_t; NULL = legacy). */
+int claire_set_stream(claire_ctx *ctx, void *stream);
+
+/* Change beta and gamma (same rules as claire_create); drops nothing but the
+ * cached gradient/objective values. */
+int claire_set_params(claire_ctx *ctx, double beta, double gamma);
+
+/* Copy template m0 and reference m1 (device, float[N] each) into ctx.
+ * Invalidates the cached linearization. */
+int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1);
+
+/* Forward problem (Eq. 2.1b by the semi-Lagrangian scheme of Section 3):
+ * m(.,1) from m0 along the RK2 backward characteristics of v (float[3][N]).
+ * Writes m(.,1) to m_final (float[N], nullable) and
+ * *mismatch = 1/2 ||m(.,1) - m1||^2_{L2} (nullable; synchronizes if given).
+ * Does not touch the cached linearization. */
+int claire_forward(claire_ctx *ctx, const float *v, float *m_final, double *mismatch);
+
+/* Objective J(v) of Eq. 2.1a: mismatch term plus 1/2 <beta*A v, v>_{L2}.
+ * Synchronizes. */
+int claire_objective(claire_ctx *ctx, const float *v, double *objective, double *mismatch);
+
+/* Linearize at v (float[3][N]): RK2 foot points X- and X+, the state history
+ * m^j (j = 0..nt), its spectral gradients grad m^j (stored, paper Section 5.2),
+ * div v and the adjoint source factor.  Cached for claire_hess_matvec. */
+int claire_linearize(claire_ctx *ctx, const float *v);
+
+/* Reduced gradient (Eq. 3.1): g = beta*A v + int_0^1 lambda grad m dt with
+ * lambda from the adjoint equation (Eq. 3.2), lambda(1) = m1 - m(1).
+ * Linearizes at v (cached).  g: float[3][N].  *objective (nullable; J of
+ * Eq. 2.1a at v) synchronizes. */
+int claire_gradient(claire_ctx *ctx, const float *v, float *g, double *objective);
+
+/* Gauss-Newton Hessian matvec (Eq. 3.4): Hvt = beta*A vt + int lt grad m dt,
+ * lt from the incremental adjoint (Eq. 3.6) with lt(1) = -mt(1), mt from the
+ * incremental state (Eq. 3.5).  v is the linearization point: if v is NULL the
+ * cached linearization is used (CLAIRE_ERR_STATE if there is none); otherwise
+ * v is compared on the device with the cached point and the context
+ * re-linearizes when they differ.  vt, Hvt: float[3][N] (may not alias). */
+int claire_hess_matvec(claire_ctx *ctx, const float *v, const float *vt, float *Hvt);
+
+/* Spectral preconditioner (Section 3 "Preconditioning"): s = (beta*A)^{-1} r,
+ * identity on the zero wavenumber.  r, s: float[3][N]; s may equal r. */
+int claire_precond(claire_ctx *ctx, const float *r, float *s);
+
+/* ---- single operators (for checks and composition) ------------------- */
+
+/* Spectral gradient of a scalar field (Section 3): g_d = F^-1[i k_d F f].
+ * f: float[N], g: float[3][N]. */
+int claire_grad(claire_ctx *ctx, const float *f, float *g);
+
+/* Spectral divergence of a vector field: out = sum_d F^-1[i k_d F v_d]. */
+int claire_div(claire_ctx *ctx, const float *v, float *out);
+
+/* beta*A applied to a vector field (Eq. 3.1 regularization term). */
+int claire_apply_A(claire_ctx *ctx, const float *v, float *out);
+
+/* Periodic cubic Lagrange interpolation (Section 4.1) of the scalar field f
+ * at the points x_ijk + disp_ijk, disp: float[3][N] in grid-index units.
+ * out: float[N]. */
+int claire_interp(claire_ctx *ctx, const float *f, const float *disp, float *out);
+
+/* Copy a part of the cached linearization into a caller buffer (float):
+ *   CLAIRE_FIELD_DISPM  X- minus x, index units, [3][N]
+ *   CLAIRE_FIELD_DISPP  X+ minus x, index units, [3][N]
+ *   CLAIRE_FIELD_STATE  m^j, [N]            (j = 0..nt)
+ *   CLAIRE_FIELD_GRADM  grad m^j, [3][N]    (j = 0..nt)
+ *   CLAIRE_FIELD_DIVV   div v, [N]
+ *   CLAIRE_FIELD_ADJF   adjoint factor c = 1 + dt/2 (d(X+) + d) + dt^2/2 d d(X+), [N]
+ *   CLAIRE_FIELD_ADJ    lambda^j of the last gradient, [N] (j = 0..nt)
+ *   CLAIRE_FIELD_INCADJ incremental adjoint lt^j of the last matvec, [N]
+ *   CLAIRE_FIELD_INCST  mt(1) of the last matvec, [N]                    */
+enum {
+    CLAIRE_FIELD_DISPM = 0, CLAIRE_FIELD_DISPP = 1, CLAIRE_FIELD_STATE = 2,
+    CLAIRE_FIELD_GRADM = 3, CLAIRE_FIELD_DIVV = 4, CLAIRE_FIELD_ADJF = 5,
+    CLAIRE_FIELD_ADJ = 6, CLAIRE_FIELD_INCADJ = 7, CLAIRE_FIELD_INCST = 8
+};
+int claire_get_field(claire_ctx *ctx, int which, int j, float *out);
+
+/* ---- Gauss-Newton-Krylov solver (Algorithm 1, Eq. 3.3) --------------- */
+
+typedef struct {
+    int max_gn;        /* max Gauss-Newton iterations (default 50) */
+    int max_pcg;       /* max PCG iterations per GN step (default 100) */
+    int fixed_pcg;     /* > 0: exactly this many PCG iterations per GN step */
+    double eps_n;      /* stop when ||g_k|| / ||g_0|| <= eps_n (default 5e-2) */
+    double armijo_c1;  /* sufficient decrease constant (default 1e-4) */
+    int max_ls;        /* max step halvings in the line search (default 12) */
+} claire_solve_opts;
+
+typedef struct {
+    int n_gn;          /* GN steps taken */
+    int n_pcg;         /* PCG iterations over all GN steps */
+    int n_matvec;      /* Hessian matvecs */
+    int n_precond;     /* preconditioner applications */
+    int n_ls;          /* objective evaluations in line searches */
+    int status;        /* claire_status of the solve */
+    double J0, J;      /* objective at the initial and final v */
+    double g0, g;      /* ||g|| (2-norm over the grid) at the initial and final v */
+    double grel;       /* g / g0 */
+    double mismatch_rel; /* ||m(1) - m1|| / ||m0 - m1|| at the final v */
+    double t_grad_ms, t_hess_ms, t_pc_ms, t_obj_ms, t_pcg_ms, t_total_ms; /* CUDA-event times */
+} claire_solve_report;
+
+/* Fill *opts with the defaults above. */
+void claire_solve_opts_default(claire_solve_opts *opts);
+
+/* Solve from the initial velocity in v_inout (device, float[3][N]); the
+ * result overwrites it.  PCG: x0 = 0, r0 = -g, preconditioner (beta*A)^{-1},
+ * forcing eps_K = min(sqrt(||g_k||/||g_0||), 0.5) (Algorithm 1), FP64 dot
+ * products; stops at ||r|| <= eps_K ||r0||, max_pcg, or p.Hp <= 0 (keeps the
+ * current iterate).  Armijo: alpha = 1, halve until
+ * J(v + alpha vt) <= J(v) + c1 alpha <g, vt>_{L2}.  report may be NULL.
+ * Returns CLAIRE_OK, or CLAIRE_ERR_LINESEARCH / CLAIRE_ERR_NONFINITE (v_inout
+ * then holds the last accepted iterate). */
+int claire_solve(claire_ctx *ctx, float *v_inout, const claire_solve_opts *opts,
+                 claire_solve_report *report);
+
+/* ---- instrumentation -------------------------------------------------- */
+
+/* Kernel classes timed by the profiler. */
+enum {
+    CLAIRE_K_FOOTPOINT = 0, CLAIRE_K_STATE = 1, CLAIRE_K_ADJOINT = 2,
+    CLAIRE_K_INCSTATE = 3, CLAIRE_K_INCADJ = 4, CLAIRE_K_BODYFORCE = 5,
+    CLAIRE_K_FFT_R2C = 6, CLAIRE_K_FFT_C2C = 7, CLAIRE_K_FFT_MUL = 8,
+    CLAIRE_K_FFT_C2R = 9, CLAIRE_K_REDUCE = 10, CLAIRE_K_VECTOR = 11,
+    CLAIRE_K_INTERP = 12, CLAIRE_K_COUNT = 13
+};
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing of every kernel the
+ * context launches (on its stream); enabling clears earlier records. */
+int claire_profile_enable(claire_ctx *ctx, int on);
+
+/* For one kernel class, since profiling was enabled: the number of timed
+ * launch groups, their summed device time (ms) and their summed algorithmic
+ * HBM bytes (every field a launch reads or writes counted once; a gathered
+ * field counted as one read).  Any output pointer may be NULL.  Synchronizes. */
+int claire_profile_read(claire_ctx *ctx, int kernel_class, long *launches, double *total_ms,
+                        double *total_bytes);
+
+/* Total number of kernels the context has launched since creation. */
+int claire_launch_count(const claire_ctx *ctx, long *launches);
+
+/* Device bytes held by the context. */
+int claire_workspace_bytes(const claire_ctx *ctx, size_t *bytes);
+
+/* Message of the last error on ctx (or of the last failed claire_create when
+ * ctx is NULL); never NULL. */
+const char *claire_last_error(const claire_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLAIRE_H */

@@ -1,0 +1,291 @@
+"""Thin ctypes binding of the C ABI in ``include/claire.h``.
+
+Argument marshalling only: every step of the registration runs in the CUDA
+kernels of ``libclaire_gb.so``.  Fields are torch CUDA tensors (float32,
+contiguous; vectors shaped ``[3, nx, ny, nz]``) whose device pointers are
+passed through.  There is no CPU path: if the library is missing or no GPU is
+present the calls raise.
+
+The function names mirror the C entry points (``claire_create``,
+``claire_gradient``, ...); :class:`Registration` bundles them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libclaire_gb.so")
+
+CLAIRE_OK = 0
+STATUS = {0: "CLAIRE_OK", 1: "CLAIRE_ERR_ARG", 2: "CLAIRE_ERR_OOM", 3: "CLAIRE_ERR_CUDA",
+          4: "CLAIRE_ERR_STATE", 5: "CLAIRE_ERR_NONFINITE", 6: "CLAIRE_ERR_LINESEARCH",
+          7: "CLAIRE_ERR_PCG_BREAKDOWN", 8: "CLAIRE_ERR_TIMEOUT"}
+
+FIELD = dict(dispm=0, dispp=1, state=2, gradm=3, divv=4, adjf=5, adj=6, incadj=7, incst=8)
+KERNEL = dict(footpoint=0, state=1, adjoint=2, incstate=3, incadj=4, bodyforce=5, fft_r2c=6,
+              fft_c2c=7, fft_mul=8, fft_c2r=9, reduce=10, vector=11, interp=12)
+
+EXPORTED = [
+    "claire_create", "claire_destroy", "claire_set_stream", "claire_set_params",
+    "claire_set_images", "claire_forward", "claire_objective", "claire_linearize",
+    "claire_gradient", "claire_hess_matvec", "claire_precond", "claire_grad", "claire_div",
+    "claire_apply_A", "claire_interp", "claire_get_field", "claire_solve_opts_default",
+    "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
+    "claire_workspace_bytes", "claire_last_error",
+]
+
+
+class ClaireError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("max_gn", ctypes.c_int), ("max_pcg", ctypes.c_int), ("fixed_pcg", ctypes.c_int),
+                ("eps_n", ctypes.c_double), ("armijo_c1", ctypes.c_double),
+                ("max_ls", ctypes.c_int)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int), ("n_matvec", ctypes.c_int),
+                ("n_precond", ctypes.c_int), ("n_ls", ctypes.c_int), ("status", ctypes.c_int),
+                ("J0", ctypes.c_double), ("J", ctypes.c_double), ("g0", ctypes.c_double),
+                ("g", ctypes.c_double), ("grel", ctypes.c_double),
+                ("mismatch_rel", ctypes.c_double), ("t_grad_ms", ctypes.c_double),
+                ("t_hess_ms", ctypes.c_double), ("t_pc_ms", ctypes.c_double),
+                ("t_obj_ms", ctypes.c_double), ("t_pcg_ms", ctypes.c_double),
+                ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libclaire_gb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "claire_create": [I, I, I, I, D, D, ctypes.POINTER(P)],
+        "claire_destroy": [P], "claire_set_stream": [P, V], "claire_set_params": [P, D, D],
+        "claire_set_images": [P, V, V], "claire_forward": [P, V, V, pd],
+        "claire_objective": [P, V, pd, pd], "claire_linearize": [P, V],
+        "claire_gradient": [P, V, V, pd], "claire_hess_matvec": [P, V, V, V],
+        "claire_precond": [P, V, V], "claire_grad": [P, V, V], "claire_div": [P, V, V],
+        "claire_apply_A": [P, V, V], "claire_interp": [P, V, V, V],
+        "claire_get_field": [P, I, I, V],
+        "claire_solve": [P, V, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
+        "claire_profile_enable": [P, I],
+        "claire_profile_read": [P, I, ctypes.POINTER(ctypes.c_long), pd, pd],
+        "claire_launch_count": [P, ctypes.POINTER(ctypes.c_long)],
+        "claire_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.claire_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
+    L.claire_solve_opts_default.restype = None
+    L.claire_last_error.argtypes = [P]
+    L.claire_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("fields must be contiguous float32 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, rc):
+    if rc != CLAIRE_OK:
+        msg = load().claire_last_error(ctx).decode()
+        raise ClaireError(rc, msg)
+
+
+@dataclass
+class Report:
+    n_gn: int
+    n_pcg: int
+    n_matvec: int
+    n_precond: int
+    n_ls: int
+    status: int
+    J0: float
+    J: float
+    g0: float
+    g: float
+    grel: float
+    mismatch_rel: float
+    t_grad_ms: float
+    t_hess_ms: float
+    t_pc_ms: float
+    t_obj_ms: float
+    t_pcg_ms: float
+    t_total_ms: float
+
+
+class Registration:
+    """One registration problem on an nx*ny*nz grid (a claire_ctx).
+
+    All field arguments are torch CUDA tensors on the current device; the
+    context runs on torch's current stream unless ``stream`` is given."""
+
+    def __init__(self, shape, nt, beta, gamma, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        nx, ny, nz = (int(s) for s in shape)
+        rc = L.claire_create(nx, ny, nz, int(nt), float(beta), float(gamma), ctypes.byref(h))
+        if rc != CLAIRE_OK:
+            raise ClaireError(rc, L.claire_last_error(None).decode())
+        self._h = h
+        self.shape = (nx, ny, nz)
+        self.nt, self.beta, self.gamma = nt, beta, gamma
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(h, L.claire_set_stream(h, ctypes.c_void_p(st.cuda_stream)))
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "_h", None):
+            load().claire_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _c(self, name, *args):
+        _check(self._h, getattr(load(), name)(self._h, *args))
+
+    def _new(self, *lead):
+        return torch.empty(lead + self.shape, device="cuda", dtype=torch.float32)
+
+    # ---- API ----
+    def set_params(self, beta, gamma):
+        self._c("claire_set_params", float(beta), float(gamma))
+        self.beta, self.gamma = beta, gamma
+
+    def set_images(self, m0, m1):
+        self._c("claire_set_images", _ptr(m0), _ptr(m1))
+
+    def forward(self, v, want_mismatch=True):
+        m = self._new()
+        mis = ctypes.c_double(0)
+        self._c("claire_forward", _ptr(v), _ptr(m), ctypes.byref(mis) if want_mismatch else None)
+        return m, mis.value
+
+    def objective(self, v):
+        J, mis = ctypes.c_double(0), ctypes.c_double(0)
+        self._c("claire_objective", _ptr(v), ctypes.byref(J), ctypes.byref(mis))
+        return J.value, mis.value
+
+    def linearize(self, v):
+        self._c("claire_linearize", _ptr(v))
+
+    def gradient(self, v, out=None, want_objective=True):
+        g = out if out is not None else self._new(3)
+        J = ctypes.c_double(0)
+        self._c("claire_gradient", _ptr(v), _ptr(g), ctypes.byref(J) if want_objective else None)
+        return g, J.value
+
+    def hess_matvec(self, v, vt, out=None):
+        Hv = out if out is not None else self._new(3)
+        self._c("claire_hess_matvec", _ptr(v), _ptr(vt), _ptr(Hv))
+        return Hv
+
+    def precond(self, r, out=None):
+        s = out if out is not None else self._new(3)
+        self._c("claire_precond", _ptr(r), _ptr(s))
+        return s
+
+    def grad(self, f):
+        g = self._new(3)
+        self._c("claire_grad", _ptr(f), _ptr(g))
+        return g
+
+    def div(self, v):
+        d = self._new()
+        self._c("claire_div", _ptr(v), _ptr(d))
+        return d
+
+    def apply_A(self, v):
+        out = self._new(3)
+        self._c("claire_apply_A", _ptr(v), _ptr(out))
+        return out
+
+    def interp(self, f, disp):
+        out = self._new()
+        self._c("claire_interp", _ptr(f), _ptr(disp), _ptr(out))
+        return out
+
+    def field(self, name, j=0):
+        comps = 3 if name in ("dispm", "dispp", "gradm") else 1
+        out = self._new(3) if comps == 3 else self._new()
+        self._c("claire_get_field", FIELD[name], int(j), _ptr(out))
+        return out
+
+    @staticmethod
+    def default_opts(**kw):
+        o = SolveOpts()
+        load().claire_solve_opts_default(ctypes.byref(o))
+        for k, val in kw.items():
+            setattr(o, k, val)
+        return o
+
+    def solve(self, v_inout, check=True, **opts):
+        o = self.default_opts(**opts)
+        rep = SolveReport()
+        rc = load().claire_solve(self._h, _ptr(v_inout), ctypes.byref(o), ctypes.byref(rep))
+        if check and rc not in (CLAIRE_OK,):
+            _check(self._h, rc)
+        return Report(**rep.as_dict())
+
+    def profile_enable(self, on=True):
+        self._c("claire_profile_enable", 1 if on else 0)
+
+    def profile_read(self, kernel):
+        """(launch groups, device ms, algorithmic bytes) of one kernel class."""
+        n, ms, by = ctypes.c_long(0), ctypes.c_double(0), ctypes.c_double(0)
+        self._c("claire_profile_read", KERNEL[kernel] if isinstance(kernel, str) else int(kernel),
+                ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+        return n.value, ms.value, by.value
+
+    def launch_count(self):
+        n = ctypes.c_long(0)
+        _check(self._h, load().claire_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def workspace_bytes(self):
+        n = ctypes.c_size_t(0)
+        _check(self._h, load().claire_workspace_bytes(self._h, ctypes.byref(n)))
+        return n.value

@@ -1,0 +1,732 @@
+// capi.cu -- the C ABI (include/claire.h): context and workspace, the
+// linearization cache, reduced gradient (Eq. 3.1), Gauss-Newton Hessian matvec
+// (Eq. 3.4), spectral preconditioner, PCG and the Gauss-Newton-Krylov solver
+// with Armijo line search (Algorithm 1, Eq. 3.3).
+//
+// All arithmetic on fields runs in the kernels of transport.cu, fft.cu and
+// vec.cu; this file only sequences launches on the context's stream and reads
+// back the FP64 scalars the Krylov and Newton iterations branch on.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "claire.h"
+#include "claire_internal.cuh"
+
+using namespace claire;
+
+namespace {
+
+struct Error : std::exception {
+    int code;
+    std::string msg;
+    Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+    const char *what() const noexcept override { return msg.c_str(); }
+};
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear a non-sticky error so the context stays usable
+        throw Error(e == cudaErrorMemoryAllocation ? CLAIRE_ERR_OOM : CLAIRE_ERR_CUDA,
+                    std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+#define CK(x) check_cuda((x), #x)
+
+void check_launch(const char *where) {
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(CLAIRE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    }
+}
+
+thread_local std::string g_create_error = "no error";
+
+bool valid_n(int n) {
+    if (n < 4 || n > 1024) return false;
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// radix sequence for a length-n Stockham FFT: 4s first, then 2, 3, 5
+FftPlan make_plan(int n) {
+    FftPlan p{};
+    p.n = n;
+    int m = n;
+    while (m % 4 == 0) { p.rad[p.nst++] = 4; m /= 4; }
+    while (m % 2 == 0) { p.rad[p.nst++] = 2; m /= 2; }
+    while (m % 3 == 0) { p.rad[p.nst++] = 3; m /= 3; }
+    while (m % 5 == 0) { p.rad[p.nst++] = 5; m /= 5; }
+    return p;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- profiler ----
+namespace claire {
+int Profiler::begin(int cls, double bytes, cudaStream_t st) {
+    if (!on) return -1;
+    if (used == recs.size()) {
+        Rec r{};
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+        recs.push_back(r);
+    }
+    recs[used].cls = cls;
+    recs[used].bytes = bytes;
+    cudaEventRecord(recs[used].a, st);
+    return (int)used++;
+}
+void Profiler::end(int slot, cudaStream_t st) { cudaEventRecord(recs[slot].b, st); }
+void Profiler::reset() { used = 0; }
+Profiler::~Profiler() {
+    for (auto &r : recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+}
+}  // namespace claire
+
+// --------------------------------------------------------------- context ---
+struct claire_ctx {
+    Dims d{};
+    int nt = 0;
+    double beta = 0, gamma = 0;
+    cudaStream_t st = 0;
+    std::string err = "no error";
+    FftPlan ax[3]{};
+    Profiler prof;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+
+    float *m0 = nullptr, *m1 = nullptr;
+    float *vlin = nullptr, *dispm = nullptr, *dispp = nullptr;
+    float *mhist = nullptr, *gmhist = nullptr, *divv = nullptr, *cfac = nullptr;
+    float *lhist = nullptr, *mt = nullptr;
+    float *s3a = nullptr, *s1a = nullptr, *s1b = nullptr, *fdisp = nullptr;
+    float2 *spec = nullptr;
+    double *partial = nullptr, *dres = nullptr;
+    int *dflag = nullptr;
+    // solver vectors, allocated on the first solve
+    float *sv = nullptr;
+
+    bool have_images = false, have_lin = false;
+
+    float *alloc_f(size_t n) { return (float *)alloc_bytes(n * sizeof(float)); }
+    void *alloc_bytes(size_t b) {
+        void *p = nullptr;
+        CK(cudaMalloc(&p, b));
+        allocs.push_back(p);
+        bytes += b;
+        return p;
+    }
+    ~claire_ctx() {
+        for (void *p : allocs) cudaFree(p);
+        for (int a = 0; a < 3; ++a) cudaFree((void *)ax[a].tw);
+    }
+
+    long long N() const { return d.N; }
+    float *hist(float *base, int j, int comps = 1) const { return base + (size_t)j * comps * d.N; }
+    double h3() const {
+        const double tp = 6.283185307179586476925286766559;
+        return (tp / d.n1) * (tp / d.n2) * (tp / d.n3);
+    }
+    SpecParams sp() const { return SpecParams{(float)beta, (float)gamma, (float)(1.0 / (double)d.N)}; }
+
+    double fetch(int slot = 0) {
+        double h = 0;
+        CK(cudaMemcpyAsync(&h, dres + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return h;
+    }
+    double dot(const float *a, const float *b, long long n) {
+        launch_dot(a, b, n, partial, dres, st, &prof);
+        return fetch();
+    }
+
+    // ---- operators ------------------------------------------------------
+    void spectral(SpecOp op, const float *in, float *out, const float *add) {
+        spectral_apply(d, ax, op, sp(), in, out, add, spec, st, &prof);
+    }
+
+    void linearize(const float *v) {
+        if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
+        const size_t N = d.N;
+        if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        launch_footpoints(d, nt, vlin, dispm, dispp, st, &prof);
+        CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        for (int j = 0; j < nt; ++j) launch_state_step(d, hist(mhist, j), dispm, hist(mhist, j + 1), st, &prof);
+        for (int j = 0; j <= nt; ++j) spectral(OP_GRAD, hist(mhist, j), hist(gmhist, j, 3), nullptr);
+        spectral(OP_DIV, vlin, divv, nullptr);
+        launch_adjoint_factor(d, nt, divv, dispp, cfac, st, &prof);
+        check_launch("linearize");
+        have_lin = true;
+    }
+
+    // adjoint solve + body force + beta A v; J into *J when asked
+    void gradient(const float *v, float *g, double *J, double *mis_out) {
+        linearize(v);
+        const size_t N = d.N;
+        launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
+        for (int j = nt; j >= 1; --j)
+            launch_adjoint_step(d, hist(lhist, j), dispp, cfac, hist(lhist, j - 1), st, &prof, CLAIRE_K_ADJOINT);
+        spectral(OP_A, vlin, s3a, nullptr);
+        launch_bodyforce(d, nt, lhist, gmhist, s3a, g, st, &prof);
+        check_launch("gradient");
+        if (J || mis_out) {
+            const double H3 = h3();
+            const double mis = 0.5 * H3 * dot(hist(lhist, nt), hist(lhist, nt), (long long)N);
+            const double reg = 0.5 * H3 * dot(vlin, s3a, 3 * (long long)N);
+            if (J) *J = mis + reg;
+            if (mis_out) *mis_out = mis;
+        }
+    }
+
+    void matvec(const float *vt, float *Hvt) {
+        if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
+        const float dt = 1.f / nt;
+        float *u = s1a, *un = s1b;
+        launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
+        for (int j = 0; j < nt; ++j) {
+            launch_incstate_step(d, dt, u, dispm, vt, hist(gmhist, j + 1, 3), un, st, &prof);
+            float *t = u; u = un; un = t;
+        }
+        launch_incadj_init(d, dt, u, vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
+        for (int j = nt; j >= 1; --j)
+            launch_adjoint_step(d, hist(lhist, j), dispp, cfac, hist(lhist, j - 1), st, &prof, CLAIRE_K_INCADJ);
+        launch_bodyforce(d, nt, lhist, gmhist, nullptr, Hvt, st, &prof);
+        spectral(OP_A, vt, Hvt, Hvt);
+        check_launch("hess_matvec");
+    }
+
+    // m(1) for v into mout (N); uses fdisp, s1a, s1b; leaves the cache alone
+    const float *forward(const float *v) {
+        if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
+        launch_footpoints(d, nt, v, fdisp, nullptr, st, &prof);
+        const float *src = m0;
+        float *a = s1a, *b = s1b;
+        for (int j = 0; j < nt; ++j) {
+            launch_state_step(d, src, fdisp, a, st, &prof);
+            src = a;
+            float *t = a; a = b; b = t;
+        }
+        check_launch("forward");
+        return src;
+    }
+
+    double mismatch_of(const float *mfinal) {
+        launch_sqdiff(mfinal, m1, d.N, partial, dres, st, &prof);
+        return 0.5 * h3() * fetch();
+    }
+
+    double objective(const float *v, double *mis_out) {
+        const float *mf = forward(v);
+        const double mis = mismatch_of(mf);
+        spectral(OP_A, v, s3a, nullptr);
+        const double reg = 0.5 * h3() * dot(v, s3a, 3 * d.N);
+        if (mis_out) *mis_out = mis;
+        return mis + reg;
+    }
+};
+
+// -------------------------------------------------------------- helpers ----
+#define API_BEGIN(ctx)                                                        \
+    if (!(ctx)) return CLAIRE_ERR_ARG;                                        \
+    try {
+#define API_END(ctx)                                                          \
+    }                                                                         \
+    catch (const Error &e) {                                                  \
+        (ctx)->err = e.msg;                                                   \
+        return e.code;                                                        \
+    }                                                                         \
+    catch (const std::bad_alloc &) {                                          \
+        (ctx)->err = "host allocation failed";                                \
+        return CLAIRE_ERR_OOM;                                                \
+    }                                                                         \
+    catch (const std::exception &e) {                                         \
+        (ctx)->err = e.what();                                                \
+        return CLAIRE_ERR_CUDA;                                               \
+    }                                                                         \
+    return CLAIRE_OK;
+
+static void need(const void *p, const char *name) {
+    if (!p) throw Error(CLAIRE_ERR_ARG, std::string(name) + " is NULL");
+}
+
+static void check_params(double beta, double gamma) {
+    if (!(beta > 0) || !std::isfinite(beta)) throw Error(CLAIRE_ERR_ARG, "beta must be finite and > 0");
+    if (!(gamma >= 0) || !std::isfinite(gamma)) throw Error(CLAIRE_ERR_ARG, "gamma must be finite and >= 0");
+}
+
+// ------------------------------------------------------------------- ABI ---
+extern "C" {
+
+int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, claire_ctx **out) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return CLAIRE_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!valid_n(nx) || !valid_n(ny) || !valid_n(nz)) {
+        g_create_error = "grid sizes must be in [4, 1024] with prime factors 2, 3, 5 only";
+        return CLAIRE_ERR_ARG;
+    }
+    if (nt < 1 || nt > 256) {
+        g_create_error = "nt must be in [1, 256]";
+        return CLAIRE_ERR_ARG;
+    }
+    claire_ctx *c = nullptr;
+    try {
+        check_params(beta, gamma);
+        c = new claire_ctx();
+        c->d.n1 = nx;
+        c->d.n2 = ny;
+        c->d.n3 = nz;
+        c->d.N = (long long)nx * ny * nz;
+        c->d.h3 = nz / 2 + 1;
+        c->d.p3 = (c->d.h3 + 3) / 4 * 4;
+        c->nt = nt;
+        c->beta = beta;
+        c->gamma = gamma;
+        const int ns[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; ++a) {
+            c->ax[a] = make_plan(ns[a]);
+            std::vector<float2> tw(ns[a]);
+            for (int t = 0; t < ns[a]; ++t) {
+                const double ang = 6.283185307179586476925286766559 * (double)t / (double)ns[a];
+                tw[t] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+            }
+            float2 *dtw = nullptr;
+            CK(cudaMalloc(&dtw, ns[a] * sizeof(float2)));
+            c->ax[a].tw = dtw;
+            CK(cudaMemcpy(dtw, tw.data(), ns[a] * sizeof(float2), cudaMemcpyHostToDevice));
+        }
+        const size_t N = c->d.N;
+        c->m0 = c->alloc_f(N);
+        c->m1 = c->alloc_f(N);
+        c->vlin = c->alloc_f(3 * N);
+        c->dispm = c->alloc_f(3 * N);
+        c->dispp = c->alloc_f(3 * N);
+        c->mhist = c->alloc_f((size_t)(nt + 1) * N);
+        c->gmhist = c->alloc_f((size_t)(nt + 1) * 3 * N);
+        c->divv = c->alloc_f(N);
+        c->cfac = c->alloc_f(N);
+        c->lhist = c->alloc_f((size_t)(nt + 1) * N);
+        c->mt = c->alloc_f(N);
+        c->s3a = c->alloc_f(3 * N);
+        c->s1a = c->alloc_f(N);
+        c->s1b = c->alloc_f(N);
+        c->fdisp = c->alloc_f(3 * N);
+        c->spec = (float2 *)c->alloc_bytes((size_t)3 * nx * ny * c->d.p3 * sizeof(float2));
+        c->partial = (double *)c->alloc_bytes(kReduceBlocks * sizeof(double));
+        c->dres = (double *)c->alloc_bytes(8 * sizeof(double));
+        c->dflag = (int *)c->alloc_bytes(sizeof(int));
+    } catch (const Error &e) {
+        g_create_error = e.msg;
+        delete c;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_create_error = "host allocation failed";
+        delete c;
+        return CLAIRE_ERR_OOM;
+    }
+    *out = c;
+    return CLAIRE_OK;
+}
+
+int claire_destroy(claire_ctx *ctx) {
+    if (!ctx) return CLAIRE_OK;
+    cudaStreamSynchronize(ctx->st);
+    delete ctx;
+    return CLAIRE_OK;
+}
+
+int claire_set_stream(claire_ctx *ctx, void *stream) {
+    API_BEGIN(ctx)
+    ctx->st = (cudaStream_t)stream;
+    API_END(ctx)
+}
+
+int claire_set_params(claire_ctx *ctx, double beta, double gamma) {
+    API_BEGIN(ctx)
+    check_params(beta, gamma);
+    ctx->beta = beta;
+    ctx->gamma = gamma;
+    API_END(ctx)
+}
+
+int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1) {
+    API_BEGIN(ctx)
+    need(m0, "m0");
+    need(m1, "m1");
+    const size_t b = ctx->d.N * sizeof(float);
+    CK(cudaMemcpyAsync(ctx->m0, m0, b, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->m1, m1, b, cudaMemcpyDeviceToDevice, ctx->st));
+    ctx->have_images = true;
+    ctx->have_lin = false;
+    API_END(ctx)
+}
+
+int claire_forward(claire_ctx *ctx, const float *v, float *m_final, double *mismatch) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    const float *mf = ctx->forward(v);
+    if (m_final)
+        CK(cudaMemcpyAsync(m_final, mf, ctx->d.N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    if (mismatch) *mismatch = ctx->mismatch_of(mf);
+    API_END(ctx)
+}
+
+int claire_objective(claire_ctx *ctx, const float *v, double *objective, double *mismatch) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    need(objective, "objective");
+    *objective = ctx->objective(v, mismatch);
+    API_END(ctx)
+}
+
+int claire_linearize(claire_ctx *ctx, const float *v) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    ctx->linearize(v);
+    API_END(ctx)
+}
+
+int claire_gradient(claire_ctx *ctx, const float *v, float *g, double *objective) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    need(g, "g");
+    ctx->gradient(v, g, objective, nullptr);
+    API_END(ctx)
+}
+
+int claire_hess_matvec(claire_ctx *ctx, const float *v, const float *vt, float *Hvt) {
+    API_BEGIN(ctx)
+    need(vt, "vt");
+    need(Hvt, "Hvt");
+    if (vt == Hvt) throw Error(CLAIRE_ERR_ARG, "vt and Hvt may not alias");
+    if (v) {
+        bool same = false;
+        if (ctx->have_lin) {
+            launch_diff_flag(v, ctx->vlin, 3 * ctx->d.N, ctx->dflag, ctx->st, &ctx->prof);
+            int h = 1;
+            CK(cudaMemcpyAsync(&h, ctx->dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+            CK(cudaStreamSynchronize(ctx->st));
+            same = (h == 0);
+        }
+        if (!same) ctx->linearize(v);
+    }
+    ctx->matvec(vt, Hvt);
+    API_END(ctx)
+}
+
+int claire_precond(claire_ctx *ctx, const float *r, float *s) {
+    API_BEGIN(ctx)
+    need(r, "r");
+    need(s, "s");
+    ctx->spectral(OP_AINV, r, s, nullptr);
+    check_launch("precond");
+    API_END(ctx)
+}
+
+int claire_grad(claire_ctx *ctx, const float *f, float *g) {
+    API_BEGIN(ctx)
+    need(f, "f");
+    need(g, "g");
+    ctx->spectral(OP_GRAD, f, g, nullptr);
+    check_launch("grad");
+    API_END(ctx)
+}
+
+int claire_div(claire_ctx *ctx, const float *v, float *out) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    need(out, "out");
+    ctx->spectral(OP_DIV, v, out, nullptr);
+    check_launch("div");
+    API_END(ctx)
+}
+
+int claire_apply_A(claire_ctx *ctx, const float *v, float *out) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    need(out, "out");
+    ctx->spectral(OP_A, v, out, nullptr);
+    check_launch("apply_A");
+    API_END(ctx)
+}
+
+int claire_interp(claire_ctx *ctx, const float *f, const float *disp, float *out) {
+    API_BEGIN(ctx)
+    need(f, "f");
+    need(disp, "disp");
+    need(out, "out");
+    if (f == out) throw Error(CLAIRE_ERR_ARG, "f and out may not alias");
+    launch_interp(ctx->d, f, disp, out, ctx->st, &ctx->prof, CLAIRE_K_INTERP);
+    check_launch("interp");
+    API_END(ctx)
+}
+
+int claire_get_field(claire_ctx *ctx, int which, int j, float *out) {
+    API_BEGIN(ctx)
+    need(out, "out");
+    const size_t N = ctx->d.N;
+    const float *src = nullptr;
+    size_t n = N;
+    const bool hist = (which == CLAIRE_FIELD_STATE || which == CLAIRE_FIELD_GRADM ||
+                       which == CLAIRE_FIELD_ADJ || which == CLAIRE_FIELD_INCADJ);
+    if (hist && (j < 0 || j > ctx->nt)) throw Error(CLAIRE_ERR_ARG, "time index out of range");
+    if (which != CLAIRE_FIELD_ADJ && which != CLAIRE_FIELD_INCADJ && which != CLAIRE_FIELD_INCST &&
+        !ctx->have_lin)
+        throw Error(CLAIRE_ERR_STATE, "no linearization");
+    switch (which) {
+        case CLAIRE_FIELD_DISPM: src = ctx->dispm; n = 3 * N; break;
+        case CLAIRE_FIELD_DISPP: src = ctx->dispp; n = 3 * N; break;
+        case CLAIRE_FIELD_STATE: src = ctx->hist(ctx->mhist, j); break;
+        case CLAIRE_FIELD_GRADM: src = ctx->hist(ctx->gmhist, j, 3); n = 3 * N; break;
+        case CLAIRE_FIELD_DIVV: src = ctx->divv; break;
+        case CLAIRE_FIELD_ADJF: src = ctx->cfac; break;
+        case CLAIRE_FIELD_ADJ:
+        case CLAIRE_FIELD_INCADJ: src = ctx->hist(ctx->lhist, j); break;
+        case CLAIRE_FIELD_INCST: src = ctx->mt; break;
+        default: throw Error(CLAIRE_ERR_ARG, "unknown field");
+    }
+    CK(cudaMemcpyAsync(out, src, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    API_END(ctx)
+}
+
+void claire_solve_opts_default(claire_solve_opts *o) {
+    if (!o) return;
+    o->max_gn = 50;
+    o->max_pcg = 100;
+    o->fixed_pcg = 0;
+    o->eps_n = 5e-2;
+    o->armijo_c1 = 1e-4;
+    o->max_ls = 12;
+}
+
+namespace {
+struct EvTimer {
+    cudaEvent_t a{}, b{};
+    cudaStream_t st;
+    double *acc;
+    EvTimer(cudaStream_t s, double *acc_) : st(s), acc(acc_) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+    }
+    ~EvTimer() {
+        float ms = 0;
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        *acc += ms;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+}  // namespace
+
+int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, claire_solve_report *rep_out) {
+    API_BEGIN(ctx)
+    need(v, "v_inout");
+    claire_solve_opts o;
+    if (opts) o = *opts; else claire_solve_opts_default(&o);
+    if (o.max_gn < 0 || o.max_pcg < 1 || o.fixed_pcg < 0 || !(o.eps_n >= 0) || o.max_ls < 0)
+        throw Error(CLAIRE_ERR_ARG, "invalid solve options");
+    claire_solve_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    const long long n3 = 3 * ctx->d.N;
+    if (!ctx->sv) ctx->sv = ctx->alloc_f((size_t)7 * n3);
+    float *g = ctx->sv, *x = g + n3, *r = x + n3, *z = r + n3, *p = z + n3, *q = p + n3, *vn = q + n3;
+    const double H3 = ctx->h3();
+    cudaStream_t st = ctx->st;
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    struct EvFree {
+        cudaEvent_t a, b;
+        ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } evfree{ev0, ev1};
+    CK(cudaEventRecord(ev0, st));
+    double J = 0;
+    {
+        EvTimer t(st, &rep.t_grad_ms);
+        ctx->gradient(v, g, &J, nullptr);
+    }
+    const double g0 = std::sqrt(ctx->dot(g, g, n3));
+    if (!std::isfinite(g0) || !std::isfinite(J)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite gradient or objective");
+    rep.J0 = J;
+    rep.g0 = g0;
+    double gn = g0;
+    int k = 0;
+    int status = CLAIRE_OK;
+    for (;;) {
+        const double grel = g0 > 0 ? gn / g0 : 0.0;
+        if (grel <= o.eps_n || k >= o.max_gn) break;
+        const double epsk = std::fmin(std::sqrt(grel), 0.5);
+        // ---- PCG on H x = -g, x0 = 0
+        double t_pcg = 0;
+        {
+            EvTimer tp(st, &t_pcg);
+            CK(cudaMemsetAsync(x, 0, n3 * sizeof(float), st));
+            launch_axpby(r, -1.f, g, 0.f, nullptr, n3, st, &ctx->prof);
+            const double r0 = std::sqrt(ctx->dot(r, r, n3));
+            const int maxit = o.fixed_pcg > 0 ? o.fixed_pcg : o.max_pcg;
+            int it = 0;
+            if (r0 > 0) {
+                {
+                    EvTimer t(st, &rep.t_pc_ms);
+                    ctx->spectral(OP_AINV, r, z, nullptr);
+                }
+                rep.n_precond++;
+                CK(cudaMemcpyAsync(p, z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                double rz = ctx->dot(r, z, n3);
+                while (it < maxit) {
+                    {
+                        EvTimer t(st, &rep.t_hess_ms);
+                        ctx->matvec(p, q);
+                    }
+                    rep.n_matvec++;
+                    const double pq = ctx->dot(p, q, n3);
+                    if (!std::isfinite(pq)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite p.Hp in PCG");
+                    if (pq <= 0) {
+                        if (it == 0) CK(cudaMemcpyAsync(x, z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                        ++it;
+                        break;
+                    }
+                    const double alpha = rz / pq;
+                    launch_pcg_xr(x, r, p, q, (float)alpha, n3, ctx->partial, ctx->dres, st, &ctx->prof);
+                    ++it;
+                    const double rn = std::sqrt(ctx->fetch());
+                    if (o.fixed_pcg == 0 && rn <= epsk * r0) break;
+                    if (it >= maxit) break;
+                    {
+                        EvTimer t(st, &rep.t_pc_ms);
+                        ctx->spectral(OP_AINV, r, z, nullptr);
+                    }
+                    rep.n_precond++;
+                    const double rz_new = ctx->dot(r, z, n3);
+                    const double beta = rz_new / rz;
+                    rz = rz_new;
+                    launch_pcg_p(p, z, (float)beta, n3, st, &ctx->prof);
+                }
+            }
+            rep.n_pcg += it;
+        }
+        rep.t_pcg_ms += t_pcg;
+        // ---- Armijo backtracking
+        const double slope = H3 * ctx->dot(g, x, n3);
+        double alpha = 1.0;
+        bool ok = false;
+        {
+            EvTimer t(st, &rep.t_obj_ms);
+            for (int ls = 0; ls <= o.max_ls; ++ls) {
+                launch_axpby(vn, 1.f, v, (float)alpha, x, n3, st, &ctx->prof);
+                const double Jt = ctx->objective(vn, nullptr);
+                rep.n_ls++;
+                if (std::isfinite(Jt) && Jt <= J + o.armijo_c1 * alpha * slope) {
+                    ok = true;
+                    break;
+                }
+                alpha *= 0.5;
+            }
+        }
+        if (!ok) {
+            status = CLAIRE_ERR_LINESEARCH;
+            break;
+        }
+        CK(cudaMemcpyAsync(v, vn, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        ++k;
+        {
+            EvTimer t(st, &rep.t_grad_ms);
+            ctx->gradient(v, g, &J, nullptr);
+        }
+        gn = std::sqrt(ctx->dot(g, g, n3));
+        if (!std::isfinite(gn) || !std::isfinite(J)) {
+            status = CLAIRE_ERR_NONFINITE;
+            break;
+        }
+    }
+    rep.n_gn = k;
+    rep.J = J;
+    rep.g = gn;
+    rep.grel = g0 > 0 ? gn / g0 : 0.0;
+    {
+        // relative mismatch at the final v: the cached state is at v
+        launch_sqdiff(ctx->hist(ctx->mhist, ctx->nt), ctx->m1, ctx->d.N, ctx->partial, ctx->dres, st, &ctx->prof);
+        const double a = ctx->fetch();
+        launch_sqdiff(ctx->m0, ctx->m1, ctx->d.N, ctx->partial, ctx->dres, st, &ctx->prof);
+        const double b = ctx->fetch();
+        rep.mismatch_rel = b > 0 ? std::sqrt(a / b) : 0.0;
+    }
+    rep.status = status;
+    {
+        float ms = 0;
+        CK(cudaEventRecord(ev1, st));
+        CK(cudaEventSynchronize(ev1));
+        CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        rep.t_total_ms = ms;
+    }
+    if (rep_out) *rep_out = rep;
+    if (status != CLAIRE_OK) {
+        ctx->err = status == CLAIRE_ERR_LINESEARCH ? "line search failed" : "non-finite gradient";
+        return status;
+    }
+    API_END(ctx)
+}
+
+int claire_profile_enable(claire_ctx *ctx, int on) {
+    API_BEGIN(ctx)
+    ctx->prof.on = on != 0;
+    ctx->prof.reset();
+    API_END(ctx)
+}
+
+int claire_profile_read(claire_ctx *ctx, int cls, long *launches, double *total_ms,
+                        double *total_bytes) {
+    API_BEGIN(ctx)
+    if (cls < 0 || cls >= CLAIRE_K_COUNT) throw Error(CLAIRE_ERR_ARG, "kernel class out of range");
+    CK(cudaStreamSynchronize(ctx->st));
+    long n = 0;
+    double ms = 0, by = 0;
+    for (size_t i = 0; i < ctx->prof.used; ++i) {
+        auto &r = ctx->prof.recs[i];
+        if (r.cls != cls) continue;
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        by += r.bytes;
+        ++n;
+    }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = ms;
+    if (total_bytes) *total_bytes = by;
+    API_END(ctx)
+}
+
+int claire_launch_count(const claire_ctx *ctx, long *launches) {
+    if (!ctx || !launches) return CLAIRE_ERR_ARG;
+    *launches = ctx->prof.launches;
+    return CLAIRE_OK;
+}
+
+int claire_workspace_bytes(const claire_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return CLAIRE_ERR_ARG;
+    *bytes = ctx->bytes;
+    return CLAIRE_OK;
+}
+
+const char *claire_last_error(const claire_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// claire_internal.cuh -- internal declarations of the GB300 registration library.
+//
+// Layout (all device memory):
+//   scalar field  float[n1][n2][n3]        (x3 contiguous)
+//   vector field  float[3][n1][n2][n3]
+//   half spectrum float2[c][n1][n2][p3]    (k3 = 0..h3-1 valid, h3 = n3/2+1,
+//                                           p3 = h3 rounded up to 4: pitch)
+// Wavenumbers on an axis of n points: index i -> i for 2i < n, else i - n.
+// First derivatives use 0 at the Nyquist index of an even axis.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "claire.h"
+
+namespace claire {
+
+struct Profiler;
+
+constexpr int kMaxStages = 16;
+constexpr int kThreads = 256;
+
+// plan of a 1D FFT of length n: radix per stage and the twiddle table
+// tw[t] = exp(-2*pi*i*t/n), t = 0..n-1 (computed on the host in double)
+struct FftPlan {
+    int n;
+    int nst;
+    int rad[kMaxStages];
+    const float2 *tw;
+};
+
+struct Dims {
+    int n1, n2, n3;
+    long long N;     // n1*n2*n3
+    int h3, p3;      // half-spectrum length and pitch along x3
+};
+
+// spectral operators applied in the fused x1 pass
+enum SpecOp { OP_GRAD = 0, OP_DIV = 1, OP_A = 2, OP_AINV = 3 };
+
+// epilogues of the inverse x3 pass
+enum C2rEpi { EPI_STORE = 0, EPI_ADD = 1 };
+
+struct SpecParams {
+    float beta, gamma, scale;  // scale = 1/N folds the inverse-FFT normalization
+};
+
+// ------------------------------------------------------------------ FFT ----
+// out-of-place forward: real [ncomp][n1][n2][n3] -> spectrum [ncomp] ;
+// multiply ; inverse into real [nout][n1][n2][n3] (+ optional addend)
+void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParams &sp,
+                    const float *in, float *out, const float *add, float2 *spec,
+                    cudaStream_t st, Profiler *prof);
+
+// ------------------------------------------------------------ transport ----
+void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
+                       cudaStream_t st, Profiler *prof);
+void launch_interp(const Dims &d, const float *f, const float *disp, float *out,
+                   cudaStream_t st, Profiler *prof, int kclass);
+void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
+                           float *cfac, cudaStream_t st, Profiler *prof);
+void launch_state_step(const Dims &d, const float *src, const float *dispm, float *dst,
+                       cudaStream_t st, Profiler *prof);
+void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const float *cfac,
+                         float *dst, cudaStream_t st, Profiler *prof, int kclass);
+void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
+                          cudaStream_t st, Profiler *prof);
+void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
+                          const float *vt, const float *gm_next, float *dst, cudaStream_t st,
+                          Profiler *prof);
+void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
+                        const float *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
+                        Profiler *prof);
+void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
+                Profiler *prof);  // out = a - b
+void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,
+                      const float *add, float *out, cudaStream_t st, Profiler *prof);
+
+// ------------------------------------------------------------- vectors ----
+// FP64 reductions; results land in dev_out[0..k) (device doubles)
+void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
+                cudaStream_t st, Profiler *prof);
+void launch_sqdiff(const float *a, const float *b, long long n, double *partial,
+                   double *dev_out, cudaStream_t st, Profiler *prof);
+void launch_pcg_xr(float *x, float *r, const float *p, const float *q, float alpha,
+                   long long n, double *partial, double *dev_out, cudaStream_t st,
+                   Profiler *prof);  // x += a p, r -= a q, out = ||r||^2
+void launch_pcg_p(float *p, const float *z, float beta, long long n, cudaStream_t st,
+                  Profiler *prof);   // p = z + beta p
+void launch_axpby(float *out, float a, const float *x, float b, const float *y, long long n,
+                  cudaStream_t st, Profiler *prof);  // out = a x + b y
+void launch_diff_flag(const float *a, const float *b, long long n, int *flag, cudaStream_t st,
+                      Profiler *prof);
+constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
+
+// ------------------------------------------------------------ profiler ----
+// Counts kernel launches and, when on, brackets each launch group with CUDA
+// events on its stream and records the algorithmic HBM bytes it moves (each
+// input and output field counted once, gathers counted as one read).
+struct Profiler {
+    bool on = false;
+    long launches = 0;
+    struct Rec { cudaEvent_t a, b; int cls; double bytes; };
+    std::vector<Rec> recs;
+    size_t used = 0;
+    // mark the start of a launch of class cls on stream st; returns slot or -1
+    int begin(int cls, double bytes, cudaStream_t st);
+    void end(int slot, cudaStream_t st);
+    void reset();
+    ~Profiler();
+};
+
+struct ProfScope {
+    Profiler *p;
+    int slot;
+    cudaStream_t st;
+    // nk = kernels launched inside the scope
+    ProfScope(Profiler *p_, int cls, cudaStream_t st_, double bytes = 0, int nk = 1)
+        : p(p_), slot(-1), st(st_) {
+        if (p) { p->launches += nk; slot = p->begin(cls, bytes, st); }
+    }
+    ~ProfScope() { if (p && slot >= 0) p->end(slot, st); }
+};
+
+}  // namespace claire

@@ -1,0 +1,186 @@
+// vec.cu -- FP64-accumulated reductions and fused vector updates for PCG and
+// the Gauss-Newton step (paper Algorithm 1; Eq. 3.3).
+//
+// Reductions: FP64 is slow on this part, so a thread does not widen every
+// element.  It accumulates its grid-stride range with error-free
+// transformations in FP32 (the compensated dot product of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005: TwoProduct
+// by fma, TwoSum by Knuth), which is as accurate as summing in twice the
+// working precision; the pair (sum, compensation) is widened to FP64 once, a
+// block reduces in FP64 by warp shuffles, block partials go to a fixed-size
+// array, and one block sums them in a fixed order: deterministic for a given
+// grid.
+#include <cuda_runtime.h>
+
+#include "claire_internal.cuh"
+
+namespace claire {
+
+namespace {
+
+constexpr int RT = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block sum of v; valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[RT / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (w == 0) {
+        v = lane < RT / 32 ? ws[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// compensated accumulator: the exact value of the sum so far is s + c up to
+// O(eps^2) relative terms.  The _rn intrinsics keep the compiler from fusing
+// a product into a neighbouring add, which would break the error terms.
+struct Acc2 {
+    float s = 0.f, c = 0.f;
+    // add the exact product x*y
+    __device__ __forceinline__ void add_prod(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        const float ep = fmaf(x, y, -p);  // TwoProduct error
+        add(p, ep);
+    }
+    // add p + ep (ep a small correction)
+    __device__ __forceinline__ void add(float p, float ep) {
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // TwoSum error
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(es, ep));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// MODE 0: sum a*b;  MODE 1: sum (a-b)^2
+template <int MODE>
+__global__ void __launch_bounds__(RT) k_reduce2(const float *__restrict__ a, const float *__restrict__ b,
+                                                long long n, double *__restrict__ partial) {
+    Acc2 acc;
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride) {
+        const float x = a[i], y = b[i];
+        if (MODE == 0) {
+            acc.add_prod(x, y);
+        } else {
+            // d = x - y exactly as dh + dl (TwoSum), then d^2 ~ dh^2 + 2 dh dl
+            const float dh = __fsub_rn(x, y);
+            const float z = __fsub_rn(dh, x);
+            const float dl = __fadd_rn(__fsub_rn(x, __fsub_rn(dh, z)), __fsub_rn(-y, z));
+            const float p = __fmul_rn(dh, dh);
+            acc.add(p, fmaf(dh, dh, -p) + 2.f * dh * dl);
+        }
+    }
+    double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RT) k_finalize(const double *__restrict__ partial, int nb,
+                                                 double *__restrict__ out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += RT) s += partial[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[0] = s;
+}
+
+// x += alpha p ; r -= alpha q ; partial sums of r.r
+__global__ void __launch_bounds__(RT) k_pcg_xr(float *__restrict__ x, float *__restrict__ r,
+                                               const float *__restrict__ p, const float *__restrict__ q,
+                                               float alpha, long long n, double *__restrict__ partial) {
+    Acc2 acc;
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride) {
+        x[i] = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        acc.add_prod(ri, ri);
+    }
+    double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(RT) k_pcg_p(float *__restrict__ p, const float *__restrict__ z,
+                                              float beta, long long n) {
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride)
+        p[i] = fmaf(beta, p[i], z[i]);
+}
+
+__global__ void __launch_bounds__(RT) k_axpby(float *__restrict__ out, float a, const float *__restrict__ x,
+                                              float b, const float *__restrict__ y, long long n) {
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride)
+        out[i] = y ? fmaf(a, x[i], b * y[i]) : a * x[i];
+}
+
+__global__ void __launch_bounds__(RT) k_diff_flag(const float *__restrict__ a, const float *__restrict__ b,
+                                                  long long n, int *__restrict__ flag) {
+    const long long stride = (long long)gridDim.x * RT;
+    bool diff = false;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride)
+        diff |= (__float_as_uint(a[i]) != __float_as_uint(b[i]));
+    if (__syncthreads_or(diff) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+inline int blocks_for(long long n) {
+    long long b = (n + RT - 1) / RT;
+    return (int)(b < kReduceBlocks ? b : kReduceBlocks);
+}
+
+}  // namespace
+
+void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
+                cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st, 8.0 * n, 2);
+    const int nb = blocks_for(n);
+    k_reduce2<0><<<nb, RT, 0, st>>>(a, b, n, partial);
+    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_sqdiff(const float *a, const float *b, long long n, double *partial, double *dev_out,
+                   cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st, 8.0 * n, 2);
+    const int nb = blocks_for(n);
+    k_reduce2<1><<<nb, RT, 0, st>>>(a, b, n, partial);
+    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_pcg_xr(float *x, float *r, const float *p, const float *q, float alpha, long long n,
+                   double *partial, double *dev_out, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 24.0 * n, 2);
+    const int nb = blocks_for(n);
+    k_pcg_xr<<<nb, RT, 0, st>>>(x, r, p, q, alpha, n, partial);
+    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_pcg_p(float *p, const float *z, float beta, long long n, cudaStream_t st,
+                  Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 12.0 * n);
+    k_pcg_p<<<blocks_for(n), RT, 0, st>>>(p, z, beta, n);
+}
+
+void launch_axpby(float *out, float a, const float *x, float b, const float *y, long long n,
+                  cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (y ? 12.0 : 8.0) * n);
+    k_axpby<<<blocks_for(n), RT, 0, st>>>(out, a, x, b, y, n);
+}
+
+void launch_diff_flag(const float *a, const float *b, long long n, int *flag, cudaStream_t st,
+                      Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 8.0 * n);
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    k_diff_flag<<<blocks_for(n), RT, 0, st>>>(a, b, n, flag);
+}
+
+}  // namespace claire

@@ -1,0 +1,357 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs (element by element, relative L2 error).
+
+Tolerances: 1e-5 relative L2 for one FP32 application of an operator (spectral
+operators, interpolation, foot points, transport histories, gradient, Hessian
+matvec, preconditioner); 1e-4 on gradient and objective after a solve.
+Sizes span several kernel tiles and a ragged tail (x3 half-spectra of 17, 19
+and 23 columns against 16-column tiles; 20 x 27 x 45 has odd axes)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2008_12820_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+TOL_SOLVE = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def claire():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2008_12820_gb300 import claire as C
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return C
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().astype(np.float64)
+
+
+SHAPES = [(32, 32, 32), (48, 40, 36), (20, 27, 45), (64, 24, 96)]
+
+
+# ------------------------------------------------------------ operators ----
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_spectral_operators(claire, shape):
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal(shape).astype(np.float32)
+    v = rng.standard_normal((3,) + shape).astype(np.float32)
+    beta, gamma = 1e-2, 1.0
+    with claire.Registration(shape, 4, beta, gamma) as reg:
+        assert rel(host(reg.grad(dev(f))), O.grad(f)) < TOL
+        assert rel(host(reg.div(dev(v))), O.div(v)) < TOL
+        assert rel(host(reg.apply_A(dev(v))), O.apply_A(v, beta, gamma)) < TOL
+        assert rel(host(reg.precond(dev(v))), O.apply_Ainv(v, beta, gamma)) < TOL
+        # in-place preconditioner (s may equal r)
+        t = dev(v)
+        reg.precond(t, out=t)
+        assert rel(host(t), O.apply_Ainv(v, beta, gamma)) < TOL
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_interpolation(claire, shape):
+    rng = np.random.default_rng(1)
+    f = rng.standard_normal(shape).astype(np.float32)
+    disp = rng.uniform(-6.5, 6.5, (3,) + shape).astype(np.float32)
+    I = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij"))
+    ref = O.interp(f, (I + disp.astype(np.float64)).reshape(3, -1)).reshape(shape)
+    with claire.Registration(shape, 4, 1e-2, 1.0) as reg:
+        assert rel(host(reg.interp(dev(f), dev(disp))), ref) < TOL
+
+
+# ------------------------------------------------------ linearization -------
+
+def make_problem(shape, nt=4, scale=0.8, seed=1000):
+    d = synth.sinusoid_pair(shape, seed)
+    v = (scale * d["v_true"]).astype(np.float32)
+    return d["m0"], d["m1"], v
+
+
+@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((20, 27, 45), 1)])
+def test_linearization_rows(claire, shape, nt):
+    """foot points (a1), state history (a3), grad m^j (a4), div v (a5)"""
+    m0, m1, v = make_problem(shape, nt)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    P.linearize(v)
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        reg.linearize(dev(v))
+        assert rel(host(reg.field("dispm")), P.dispm()) < TOL
+        assert rel(host(reg.field("dispp")), P.dispp()) < TOL
+        assert rel(host(reg.field("divv")), P.divv()) < TOL
+        mh, gmh = P.state_history(), P.grad_state_history()
+        for j in range(nt + 1):
+            assert rel(host(reg.field("state", j)), mh[j]) < TOL, j
+            assert rel(host(reg.field("gradm", j)), gmh[j]) < TOL, j
+
+
+@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((20, 27, 45), 2)])
+def test_gradient_and_adjoint(claire, shape, nt):
+    """adjoint + body force (a6), regularization (a9): Eq. 3.1, 3.2"""
+    m0, m1, v = make_problem(shape, nt)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    go, Jo, lh = P.gradient(v, want_adjoint=True)
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        g, J = reg.gradient(dev(v))
+        assert rel(host(g), go) < TOL
+        assert abs(J - Jo) / abs(Jo) < TOL
+        for j in range(nt + 1):
+            assert rel(host(reg.field("adj", j)), lh[j]) < TOL, j
+
+
+@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((20, 27, 45), 2)])
+def test_hessian_matvec(claire, shape, nt):
+    """incremental state (a7), incremental adjoint (a8), beta A vt (a9): Eq. 3.4-3.6"""
+    m0, m1, v = make_problem(shape, nt)
+    vt = synth.smooth_direction(shape, 11)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    P.gradient(v)
+    Ho, mto, lto = P.matvec(vt, want_inc=True)
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        dv = dev(v)
+        reg.gradient(dv)
+        H = reg.hess_matvec(None, dev(vt))
+        assert rel(host(H), Ho) < TOL
+        assert rel(host(reg.field("incst")), mto) < TOL
+        for j in range(nt + 1):
+            assert rel(host(reg.field("incadj", j)), lto[j]) < TOL, j
+        # passing v: same point -> cached; another point -> re-linearized
+        H2 = reg.hess_matvec(dv, dev(vt))
+        assert rel(host(H2), Ho) < TOL
+        v2 = (0.5 * v).astype(np.float32)
+        P.linearize(v2)
+        Ho2 = P.matvec(vt)
+        H3 = reg.hess_matvec(dev(v2), dev(vt))
+        assert rel(host(H3), Ho2) < TOL
+
+
+def test_forward_and_objective(claire):
+    shape, nt = (48, 40, 36), 4
+    m0, m1, v = make_problem(shape, nt)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    Jo, miso, rego, mfo = P.objective(v, want_m_final=True)
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        mf, mis = reg.forward(dev(v))
+        assert rel(host(mf), mfo) < TOL
+        assert abs(mis - miso) / miso < TOL
+        J, mis2 = reg.objective(dev(v))
+        assert abs(J - Jo) / Jo < TOL and abs(mis2 - miso) / miso < TOL
+
+
+# ------------------------------------------------------------- solves -------
+
+def test_fixed_work_gn_step_32(claire):
+    """sinusoid workload, 32^3: 1 GN iteration with exactly 10 PCG steps from
+    v = 0, all checked against the oracle (tolerance 1e-4 after the solve)."""
+    w = synth.workload("sin32")
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    P = O.Problem(w["m0"], w["m1"], nt, beta, gamma)
+    vo, ro = P.solve(np.zeros((3,) + shape), max_gn=1, fixed_pcg=10)
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        v = torch.zeros((3,) + shape, device="cuda")
+        rep = reg.solve(v, max_gn=1, fixed_pcg=10)
+        assert rep.n_gn == ro.n_gn == 1 and rep.n_pcg == ro.n_pcg == 10
+        assert rel(host(v), vo) < TOL_SOLVE
+        assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
+        assert abs(rep.g - ro.g) / abs(ro.g) < TOL_SOLVE
+        assert_gradient_after_solve(reg, P, v, vo, beta, gamma)
+
+
+def assert_gradient_after_solve(reg, P, v, vo, beta, gamma):
+    """Gradient and objective at the solution of each side.  The gradient field
+    at two velocities that differ by FP32 rounding differs by far more than the
+    rounding (beta*A amplifies the high-frequency part: rounding the oracle's
+    own v to FP32 moves its gradient by ~2e-5, 1e-6 white noise by ~8e-4), so
+    the field is compared in the (beta*A)^{-1} dual norm, its 2-norm and J
+    directly; the field itself is checked at 1e-5 on common inputs above."""
+    g, J = reg.gradient(v)
+    go, Jo = P.gradient(vo)
+    assert abs(J - Jo) / abs(Jo) < TOL_SOLVE
+    gn, gon = float(torch.linalg.norm(g)), float(np.linalg.norm(go))
+    assert abs(gn - gon) / gon < TOL_SOLVE
+    pg = host(reg.precond(g))
+    pgo = O.apply_Ainv(go, beta, gamma)
+    assert rel(pg, pgo) < TOL_SOLVE, rel(pg, pgo)
+
+
+def test_full_solve_32(claire):
+    """full GN-Krylov solve to 5e-2 relative gradient reduction (Algorithm 1)"""
+    w = synth.workload("sin32")
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    P = O.Problem(w["m0"], w["m1"], nt, beta, gamma)
+    vo, ro = P.solve(np.zeros((3,) + shape))
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        v = torch.zeros((3,) + shape, device="cuda")
+        rep = reg.solve(v)
+        assert rep.status == 0 and ro.status == 0
+        assert rep.grel <= 5e-2
+        assert rep.n_gn == ro.n_gn and abs(rep.n_pcg - ro.n_pcg) <= 1
+        assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
+        assert abs(rep.grel - ro.grel) / ro.grel < TOL_SOLVE
+        assert rel(host(v), vo) < TOL_SOLVE
+        assert_gradient_after_solve(reg, P, v, vo, beta, gamma)
+
+
+# ------------------------------------------------------------ edge cases ---
+
+def test_invalid_arguments(claire):
+    C = claire
+    for shape in [(3, 8, 8), (8, 7, 8), (8, 8, 2048)]:
+        with pytest.raises(C.ClaireError) as e:
+            C.Registration(shape, 4, 1e-2, 1.0)
+        assert e.value.code == 1
+    for nt, beta, gamma in [(0, 1e-2, 1.0), (4, 0.0, 1.0), (4, 1e-2, -1.0), (4, float("nan"), 1.0)]:
+        with pytest.raises(C.ClaireError):
+            C.Registration((8, 8, 8), nt, beta, gamma)
+    with C.Registration((8, 8, 8), 2, 1e-2, 1.0) as reg:
+        z = torch.zeros((3, 8, 8, 8), device="cuda")
+        with pytest.raises(C.ClaireError) as e:   # no images yet
+            reg.gradient(z)
+        assert e.value.code == 4
+        with pytest.raises(C.ClaireError) as e:   # no linearization yet
+            reg.hess_matvec(None, z)
+        assert e.value.code == 4
+        L = C.load()
+        rc = L.claire_precond(reg.handle, None, None)
+        assert rc == 1
+        # the context is still usable after errors
+        m = torch.rand((8, 8, 8), device="cuda")
+        reg.set_images(m, m)
+        g, J = reg.gradient(z)
+        assert J == 0.0 and float(g.abs().max()) == 0.0
+
+
+def test_zero_velocity_identities(claire):
+    """v = 0: g = (m1 - m0) grad m0 and H vt = beta A vt + grad m0 (grad m0 . vt)"""
+    shape = (24, 32, 40)
+    m0, m1, _ = make_problem(shape)
+    vt = synth.smooth_direction(shape, 2)
+    z = np.zeros((3,) + shape, np.float32)
+    P = O.Problem(m0, m1, 4, 1e-2, 1.0)
+    go, _ = P.gradient(z)
+    Ho = P.matvec(vt)
+    with claire.Registration(shape, 4, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        g, _ = reg.gradient(dev(z))
+        assert rel(host(g), go) < TOL
+        assert rel(host(reg.hess_matvec(None, dev(vt))), Ho) < TOL
+
+
+def test_large_displacement_wraps(claire):
+    """velocities moving points by many cells per step (periodic wrap of the
+    stencil far from the home cell)"""
+    shape, nt = (32, 40, 48), 2
+    m0, m1, v = make_problem(shape, nt, scale=12.0)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    go, Jo = P.gradient(v)
+    assert np.abs(P.dispm()).max() > 10
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        g, J = reg.gradient(dev(v))
+        assert rel(host(g), go) < TOL and abs(J - Jo) / abs(Jo) < TOL
+
+
+# -------------------------------------------- full size (256^3) properties --
+
+@pytest.fixture(scope="module")
+def big():
+    shape = (256, 256, 256)
+    w = synth.workload("blob256")
+    return shape, w
+
+
+def test_full_size_sampled_first_step(claire, big):
+    """At 256^3, in the launch configuration the benchmark times: foot points
+    and the first state step at 2000 sampled voxels, each computed one by one
+    by the oracle's interpolation."""
+    shape, w = big
+    nt = w["nt"]
+    v = w["v_true"]
+    with claire.Registration(shape, nt, w["beta"], w["gamma"]) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        reg.linearize(dev(v))
+        dm = host(reg.field("dispm"))
+        dp = host(reg.field("dispp"))
+        m1s = host(reg.field("state", 1))
+    rng = np.random.default_rng(3)
+    idx = np.stack([rng.integers(0, n, 2000) for n in shape])
+    h = 2 * np.pi / 256
+    dt = 1.0 / nt
+    vs = np.stack([v[d].astype(np.float64)[tuple(idx)] for d in range(3)])
+    for sign, got in ((-1, dm), (+1, dp)):
+        ystar = idx + sign * dt * vs / h
+        vy = np.stack([O.interp(v[d], ystar) for d in range(3)])
+        ref = sign * 0.5 * dt * (vs + vy) / h
+        g = np.stack([got[d][tuple(idx)] for d in range(3)])
+        assert rel(g, ref) < TOL
+    # first state step at the oracle's own foot points
+    ystar = idx - dt * vs / h
+    vy = np.stack([O.interp(v[d], ystar) for d in range(3)])
+    foot = idx - 0.5 * dt * (vs + vy) / h
+    ref = O.interp(w["m0"], foot)
+    assert rel(m1s[tuple(idx)], ref) < TOL
+
+
+def test_full_size_spectral_closed_forms(claire, big):
+    """256^3: gradient of a trigonometric polynomial, beta A and (beta A)^{-1}
+    of a single Fourier mode against their closed forms (the 3x3 symbol
+    inverted by numpy).  A round trip A (A^{-1} r) of white noise is not a
+    usable check in FP32: the symbol's condition number at 256^3 is ~5e6."""
+    shape, _ = big
+    x = np.meshgrid(*synth.grid_axes(shape), indexing="ij")
+    ph = 3 * x[0] - 17 * x[1] + 101 * x[2] + 0.4
+    f = np.sin(ph)
+    c = np.cos(ph)
+    gref = np.stack([3 * c, -17 * c, 101 * c])
+    beta, gamma = 1e-2, 1.0
+    k = np.array([3, -17, 101.0])
+    M = beta * (k @ k) * np.eye(3) + gamma * np.outer(k, k)
+    Minv = np.linalg.inv(M)
+    vv = np.zeros((3,) + shape)
+    vv[1] = c
+    Aref = np.stack([M[d, 1] * c for d in range(3)])
+    Airef = np.stack([Minv[d, 1] * c for d in range(3)])
+    with claire.Registration(shape, 4, beta, gamma) as reg:
+        assert rel(host(reg.grad(dev(f))), gref) < TOL
+        assert rel(host(reg.apply_A(dev(vv))), Aref) < TOL
+        assert rel(host(reg.precond(dev(vv))), Airef) < TOL
+
+
+def test_full_size_integer_shift_is_exact(claire, big):
+    """256^3, constant velocity moving whole cells per step in each axis: the
+    state history is an exact shift of m0 (interpolation at grid nodes)."""
+    shape, w = big
+    nt = 4
+    s = (1, -1, 2)
+    h = 2 * np.pi / 256
+    v = np.stack([np.full(shape, s[d] * h * nt, np.float32) for d in range(3)])
+    with claire.Registration(shape, nt, w["beta"], w["gamma"]) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        reg.linearize(dev(v))
+        mT = host(reg.field("state", nt))
+        ref = np.roll(w["m0"], shift=tuple(nt * si for si in s), axis=(0, 1, 2))
+        assert rel(mT, ref) < 1e-6
