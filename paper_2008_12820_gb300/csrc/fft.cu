@@ -83,6 +83,55 @@ template <> __device__ __forceinline__ void dft<5>(float2 *a, float s) {
     a[3] = csub(b2, e2);
 }
 
+template <> __device__ __forceinline__ void dft<8>(float2 *a, float s) {
+    const float h = 0.70710678118654752440f;  // cos(pi/4)
+    float2 e[4] = {a[0], a[2], a[4], a[6]};
+    float2 o[4] = {a[1], a[3], a[5], a[7]};
+    dft<4>(e, s);
+    dft<4>(o, s);
+    // o_q *= exp(s 2 pi i q / 8)
+    o[1] = cmul(o[1], make_float2(h, s * h));
+    o[2] = mul_si(o[2], s);
+    o[3] = cmul(o[3], make_float2(-h, s * h));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        a[q] = cadd(e[q], o[q]);
+        a[q + 4] = csub(e[q], o[q]);
+    }
+}
+
+// 16 = 4 x 4: DFT-4 over r2 for each r1, twiddle exp(s 2 pi i r1 q1 / 16),
+// DFT-4 over r1 for each q1; output index q1 + 4 q2
+template <> __device__ __forceinline__ void dft<16>(float2 *a, float s) {
+    const float c1 = 0.92387953251128675613f;  // cos(pi/8)
+    const float s1 = 0.38268343236508977173f;  // sin(pi/8)
+    const float h = 0.70710678118654752440f;
+    float2 y[4][4];
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) {
+        float2 t[4] = {a[r1], a[r1 + 4], a[r1 + 8], a[r1 + 12]};
+        dft<4>(t, s);
+#pragma unroll
+        for (int q1 = 0; q1 < 4; ++q1) y[r1][q1] = t[q1];
+    }
+    y[1][1] = cmul(y[1][1], make_float2(c1, s * s1));   // e = 1
+    y[1][2] = cmul(y[1][2], make_float2(h, s * h));     // e = 2
+    y[1][3] = cmul(y[1][3], make_float2(s1, s * c1));   // e = 3
+    y[2][1] = cmul(y[2][1], make_float2(h, s * h));     // e = 2
+    y[2][2] = mul_si(y[2][2], s);                       // e = 4
+    y[2][3] = cmul(y[2][3], make_float2(-h, s * h));    // e = 6
+    y[3][1] = cmul(y[3][1], make_float2(s1, s * c1));   // e = 3
+    y[3][2] = cmul(y[3][2], make_float2(-h, s * h));    // e = 6
+    y[3][3] = cmul(y[3][3], make_float2(-c1, -s * s1)); // e = 9
+#pragma unroll
+    for (int q1 = 0; q1 < 4; ++q1) {
+        float2 t[4] = {y[0][q1], y[1][q1], y[2][q1], y[3][q1]};
+        dft<4>(t, s);
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) a[q1 + 4 * q2] = t[q2];
+    }
+}
+
 // One Stockham stage of radix R over L lines stored as buf[e * ls + l]
 // (e = element index, l = line).  Ns = product of the earlier radices.
 template <int R, int L>
@@ -137,25 +186,109 @@ __device__ float2 *fft_lines(float2 *A, float2 *B, const FftPlan &p, int ls, flo
     return A;
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time plans for the common grid sizes: radix 16 while it divides the
+// power-of-two part, then one 8, 4 or 2, then 3s, then 5s.  With the length,
+// radices and strides known, every index division folds into shifts or
+// multiplications and the loops unroll; radix 8 and 16 keep more of the
+// transform in registers (fewer shared-memory passes and barriers).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pow2_part(int n) {
+    int p = 1;
+    while (n % 2 == 0) { n /= 2; p *= 2; }
+    return p;
+}
+__host__ __device__ constexpr int radix_at(int n, int s) {
+    int p2 = pow2_part(n), rest = n / p2, st = 0;
+    while (p2 >= 16) { if (st == s) return 16; p2 /= 16; ++st; }
+    if (p2 > 1) { if (st == s) return p2; ++st; }
+    while (rest % 3 == 0) { if (st == s) return 3; rest /= 3; ++st; }
+    while (rest % 5 == 0) { if (st == s) return 5; rest /= 5; ++st; }
+    return 0;
+}
+__host__ __device__ constexpr int num_stages(int n) {
+    int s = 0;
+    while (radix_at(n, s) != 0) ++s;
+    return s;
+}
+__host__ __device__ constexpr int ns_before(int n, int s) {
+    int p = 1;
+    for (int i = 0; i < s; ++i) p *= radix_at(n, i);
+    return p;
+}
+
+template <int N, int R, int NS, int L>
+__device__ __forceinline__ void stage_ct(const float2 *__restrict__ A, float2 *__restrict__ B,
+                                         int ls, const float2 *__restrict__ tw, float s) {
+    constexpr int NB = N / R, WORK = NB * L, TSTRIDE = N / (NS * R);
+#pragma unroll 2
+    for (int t = threadIdx.x; t < WORK; t += kThreads) {
+        const int l = t % L;
+        const int j = t / L;
+        const int k = j % NS;
+        float2 a[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[r] = A[(j + r * NB) * ls + l];
+        if (NS > 1 && k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(tw + r * k * TSTRIDE);
+                w.y *= -s;
+                a[r] = cmul(a[r], w);
+            }
+        }
+        dft<R>(a, s);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) B[(base + r * NS) * ls + l] = a[r];
+    }
+}
+
+template <int N, int L, int S = 0>
+__device__ __forceinline__ float2 *fft_ct(float2 *A, float2 *B, const float2 *__restrict__ tw,
+                                          int ls, float s) {
+    if constexpr (S == num_stages(N)) {
+        return A;
+    } else {
+        stage_ct<N, radix_at(N, S), ns_before(N, S), L>(A, B, ls, tw, s);
+        __syncthreads();
+        return fft_ct<N, L, S + 1>(B, A, tw, ls, s);
+    }
+}
+
+// N > 0: compile-time plan of that length; N == 0: the runtime plan p
+template <int N>
+struct Fft {
+    __device__ __forceinline__ static int size(const FftPlan &p) { return N > 0 ? N : p.n; }
+    template <int L>
+    __device__ __forceinline__ static float2 *run(float2 *A, float2 *B, const FftPlan &p, int ls,
+                                                  float s) {
+        if constexpr (N > 0) return fft_ct<N, L>(A, B, p.tw, ls, s);
+        else return fft_lines<L>(A, B, p, ls, s);
+    }
+};
+
 // ---------------------------------------------------------------- pass 1 ---
 // x3 forward real -> half spectrum.  Block: L complex lines = 2L real lines.
-template <int L>
+template <int N, int L>
 __global__ void __launch_bounds__(kThreads)
 k_r2c_x3(const float *__restrict__ in, float2 *__restrict__ out, long long nlines, FftPlan p,
          int h3, int p3) {
     extern __shared__ float2 sm[];
-    const int n = p.n, ls = L + 1;
+    const int n = Fft<N>::size(p), ls = L + 1;
     float2 *A = sm, *B = sm + n * ls;
     const long long line0 = (long long)blockIdx.x * 2 * L;
-    float *Af = reinterpret_cast<float *>(A);
-    for (int t = threadIdx.x; t < 2 * L * n; t += blockDim.x) {
-        const int rl = t / n, e = t - rl * n;
-        const long long line = line0 + rl;
-        const float val = line < nlines ? in[line * n + e] : 0.f;
-        Af[(e * ls + (rl >> 1)) * 2 + (rl & 1)] = val;
+    // real lines 2l and 2l+1 become the real and imaginary part of line l
+    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+        const int l = t / n, e = t - l * n;
+        const long long la = line0 + 2 * l;
+        const float re = la < nlines ? in[la * n + e] : 0.f;
+        const float im = la + 1 < nlines ? in[(la + 1) * n + e] : 0.f;
+        A[e * ls + l] = make_float2(re, im);
     }
     __syncthreads();
-    float2 *Rz = fft_lines<L>(A, B, p, ls, -1.f);
+    float2 *Rz = Fft<N>::template run<L>(A, B, p, ls, -1.f);
+    if (N > 0) h3 = N / 2 + 1;
     for (int t = threadIdx.x; t < L * h3; t += blockDim.x) {
         const int l = t / h3, k = t - l * h3;
         const float2 z = Rz[k * ls + l];
@@ -171,11 +304,11 @@ k_r2c_x3(const float *__restrict__ in, float2 *__restrict__ out, long long nline
 
 // ---------------------------------------------------------------- pass 2 ---
 // x2 complex transform in place.  Block: (k3 tile of TK, one (c, i1) plane).
-template <int TK>
+template <int N, int TK>
 __global__ void __launch_bounds__(kThreads)
 k_c2c_x2(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s) {
     extern __shared__ float2 sm[];
-    const int n = p.n;
+    const int n = Fft<N>::size(p);
     float2 *A = sm, *B = sm + n * TK;
     float2 *base = data + (long long)blockIdx.y * n * p3;
     const int k0 = blockIdx.x * TK;
@@ -184,7 +317,7 @@ k_c2c_x2(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s) {
         A[e * TK + l] = (k0 + l < h3) ? base[(long long)e * p3 + k0 + l] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2 *R = fft_lines<TK>(A, B, p, TK, s);
+    float2 *R = Fft<N>::template run<TK>(A, B, p, TK, s);
     for (int t = threadIdx.x; t < n * TK; t += blockDim.x) {
         const int e = t / TK, l = t - e * TK;
         if (k0 + l < h3) base[(long long)e * p3 + k0 + l] = R[e * TK + l];
@@ -199,7 +332,7 @@ __device__ __forceinline__ float wavenumber_d1(int i, int n) {
 // ---------------------------------------------------------------- pass 3 ---
 // x1 forward, multiplier, x1 inverse, in place.  Block: (k3 tile, k2 index).
 // Buffers: NB = max(nin, nout) component tiles of n1*TK plus one scratch.
-template <int TK, int OP>
+template <int N, int TK, int OP>
 __global__ void __launch_bounds__(kThreads)
 k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
          long long cstride, SpecParams sp) {
@@ -207,7 +340,7 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
     constexpr int NOUT = (OP == OP_DIV) ? 1 : 3;
     constexpr int NB = NIN > NOUT ? NIN : NOUT;
     extern __shared__ float2 sm[];
-    const int n1 = p1.n;
+    const int n1 = Fft<N>::size(p1);
     const int tile = n1 * TK;
     float2 *buf[NB];
     float2 *scratch = sm + NB * tile;
@@ -227,7 +360,7 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NIN; ++c) {
-        float2 *r = fft_lines<TK>(buf[c], scratch, p1, TK, -1.f);
+        float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, -1.f);
         if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
     }
     // multiplier at (k1, k2, k3)
@@ -282,7 +415,7 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < NOUT; ++c) {
-        float2 *r = fft_lines<TK>(buf[c], scratch, p1, TK, +1.f);
+        float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, +1.f);
         if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
     }
     for (int c = 0; c < NOUT; ++c) {
@@ -295,12 +428,12 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
 
 // ---------------------------------------------------------------- pass 5 ---
 // x3 inverse half spectrum -> real, two real lines per complex transform.
-template <int L, int EPI>
+template <int N, int L, int EPI>
 __global__ void __launch_bounds__(kThreads)
 k_c2r_x3(const float2 *__restrict__ in, float *__restrict__ out, const float *__restrict__ add,
          long long nlines, FftPlan p, int h3, int p3) {
     extern __shared__ float2 sm[];
-    const int n = p.n, ls = L + 1;
+    const int n = Fft<N>::size(p), ls = L + 1;
     float2 *A = sm, *B = sm + n * ls;
     const long long line0 = (long long)blockIdx.x * 2 * L;
     const bool even = (n & 1) == 0;
@@ -323,15 +456,20 @@ k_c2r_x3(const float2 *__restrict__ in, float *__restrict__ out, const float *__
         A[k * ls + l] = make_float2(a.x - b.y, a.y + b.x);
     }
     __syncthreads();
-    float2 *R = fft_lines<L>(A, B, p, ls, +1.f);
-    const float *Rf = reinterpret_cast<const float *>(R);
-    for (int t = threadIdx.x; t < 2 * L * n; t += blockDim.x) {
-        const int rl = t / n, e = t - rl * n;
-        const long long line = line0 + rl;
-        if (line < nlines) {
-            float val = Rf[(e * ls + (rl >> 1)) * 2 + (rl & 1)];
-            if (EPI == EPI_ADD) val += add[line * n + e];
-            out[line * n + e] = val;
+    float2 *R = Fft<N>::template run<L>(A, B, p, ls, +1.f);
+    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+        const int l = t / n, e = t - l * n;
+        const long long la = line0 + 2 * l;
+        const float2 z = R[e * ls + l];
+        if (la < nlines) {
+            float val = z.x;
+            if (EPI == EPI_ADD) val += add[la * n + e];
+            out[la * n + e] = val;
+        }
+        if (la + 1 < nlines) {
+            float val = z.y;
+            if (EPI == EPI_ADD) val += add[(la + 1) * n + e];
+            out[(la + 1) * n + e] = val;
         }
     }
 }
@@ -345,86 +483,158 @@ void set_smem(K kernel, size_t bytes) {
 }
 
 // lines per block of the x3 passes and column tile of the strided passes,
-// chosen so that a block's shared memory stays near or below ~110 KB
-int lines_x3(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
-int tile_x1(int n, int nbuf) {
-    // nbuf buffers + scratch of n*TK float2
-    for (int tk = 16; tk >= 4; tk /= 2)
-        if ((size_t)(nbuf + 1) * n * tk * sizeof(float2) <= 112 * 1024) return tk;
-    return 4;
+// chosen so that a block's shared memory stays near or below ~112 KB
+constexpr int lines_x3(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
+constexpr int tile_cols(int n, int nbuf) {
+    // nbuf data buffers + one scratch of n*TK float2
+    return (size_t)(nbuf + 1) * n * 16 * sizeof(float2) <= 112 * 1024 ? 16
+         : (size_t)(nbuf + 1) * n * 8 * sizeof(float2) <= 112 * 1024 ? 8 : 4;
+}
+
+// the axis lengths with a compile-time plan; other valid lengths use the
+// runtime plan (N = 0)
+#define CLAIRE_CT_SIZES(X) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(384) X(512) X(768)
+
+template <int N, int L>
+void r2c_l(const Dims &d, const FftPlan &p, const float *in, float2 *out, long long nlines,
+           cudaStream_t st) {
+    const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
+    const long long blocks = (nlines + 2 * L - 1) / (2 * L);
+    set_smem(k_r2c_x3<N, L>, smem);
+    k_r2c_x3<N, L><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3);
+}
+
+template <int N>
+void r2c_n(const Dims &d, const FftPlan &p, const float *in, float2 *out, int ncomp,
+           cudaStream_t st) {
+    const long long nlines = (long long)ncomp * d.n1 * d.n2;
+    if constexpr (N > 0) {
+        r2c_l<N, lines_x3(N)>(d, p, in, out, nlines, st);
+    } else {
+        switch (lines_x3(d.n3)) {
+            case 16: r2c_l<N, 16>(d, p, in, out, nlines, st); break;
+            case 8: r2c_l<N, 8>(d, p, in, out, nlines, st); break;
+            default: r2c_l<N, 4>(d, p, in, out, nlines, st); break;
+        }
+    }
 }
 
 void r2c_x3(const Dims &d, const FftPlan &p, const float *in, float2 *out, int ncomp,
             cudaStream_t st) {
-    const long long nlines = (long long)ncomp * d.n1 * d.n2;
-    const int L = lines_x3(d.n3);
-    const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
-    const long long blocks = (nlines + 2 * L - 1) / (2 * L);
-#define R2C_CASE(LL)                                                                     \
-    case LL:                                                                             \
-        set_smem(k_r2c_x3<LL>, smem);                                                    \
-        k_r2c_x3<LL><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3); \
-        break;
-    switch (L) { R2C_CASE(16) R2C_CASE(8) R2C_CASE(4) }
-#undef R2C_CASE
+    switch (d.n3) {
+#define CASE_N(NN) case NN: r2c_n<NN>(d, p, in, out, ncomp, st); return;
+        CLAIRE_CT_SIZES(CASE_N)
+#undef CASE_N
+        default: r2c_n<0>(d, p, in, out, ncomp, st);
+    }
+}
+
+template <int N, int TK>
+void c2c_t(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)d.n2 * TK * sizeof(float2);
+    dim3 grid((d.h3 + TK - 1) / TK, ncomp * d.n1);
+    set_smem(k_c2c_x2<N, TK>, smem);
+    k_c2c_x2<N, TK><<<grid, kThreads, smem, st>>>(data, p, d.h3, d.p3, s);
+}
+
+template <int N>
+void c2c_n(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
+    if constexpr (N > 0) {
+        c2c_t<N, tile_cols(N, 1)>(d, p, data, ncomp, s, st);
+    } else {
+        switch (tile_cols(d.n2, 1)) {
+            case 16: c2c_t<N, 16>(d, p, data, ncomp, s, st); break;
+            case 8: c2c_t<N, 8>(d, p, data, ncomp, s, st); break;
+            default: c2c_t<N, 4>(d, p, data, ncomp, s, st); break;
+        }
+    }
 }
 
 void c2c_x2(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
-    const int TK = tile_x1(d.n2, 1);
-    const size_t smem = 2 * (size_t)d.n2 * TK * sizeof(float2);
-    dim3 grid((d.h3 + TK - 1) / TK, ncomp * d.n1);
-#define C2C_CASE(T)                                                            \
-    case T:                                                                    \
-        set_smem(k_c2c_x2<T>, smem);                                           \
-        k_c2c_x2<T><<<grid, kThreads, smem, st>>>(data, p, d.h3, d.p3, s);     \
-        break;
-    switch (TK) { C2C_CASE(16) C2C_CASE(8) C2C_CASE(4) }
-#undef C2C_CASE
+    switch (d.n2) {
+#define CASE_N(NN) case NN: c2c_n<NN>(d, p, data, ncomp, s, st); return;
+        CLAIRE_CT_SIZES(CASE_N)
+#undef CASE_N
+        default: c2c_n<0>(d, p, data, ncomp, s, st);
+    }
+}
+
+template <int N, int TK, int OP>
+void mul_t(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
+    constexpr int NIN = (OP == OP_GRAD) ? 1 : 3;
+    constexpr int NOUT = (OP == OP_DIV) ? 1 : 3;
+    constexpr int NB = NIN > NOUT ? NIN : NOUT;
+    const size_t smem = (size_t)(NB + 1) * d.n1 * TK * sizeof(float2);
+    const long long cstride = (long long)d.n1 * d.n2 * d.p3;
+    dim3 grid((d.h3 + TK - 1) / TK, d.n2);
+    set_smem(k_mul_x1<N, TK, OP>, smem);
+    k_mul_x1<N, TK, OP><<<grid, kThreads, smem, st>>>(data, p, d.n2, d.n3, d.h3, d.p3, cstride, sp);
+}
+
+template <int N, int OP>
+void mul_n(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
+    constexpr int NB = 3;  // every operator keeps three component tiles
+    if constexpr (N > 0) {
+        mul_t<N, tile_cols(N, NB), OP>(d, p, data, sp, st);
+    } else {
+        switch (tile_cols(d.n1, NB)) {
+            case 16: mul_t<N, 16, OP>(d, p, data, sp, st); break;
+            case 8: mul_t<N, 8, OP>(d, p, data, sp, st); break;
+            default: mul_t<N, 4, OP>(d, p, data, sp, st); break;
+        }
+    }
 }
 
 template <int OP>
 void mul_x1_op(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp,
                cudaStream_t st) {
-    constexpr int NIN = (OP == OP_GRAD) ? 1 : 3;
-    constexpr int NOUT = (OP == OP_DIV) ? 1 : 3;
-    constexpr int NB = NIN > NOUT ? NIN : NOUT;
-    const int TK = tile_x1(d.n1, NB);
-    const size_t smem = (size_t)(NB + 1) * d.n1 * TK * sizeof(float2);
-    const long long cstride = (long long)d.n1 * d.n2 * d.p3;
-    dim3 grid((d.h3 + TK - 1) / TK, d.n2);
-#define MUL_CASE(T)                                                                          \
-    case T:                                                                                  \
-        set_smem(k_mul_x1<T, OP>, smem);                                                     \
-        k_mul_x1<T, OP><<<grid, kThreads, smem, st>>>(data, p, d.n2, d.n3, d.h3, d.p3,       \
-                                                       cstride, sp);                          \
-        break;
-    switch (TK) { MUL_CASE(16) MUL_CASE(8) MUL_CASE(4) }
-#undef MUL_CASE
+    switch (d.n1) {
+#define CASE_N(NN) case NN: mul_n<NN, OP>(d, p, data, sp, st); return;
+        CLAIRE_CT_SIZES(CASE_N)
+#undef CASE_N
+        default: mul_n<0, OP>(d, p, data, sp, st);
+    }
+}
+
+template <int N, int L>
+void c2r_l(const Dims &d, const FftPlan &p, const float2 *in, float *out, const float *add,
+           long long nlines, cudaStream_t st) {
+    const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
+    const long long blocks = (nlines + 2 * L - 1) / (2 * L);
+    if (add) {
+        set_smem(k_c2r_x3<N, L, EPI_ADD>, smem);
+        k_c2r_x3<N, L, EPI_ADD><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines, p,
+                                                                          d.h3, d.p3);
+    } else {
+        set_smem(k_c2r_x3<N, L, EPI_STORE>, smem);
+        k_c2r_x3<N, L, EPI_STORE><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines,
+                                                                            p, d.h3, d.p3);
+    }
+}
+
+template <int N>
+void c2r_n(const Dims &d, const FftPlan &p, const float2 *in, float *out, const float *add,
+           int ncomp, cudaStream_t st) {
+    const long long nlines = (long long)ncomp * d.n1 * d.n2;
+    if constexpr (N > 0) {
+        c2r_l<N, lines_x3(N)>(d, p, in, out, add, nlines, st);
+    } else {
+        switch (lines_x3(d.n3)) {
+            case 16: c2r_l<N, 16>(d, p, in, out, add, nlines, st); break;
+            case 8: c2r_l<N, 8>(d, p, in, out, add, nlines, st); break;
+            default: c2r_l<N, 4>(d, p, in, out, add, nlines, st); break;
+        }
+    }
 }
 
 void c2r_x3(const Dims &d, const FftPlan &p, const float2 *in, float *out, const float *add,
             int ncomp, cudaStream_t st) {
-    const long long nlines = (long long)ncomp * d.n1 * d.n2;
-    const int L = lines_x3(d.n3);
-    const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
-    const long long blocks = (nlines + 2 * L - 1) / (2 * L);
-#define C2R_CASE(LL, E)                                                                    \
-    set_smem(k_c2r_x3<LL, E>, smem);                                                       \
-    k_c2r_x3<LL, E><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines, p, d.h3, d.p3);
-    if (add) {
-        switch (L) {
-            case 16: C2R_CASE(16, EPI_ADD) break;
-            case 8: C2R_CASE(8, EPI_ADD) break;
-            default: C2R_CASE(4, EPI_ADD) break;
-        }
-    } else {
-        switch (L) {
-            case 16: C2R_CASE(16, EPI_STORE) break;
-            case 8: C2R_CASE(8, EPI_STORE) break;
-            default: C2R_CASE(4, EPI_STORE) break;
-        }
+    switch (d.n3) {
+#define CASE_N(NN) case NN: c2r_n<NN>(d, p, in, out, add, ncomp, st); return;
+        CLAIRE_CT_SIZES(CASE_N)
+#undef CASE_N
+        default: c2r_n<0>(d, p, in, out, add, ncomp, st);
     }
-#undef C2R_CASE
 }
 
 }  // namespace

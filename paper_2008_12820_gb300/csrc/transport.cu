@@ -14,9 +14,9 @@
 // integer part and the interpolation weight of each axis come from a small
 // number (no loss of precision at large grid indices).
 //
-// One thread computes one output voxel; a block covers 32 consecutive x3
-// points of 8 consecutive x2 rows, so the 64 gathers of a warp fall on a few
-// cache lines of the same rows (the displacement field is smooth).
+// The time-step kernels stage the source field in shared-memory halo boxes
+// (k_sl_tiled); the foot-point kernel gathers v from global memory, one
+// thread per voxel, a block covering 32 consecutive x3 points of 8 x2 rows.
 #include <cuda_runtime.h>
 
 #include "claire_internal.cuh"
@@ -39,8 +39,14 @@ __device__ __forceinline__ void lagrange4(float t, float w[4]) {
 }
 
 __device__ __forceinline__ int wrap_index(int i, int n) {
-    i %= n;
-    return i < 0 ? i + n : i;
+    // one period off is the common case; the modulo handles the rest
+    if (i < 0) i += n;
+    else if (i >= n) i -= n;
+    if ((unsigned)i >= (unsigned)n) {
+        i %= n;
+        if (i < 0) i += n;
+    }
+    return i;
 }
 
 // stencil of one axis: 4 wrapped node offsets (times the axis stride) and weights
@@ -137,62 +143,225 @@ k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__re
     }
 }
 
-// plain interpolation of f at x + disp
-__global__ void __launch_bounds__(BX * BY)
-k_interp(const float *__restrict__ f, const float *__restrict__ disp, float *__restrict__ out,
-         Dims d) {
-    Pt p = this_point(d);
-    if (!p.ok) return;
-    const long long N = d.N;
-    out[p.id] = interp_at(f, d, p, disp[p.id], disp[N + p.id], disp[2 * N + p.id]);
+// ---------------------------------------------------------------------------
+// Shared-memory tiled semi-Lagrangian step.
+// A block owns T3 x T2 x T1 = 32 x 8 x 4 output voxels (a warp per x2 row,
+// every thread 4 voxels along x1).  Per-step displacements are a few cells, so
+// the 4x4x4 stencils of a block cover a small box of the source field: the
+// block takes the minimum and maximum floor of its displacements per axis,
+// stages that box in shared memory once (coalesced rows, periodic wrap) and
+// reads the 64 taps of every output from there with immediate offsets.  A
+// block whose box exceeds the capacity (large displacements) gathers from
+// global memory instead; the choice is uniform over the block.
+// ---------------------------------------------------------------------------
+constexpr int T3 = 32, T2 = 8, T1 = 4;
+constexpr int BOX_CAP = 8192;  // floats of shared memory for the box
+
+enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3 };
+
+struct SlArgs {
+    const float *src;   // field gathered at the foot points
+    const float *disp;  // foot point minus grid point, index units, [3][N]
+    float *dst;
+    const float *aux;   // SL_ADJ: c;  SL_ADJFAC: div v on the grid
+    const float *vt;    // SL_INCSTATE: vt [3][N]
+    const float *gm;    // SL_INCSTATE: grad m^{j+1} [3][N]
+    float dt;
+};
+
+__device__ __forceinline__ int floor_int(float x) {
+    return (int)fminf(fmaxf(floorf(x), -1.0e6f), 1.0e6f);
 }
 
-// adjoint source factor along the forward characteristic (Heun for
-// dl/ds = l div v):  c = 1 + dt/2 (d(X+) + d(x)) + dt^2/2 d(x) d(X+)
-__global__ void __launch_bounds__(BX * BY)
-k_adjoint_factor(const float *__restrict__ divv, const float *__restrict__ dispp,
-                 float *__restrict__ cfac, Dims d, float dt) {
-    Pt p = this_point(d);
-    if (!p.ok) return;
+template <int MODE>
+__global__ void __launch_bounds__(T3 * T2)
+k_sl_tiled(SlArgs a, Dims d) {
+    extern __shared__ float box[];
+    __shared__ int fmin_s[3], fmax_s[3];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i3 = blockIdx.x * T3 + tx;
+    const int i2 = blockIdx.y * T2 + ty;
+    const int i1b = blockIdx.z * T1;
+    const bool ok23 = (i3 < d.n3) && (i2 < d.n2);
     const long long N = d.N;
-    const float dx = divv[p.id];
-    const float dX = interp_at(divv, d, p, dispp[p.id], dispp[N + p.id], dispp[2 * N + p.id]);
-    cfac[p.id] = 1.f + 0.5f * dt * (dX + dx) + 0.5f * dt * dt * dx * dX;
+    if (ty == 0 && tx < 3) {
+        fmin_s[tx] = 0x7fffffff;
+        fmax_s[tx] = -0x7fffffff;
+    }
+    float dd[T1][3];
+    int mn0 = 0x7fffffff, mn1 = 0x7fffffff, mn2 = 0x7fffffff;
+    int mx0 = -0x7fffffff, mx1 = -0x7fffffff, mx2 = -0x7fffffff;
+#pragma unroll
+    for (int t = 0; t < T1; ++t) {
+        const int i1 = i1b + t;
+        if (ok23 && i1 < d.n1) {
+            const long long id = ((long long)i1 * d.n2 + i2) * d.n3 + i3;
+            dd[t][0] = a.disp[id];
+            dd[t][1] = a.disp[N + id];
+            dd[t][2] = a.disp[2 * N + id];
+            const int f0 = floor_int(dd[t][0]), f1 = floor_int(dd[t][1]), f2 = floor_int(dd[t][2]);
+            mn0 = min(mn0, f0); mx0 = max(mx0, f0);
+            mn1 = min(mn1, f1); mx1 = max(mx1, f1);
+            mn2 = min(mn2, f2); mx2 = max(mx2, f2);
+        } else {
+            dd[t][0] = dd[t][1] = dd[t][2] = 0.f;
+        }
+    }
+    __syncthreads();  // fmin_s / fmax_s initialized
+    mn0 = __reduce_min_sync(0xffffffffu, mn0); mx0 = __reduce_max_sync(0xffffffffu, mx0);
+    mn1 = __reduce_min_sync(0xffffffffu, mn1); mx1 = __reduce_max_sync(0xffffffffu, mx1);
+    mn2 = __reduce_min_sync(0xffffffffu, mn2); mx2 = __reduce_max_sync(0xffffffffu, mx2);
+    if (tx == 0) {
+        atomicMin(&fmin_s[0], mn0); atomicMax(&fmax_s[0], mx0);
+        atomicMin(&fmin_s[1], mn1); atomicMax(&fmax_s[1], mx1);
+        atomicMin(&fmin_s[2], mn2); atomicMax(&fmax_s[2], mx2);
+    }
+    __syncthreads();
+    // source box [lo, lo + S) per axis covering every stencil of the block
+    const int lo1 = i1b + fmin_s[0] - 1;
+    const int lo2 = blockIdx.y * T2 + fmin_s[1] - 1;
+    const int lo3 = blockIdx.x * T3 + fmin_s[2] - 1;
+    const long long S1l = (long long)T1 + 3 + fmax_s[0] - fmin_s[0];
+    const long long S2l = (long long)T2 + 3 + fmax_s[1] - fmin_s[1];
+    const long long S3l = (long long)T3 + 3 + fmax_s[2] - fmin_s[2];
+    const bool use_box = S1l * S2l * S3l <= BOX_CAP;
+    const int S2 = (int)S2l, S3 = (int)S3l;
+    if (use_box) {
+        const int rows = (int)(S1l * S2l);
+        for (int r = ty; r < rows; r += T2) {
+            const int z = r / S2, y = r - z * S2;
+            const int g1 = wrap_index(lo1 + z, d.n1), g2 = wrap_index(lo2 + y, d.n2);
+            const float *srow = a.src + ((long long)g1 * d.n2 + g2) * d.n3;
+            float *brow = box + r * S3;
+            for (int x = tx; x < S3; x += T3) brow[x] = __ldg(srow + wrap_index(lo3 + x, d.n3));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < T1; ++t) {
+        const int i1 = i1b + t;
+        if (!(ok23 && i1 < d.n1)) continue;
+        const long long id = ((long long)i1 * d.n2 + i2) * d.n3 + i3;
+        float val;
+        if (use_box) {
+            const float fl0 = floorf(dd[t][0]), fl1 = floorf(dd[t][1]), fl2 = floorf(dd[t][2]);
+            float w1[4], w2[4], w3[4];
+            lagrange4(dd[t][0] - fl0, w1);
+            lagrange4(dd[t][1] - fl1, w2);
+            lagrange4(dd[t][2] - fl2, w3);
+            const int b1 = i1 + (int)fl0 - 1 - lo1;
+            const int b2 = i2 + (int)fl1 - 1 - lo2;
+            const int b3 = i3 + (int)fl2 - 1 - lo3;
+            const float *p = box + (b1 * S2 + b2) * S3 + b3;
+            float acc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float s2 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float *q = p + (i * S2 + j) * S3;
+                    float s3 = w3[0] * q[0];
+                    s3 = fmaf(w3[1], q[1], s3);
+                    s3 = fmaf(w3[2], q[2], s3);
+                    s3 = fmaf(w3[3], q[3], s3);
+                    s2 = fmaf(w2[j], s3, s2);
+                }
+                acc = fmaf(w1[i], s2, acc);
+            }
+            val = acc;
+        } else {
+            Pt p;
+            p.i1 = i1; p.i2 = i2; p.i3 = i3;
+            val = interp_at(a.src, d, p, dd[t][0], dd[t][1], dd[t][2]);
+        }
+        if (MODE == SL_PLAIN) {
+            a.dst[id] = val;
+        } else if (MODE == SL_ADJ) {
+            a.dst[id] = a.aux[id] * val;
+        } else if (MODE == SL_ADJFAC) {
+            const float dx = a.aux[id];
+            a.dst[id] = 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val;
+        } else {
+            const float f = -(a.vt[id] * a.gm[id] + a.vt[N + id] * a.gm[N + id] +
+                              a.vt[2 * N + id] * a.gm[2 * N + id]);
+            a.dst[id] = fmaf(a.dt, f, val);
+        }
+    }
 }
 
-// state step: dst = src(X-)
-__global__ void __launch_bounds__(BX * BY)
-k_state_step(const float *__restrict__ src, const float *__restrict__ disp, float *__restrict__ dst,
-             Dims d) {
-    Pt p = this_point(d);
-    if (!p.ok) return;
-    const long long N = d.N;
-    dst[p.id] = interp_at(src, d, p, disp[p.id], disp[N + p.id], disp[2 * N + p.id]);
+// ---------------------------------------------------------------------------
+// Lean global-memory gather (one thread per voxel, L1-cached).  A voxel whose
+// 4x4x4 stencil does not cross the periodic boundary (most of them) forms one
+// base pointer and reads the 64 taps with row offsets plus immediate column
+// offsets; the few stencils that wrap take the per-axis wrapped path.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float gather_lean(const float *__restrict__ f, const Dims &d, int i1,
+                                             int i2, int i3, float d1, float d2, float d3) {
+    const float fl1 = floorf(d1), fl2 = floorf(d2), fl3 = floorf(d3);
+    float w1[4], w2[4], w3[4];
+    lagrange4(d1 - fl1, w1);
+    lagrange4(d2 - fl2, w2);
+    lagrange4(d3 - fl3, w3);
+    const int b1 = i1 + floor_int(d1) - 1, b2 = i2 + floor_int(d2) - 1, b3 = i3 + floor_int(d3) - 1;
+    const int s2 = d.n3, s1 = d.n2 * d.n3;
+    if ((unsigned)b1 <= (unsigned)(d.n1 - 4) && (unsigned)b2 <= (unsigned)(d.n2 - 4) &&
+        (unsigned)b3 <= (unsigned)(d.n3 - 4)) {
+        const float *p = f + ((long long)b1 * d.n2 + b2) * d.n3 + b3;
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float sa = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float *q = p + a * s1 + b * s2;
+                float s3 = w3[0] * __ldg(q);
+                s3 = fmaf(w3[1], __ldg(q + 1), s3);
+                s3 = fmaf(w3[2], __ldg(q + 2), s3);
+                s3 = fmaf(w3[3], __ldg(q + 3), s3);
+                sa = fmaf(w2[b], s3, sa);
+            }
+            acc = fmaf(w1[a], sa, acc);
+        }
+        return acc;
+    }
+    Axis4 a1, a2, a3;
+    axis_stencil(i1, d1, d.n1, s1, a1);
+    axis_stencil(i2, d2, d.n2, s2, a2);
+    axis_stencil(i3, d3, d.n3, 1, a3);
+    return gather64(f, a1, a2, a3);
 }
 
-// adjoint step: dst = c * src(X+)
+template <int MODE>
 __global__ void __launch_bounds__(BX * BY)
-k_adjoint_step(const float *__restrict__ src, const float *__restrict__ disp,
-               const float *__restrict__ cfac, float *__restrict__ dst, Dims d) {
-    Pt p = this_point(d);
-    if (!p.ok) return;
+k_sl_lean(SlArgs a, Dims d) {
+    const int i3 = blockIdx.x * BX + threadIdx.x;
+    const int i2 = blockIdx.y * BY + threadIdx.y;
+    const int i1 = blockIdx.z;
+    if (i3 >= d.n3 || i2 >= d.n2) return;
     const long long N = d.N;
-    const float val = interp_at(src, d, p, disp[p.id], disp[N + p.id], disp[2 * N + p.id]);
-    dst[p.id] = cfac[p.id] * val;
+    const long long id = ((long long)i1 * d.n2 + i2) * d.n3 + i3;
+    const float val = gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
+    if (MODE == SL_PLAIN) {
+        a.dst[id] = val;
+    } else if (MODE == SL_ADJ) {
+        a.dst[id] = a.aux[id] * val;
+    } else if (MODE == SL_ADJFAC) {
+        const float dx = a.aux[id];
+        a.dst[id] = 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val;
+    } else {
+        const float f = -(a.vt[id] * a.gm[id] + a.vt[N + id] * a.gm[N + id] +
+                          a.vt[2 * N + id] * a.gm[2 * N + id]);
+        a.dst[id] = fmaf(a.dt, f, val);
+    }
 }
 
-// incremental state step: dst = src(X-) + dt f^{j+1},  f = -vt . grad m^{j+1}
-__global__ void __launch_bounds__(BX * BY)
-k_incstate_step(const float *__restrict__ src, const float *__restrict__ disp,
-                const float *__restrict__ vt, const float *__restrict__ gm, float *__restrict__ dst,
-                Dims d, float dt) {
-    Pt p = this_point(d);
-    if (!p.ok) return;
-    const long long N = d.N;
-    const float val = interp_at(src, d, p, disp[p.id], disp[N + p.id], disp[2 * N + p.id]);
-    const float f = -(vt[p.id] * gm[p.id] + vt[N + p.id] * gm[N + p.id] +
-                      vt[2 * N + p.id] * gm[2 * N + p.id]);
-    dst[p.id] = fmaf(dt, f, val);
+inline dim3 grid_tiled(const Dims &d) {
+    return dim3((d.n3 + T3 - 1) / T3, (d.n2 + T2 - 1) / T2, (d.n1 + T1 - 1) / T1);
+}
+
+template <int MODE>
+void launch_tiled(const Dims &d, const SlArgs &a, cudaStream_t st) {
+    k_sl_lean<MODE><<<dim3((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1), dim3(BX, BY), 0, st>>>(a, d);
 }
 
 // ----------------------------------------------------------- pointwise ----
@@ -273,25 +442,29 @@ void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, floa
 void launch_interp(const Dims &d, const float *f, const float *disp, float *out, cudaStream_t st,
                    Profiler *prof, int kclass) {
     ProfScope ps(prof, kclass, st, 20.0 * d.N);
-    k_interp<<<grid3(d), dim3(BX, BY), 0, st>>>(f, disp, out, d);
+    SlArgs a{f, disp, out, nullptr, nullptr, nullptr, 0.f};
+    launch_tiled<SL_PLAIN>(d, a, st);
 }
 
 void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
                            float *cfac, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 20.0 * d.N);
-    k_adjoint_factor<<<grid3(d), dim3(BX, BY), 0, st>>>(divv, dispp, cfac, d, 1.f / nt);
+    SlArgs a{divv, dispp, cfac, divv, nullptr, nullptr, 1.f / nt};
+    launch_tiled<SL_ADJFAC>(d, a, st);
 }
 
 void launch_state_step(const Dims &d, const float *src, const float *dispm, float *dst,
                        cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_STATE, st, 20.0 * d.N);
-    k_state_step<<<grid3(d), dim3(BX, BY), 0, st>>>(src, dispm, dst, d);
+    SlArgs a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f};
+    launch_tiled<SL_PLAIN>(d, a, st);
 }
 
 void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const float *cfac,
                          float *dst, cudaStream_t st, Profiler *prof, int kclass) {
     ProfScope ps(prof, kclass, st, 24.0 * d.N);
-    k_adjoint_step<<<grid3(d), dim3(BX, BY), 0, st>>>(src, dispp, cfac, dst, d);
+    SlArgs a{src, dispp, dst, cfac, nullptr, nullptr, 0.f};
+    launch_tiled<SL_ADJ>(d, a, st);
 }
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
@@ -304,7 +477,8 @@ void launch_incstate_step(const Dims &d, float dt, const float *src, const float
                           const float *vt, const float *gm_next, float *dst, cudaStream_t st,
                           Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_INCSTATE, st, 44.0 * d.N);
-    k_incstate_step<<<grid3(d), dim3(BX, BY), 0, st>>>(src, dispm, vt, gm_next, dst, d, dt);
+    SlArgs a{src, dispm, dst, nullptr, vt, gm_next, dt};
+    launch_tiled<SL_INCSTATE>(d, a, st);
 }
 
 void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
