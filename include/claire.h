@@ -215,6 +215,26 @@ int claire_launch_count(const claire_ctx *ctx, long *launches);
 /* Device bytes held by the context. */
 int claire_workspace_bytes(const claire_ctx *ctx, size_t *bytes);
 
+/* ---- preconditioner without device allocation --------------------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory (a host framework that owns the whole
+ * device heap, code that may not call cudaMalloc/cudaFree because they
+ * synchronize, a fixed memory budget).  It computes the same
+ * s = (beta*A)^{-1} r as claire_precond for an nx*ny*nz grid without a
+ * context, on `stream` (a cudaStream_t; NULL = legacy), and allocates
+ * nothing: its scratch (FFT half spectra and twiddle tables) is a file-scope
+ * device array of fixed size that every GPU loading the library holds until
+ * exit.  Limit: 3 * nx * ny * p3 <= 442368 complex values, p3 = (nz/2 + 1)
+ * rounded up to a multiple of 4 (a 64^3 grid fits); larger grids, invalid
+ * sizes, beta <= 0, gamma < 0 or NULL pointers return CLAIRE_ERR_ARG with a
+ * message in claire_last_error(NULL).  r and s are device float[3][N] and
+ * may be equal.  The first call on each device looks up the array's device
+ * address (so make it before any stream capture).  All calls on a device share
+ * the array: calls that overlap on the GPU race and must be serialized by the
+ * caller.  Returns as soon as the work is enqueued. */
+int claire_precond_noalloc(int nx, int ny, int nz, double beta, double gamma, const float *r,
+                           float *s, void *stream);
+
 /* Message of the last error on ctx (or of the last failed claire_create when
  * ctx is NULL); never NULL. */
 const char *claire_last_error(const claire_ctx *ctx);

@@ -35,7 +35,7 @@ EXPORTED = [
     "claire_gradient", "claire_hess_matvec", "claire_precond", "claire_grad", "claire_div",
     "claire_apply_A", "claire_interp", "claire_get_field", "claire_solve_opts_default",
     "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
-    "claire_workspace_bytes", "claire_last_error",
+    "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
 ]
 
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "claire_profile_read": [P, I, ctypes.POINTER(ctypes.c_long), pd, pd],
         "claire_launch_count": [P, ctypes.POINTER(ctypes.c_long)],
         "claire_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "claire_precond_noalloc": [I, I, I, D, D, V, V, V],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -141,6 +142,19 @@ class Report:
     t_obj_ms: float
     t_pcg_ms: float
     t_total_ms: float
+
+
+def precond_noalloc(r, s, beta, gamma, stream=None):
+    """s = (beta*A)^{-1} r through claire_precond_noalloc (no device allocation
+    inside the library); r, s: float32 CUDA tensors [3, nx, ny, nz]."""
+    L = load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    nx, ny, nz = (int(x) for x in r.shape[1:])
+    rc = L.claire_precond_noalloc(nx, ny, nz, float(beta), float(gamma), _ptr(r), _ptr(s),
+                                  ctypes.c_void_p(st.cuda_stream))
+    if rc != CLAIRE_OK:
+        raise ClaireError(rc, L.claire_last_error(None).decode())
+    return s
 
 
 class Registration:

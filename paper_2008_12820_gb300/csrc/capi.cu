@@ -72,6 +72,9 @@ FftPlan make_plan(int n) {
 
 // ------------------------------------------------------------- profiler ----
 namespace claire {
+// message returned by claire_last_error(NULL) on this thread
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+
 int Profiler::begin(int cls, double bytes, cudaStream_t st) {
     if (!on) return -1;
     if (used == recs.size()) {

@@ -1,0 +1,63 @@
+"""The preconditioner entry point that allocates nothing
+(claire_precond_noalloc) against the context-based claire_precond.
+
+Callers that cannot allocate device memory (a host framework owning the whole
+device heap, code that may not call cudaMalloc/cudaFree because they
+synchronize) use claire_precond_noalloc; its scratch lives in a file-scope
+device array shared by all calls.  This file is collected last so that a run
+stopping at the first failure has already run every other test; it passes
+alone in a fresh process and after the others."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2008_12820_gb300 import claire
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return claire
+
+
+def rel(a, b):
+    a = a.double()
+    b = b.double()
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+def test_noalloc_matches_precond_on_two_calls_in_a_row(C):
+    beta, gamma = 1e-2, 1.0
+    cases = [((48, 40, 36), 0), ((32, 32, 32), 1)]
+    for shape, seed in cases:
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        r = torch.randn((3,) + shape, generator=g).cuda()
+        with C.Registration(shape, 4, beta, gamma) as reg:
+            ref = reg.precond(r)
+        s = torch.full_like(r, float("nan"))
+        C.precond_noalloc(r, s, beta, gamma)
+        torch.cuda.synchronize()
+        assert rel(s, ref) < 1e-5, (shape, rel(s, ref))
+    # a second pass over the same sizes reuses the scratch left by the others
+    for shape, seed in cases:
+        g = torch.Generator(device="cpu").manual_seed(seed + 10)
+        r = torch.randn((3,) + shape, generator=g).cuda()
+        with C.Registration(shape, 4, beta, gamma) as reg:
+            ref = reg.precond(r)
+        s = C.precond_noalloc(r, torch.empty_like(r), beta, gamma)
+        torch.cuda.synchronize()
+        assert rel(s, ref) < 1e-5, (shape, rel(s, ref))
+
+
+def test_noalloc_rejects_oversized_grid(C):
+    r = torch.zeros((3, 128, 128, 128), device="cuda")
+    with pytest.raises(C.ClaireError) as e:
+        C.precond_noalloc(r, r, 1e-2, 1.0)
+    assert e.value.code == 1 and "too large" in str(e.value)
