@@ -51,13 +51,16 @@ ERR_CHECK_N = 128        # GPU vs oracle gradient / matvec on a 128^3 instance
 
 KCLASS = ["footpoint", "state", "adjoint", "incstate", "incadj", "bodyforce", "fft_r2c",
           "fft_c2c", "fft_mul", "fft_c2r", "reduce", "vector", "interp"]
-# kernel function name regex of each class (for the ncu summaries)
-KNAMES = {"footpoint": "k_footpoints|k_adjoint_factor", "state": "k_state_step",
-          "adjoint": "k_adjoint_step", "incstate": "k_incstate_step",
-          "incadj": "k_adjoint_step", "bodyforce": "k_bodyforce", "fft_r2c": "k_r2c_x3",
+# kernel function names of each class (for the ncu summaries); the template
+# argument of k_sl_pipe is the step kind: 0 plain, 1 adjoint, 2 incremental
+# state, 3 adjoint factor
+KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3>",
+          "state": "k_sl_pipe<0>", "adjoint": "k_sl_pipe<1>", "incstate": "k_sl_pipe<2>",
+          "incadj": "k_sl_pipe<1>", "bodyforce": "k_bodyforce", "fft_r2c": "k_r2c_x3",
           "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1", "fft_c2r": "k_c2r_x3",
-          "reduce": "k_reduce2|k_finalize", "vector": "k_pcg|k_axpby|k_sub|k_inc",
-          "interp": "k_interp"}
+          "reduce": "k_reduce2, k_stats, k_finalize, k_finalize4",
+          "vector": "k_pcg_update, k_pcg_dir, k_axpby, k_sub, k_incstate_init, k_incadj_init",
+          "interp": "k_sl_pipe<0>"}
 
 
 def parse():
@@ -69,6 +72,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="run the same generator on an n^3 grid (profiling captures; not a bench line)")
     return ap.parse_args()
 
 
@@ -173,7 +178,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_2008_12820_gb300 import claire, synth
 
-    w = synth.workload(args.workload)
+    w = synth.workload(args.workload, shape=(args.grid,) * 3 if args.grid else None)
     shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
     N = int(np.prod(shape))
     m0 = torch.from_numpy(w["m0"]).cuda()

@@ -117,10 +117,17 @@ struct claire_ctx {
     float2 *spec = nullptr;
     double *partial = nullptr, *dres = nullptr;
     int *dflag = nullptr;
+    // floor ranges of the displacement fields: X-, X+, forward-only X-, interp
+    int *rng = nullptr;
+    int *rng_m() { return rng; }
+    int *rng_p() { return rng + 6; }
+    int *rng_f() { return rng + 12; }
+    int *rng_i() { return rng + 18; }
     // solver vectors, allocated on the first solve
     float *sv = nullptr;
 
     bool have_images = false, have_lin = false;
+    double last_vAv = 0;  // <v, beta A v> (grid sum) of the last gradient with J
 
     float *alloc_f(size_t n) { return (float *)alloc_bytes(n * sizeof(float)); }
     void *alloc_bytes(size_t b) {
@@ -163,60 +170,75 @@ struct claire_ctx {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        launch_footpoints(d, nt, vlin, dispm, dispp, st, &prof);
+        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
         CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        for (int j = 0; j < nt; ++j) launch_state_step(d, hist(mhist, j), dispm, hist(mhist, j + 1), st, &prof);
+        for (int j = 0; j < nt; ++j)
+            launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
         for (int j = 0; j <= nt; ++j) spectral(OP_GRAD, hist(mhist, j), hist(gmhist, j, 3), nullptr);
         spectral(OP_DIV, vlin, divv, nullptr);
-        launch_adjoint_factor(d, nt, divv, dispp, cfac, st, &prof);
+        launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
         have_lin = true;
     }
 
-    // adjoint solve + body force + beta A v; J into *J when asked
-    void gradient(const float *v, float *g, double *J, double *mis_out) {
+    // adjoint solve + body force + beta A v; J into *J when asked.  Av, if
+    // given, is beta*A v already at hand (the solver carries it along);
+    // otherwise it is applied spectrally.
+    void gradient(const float *v, float *g, double *J, double *mis_out, const float *Av = nullptr) {
         linearize(v);
         const size_t N = d.N;
         launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
         for (int j = nt; j >= 1; --j)
-            launch_adjoint_step(d, hist(lhist, j), dispp, cfac, hist(lhist, j - 1), st, &prof, CLAIRE_K_ADJOINT);
-        spectral(OP_A, vlin, s3a, nullptr);
-        launch_bodyforce(d, nt, lhist, gmhist, s3a, g, st, &prof);
+            launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
+                                CLAIRE_K_ADJOINT);
+        if (!Av) {
+            spectral(OP_A, vlin, s3a, nullptr);
+            Av = s3a;
+        }
+        launch_bodyforce(d, nt, lhist, gmhist, Av, g, st, &prof);
         check_launch("gradient");
         if (J || mis_out) {
             const double H3 = h3();
             const double mis = 0.5 * H3 * dot(hist(lhist, nt), hist(lhist, nt), (long long)N);
-            const double reg = 0.5 * H3 * dot(vlin, s3a, 3 * (long long)N);
+            last_vAv = dot(vlin, Av, 3 * (long long)N);
+            const double reg = 0.5 * H3 * last_vAv;
             if (J) *J = mis + reg;
             if (mis_out) *mis_out = mis;
         }
     }
 
-    void matvec(const float *vt, float *Hvt) {
+    // Hvt = beta A vt + int lt grad m dt.  Avt, if given, is beta*A vt already
+    // at hand (PCG carries it along); otherwise it is applied spectrally.
+    void matvec(const float *vt, float *Hvt, const float *Avt = nullptr) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
         const float dt = 1.f / nt;
         float *u = s1a, *un = s1b;
         launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
         for (int j = 0; j < nt; ++j) {
-            launch_incstate_step(d, dt, u, dispm, vt, hist(gmhist, j + 1, 3), un, st, &prof);
+            launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist, j + 1, 3), un, st, &prof);
             float *t = u; u = un; un = t;
         }
         launch_incadj_init(d, dt, u, vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
         for (int j = nt; j >= 1; --j)
-            launch_adjoint_step(d, hist(lhist, j), dispp, cfac, hist(lhist, j - 1), st, &prof, CLAIRE_K_INCADJ);
-        launch_bodyforce(d, nt, lhist, gmhist, nullptr, Hvt, st, &prof);
-        spectral(OP_A, vt, Hvt, Hvt);
+            launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
+                                CLAIRE_K_INCADJ);
+        if (Avt) {
+            launch_bodyforce(d, nt, lhist, gmhist, Avt, Hvt, st, &prof);
+        } else {
+            launch_bodyforce(d, nt, lhist, gmhist, nullptr, Hvt, st, &prof);
+            spectral(OP_A, vt, Hvt, Hvt);
+        }
         check_launch("hess_matvec");
     }
 
     // m(1) for v into mout (N); uses fdisp, s1a, s1b; leaves the cache alone
     const float *forward(const float *v) {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
-        launch_footpoints(d, nt, v, fdisp, nullptr, st, &prof);
+        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
         const float *src = m0;
         float *a = s1a, *b = s1b;
         for (int j = 0; j < nt; ++j) {
-            launch_state_step(d, src, fdisp, a, st, &prof);
+            launch_state_step(d, src, fdisp, rng_f(), a, st, &prof);
             src = a;
             float *t = a; a = b; b = t;
         }
@@ -328,9 +350,10 @@ int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, cla
         c->s1b = c->alloc_f(N);
         c->fdisp = c->alloc_f(3 * N);
         c->spec = (float2 *)c->alloc_bytes((size_t)3 * nx * ny * c->d.p3 * sizeof(float2));
-        c->partial = (double *)c->alloc_bytes(kReduceBlocks * sizeof(double));
+        c->partial = (double *)c->alloc_bytes(4 * kReduceBlocks * sizeof(double));
         c->dres = (double *)c->alloc_bytes(8 * sizeof(double));
         c->dflag = (int *)c->alloc_bytes(sizeof(int));
+        c->rng = (int *)c->alloc_bytes(24 * sizeof(int));
     } catch (const Error &e) {
         g_create_error = e.msg;
         delete c;
@@ -472,7 +495,7 @@ int claire_interp(claire_ctx *ctx, const float *f, const float *disp, float *out
     need(disp, "disp");
     need(out, "out");
     if (f == out) throw Error(CLAIRE_ERR_ARG, "f and out may not alias");
-    launch_interp(ctx->d, f, disp, out, ctx->st, &ctx->prof, CLAIRE_K_INTERP);
+    launch_interp(ctx->d, f, disp, out, ctx->rng_i(), ctx->st, &ctx->prof, CLAIRE_K_INTERP);
     check_launch("interp");
     API_END(ctx)
 }
@@ -547,8 +570,12 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
     claire_solve_report rep;
     std::memset(&rep, 0, sizeof(rep));
     const long long n3 = 3 * ctx->d.N;
-    if (!ctx->sv) ctx->sv = ctx->alloc_f((size_t)7 * n3);
+    // solver vectors; Av, Ax, Ap carry beta*A applied to v, the PCG iterate x
+    // and the search direction p, so that no FFT is needed for them
+    if (!ctx->sv) ctx->sv = ctx->alloc_f((size_t)10 * n3);
     float *g = ctx->sv, *x = g + n3, *r = x + n3, *z = r + n3, *p = z + n3, *q = p + n3, *vn = q + n3;
+    float *Av = vn + n3, *Ax = Av + n3, *Ap = Ax + n3;
+    const long long N = ctx->d.N;
     const double H3 = ctx->h3();
     cudaStream_t st = ctx->st;
     cudaEvent_t ev0, ev1;
@@ -562,13 +589,15 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
     double J = 0;
     {
         EvTimer t(st, &rep.t_grad_ms);
-        ctx->gradient(v, g, &J, nullptr);
+        ctx->spectral(OP_A, v, Av, nullptr);
+        ctx->gradient(v, g, &J, nullptr, Av);
     }
     const double g0 = std::sqrt(ctx->dot(g, g, n3));
     if (!std::isfinite(g0) || !std::isfinite(J)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite gradient or objective");
     rep.J0 = J;
     rep.g0 = g0;
     double gn = g0;
+    double vAv = ctx->last_vAv;  // <v, beta A v> (sum over the grid)
     int k = 0;
     int status = CLAIRE_OK;
     for (;;) {
@@ -580,8 +609,10 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
         {
             EvTimer tp(st, &t_pcg);
             CK(cudaMemsetAsync(x, 0, n3 * sizeof(float), st));
+            CK(cudaMemsetAsync(Ax, 0, n3 * sizeof(float), st));
             launch_axpby(r, -1.f, g, 0.f, nullptr, n3, st, &ctx->prof);
-            const double r0 = std::sqrt(ctx->dot(r, r, n3));
+            launch_stats(r, N, ctx->partial, ctx->dres, st, &ctx->prof);
+            const double r0 = std::sqrt(ctx->fetch(0));
             const int maxit = o.fixed_pcg > 0 ? o.fixed_pcg : o.max_pcg;
             int it = 0;
             if (r0 > 0) {
@@ -590,25 +621,30 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
                     ctx->spectral(OP_AINV, r, z, nullptr);
                 }
                 rep.n_precond++;
-                CK(cudaMemcpyAsync(p, z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, 0.f, N, true, st, &ctx->prof);
                 double rz = ctx->dot(r, z, n3);
                 while (it < maxit) {
                     {
                         EvTimer t(st, &rep.t_hess_ms);
-                        ctx->matvec(p, q);
+                        ctx->matvec(p, q, Ap);
                     }
                     rep.n_matvec++;
                     const double pq = ctx->dot(p, q, n3);
                     if (!std::isfinite(pq)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite p.Hp in PCG");
                     if (pq <= 0) {
-                        if (it == 0) CK(cudaMemcpyAsync(x, z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                        if (it == 0) {
+                            // keep the preconditioned residual z0 = p0 (and beta*A z0 = Ap0)
+                            CK(cudaMemcpyAsync(x, z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                            CK(cudaMemcpyAsync(Ax, Ap, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                        }
                         ++it;
                         break;
                     }
                     const double alpha = rz / pq;
-                    launch_pcg_xr(x, r, p, q, (float)alpha, n3, ctx->partial, ctx->dres, st, &ctx->prof);
+                    launch_pcg_update(x, Ax, r, p, Ap, q, (float)alpha, N, ctx->partial, ctx->dres, st,
+                                      &ctx->prof);
                     ++it;
-                    const double rn = std::sqrt(ctx->fetch());
+                    const double rn = std::sqrt(ctx->fetch(0));
                     if (o.fixed_pcg == 0 && rn <= epsk * r0) break;
                     if (it >= maxit) break;
                     {
@@ -619,21 +655,25 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
                     const double rz_new = ctx->dot(r, z, n3);
                     const double beta = rz_new / rz;
                     rz = rz_new;
-                    launch_pcg_p(p, z, (float)beta, n3, st, &ctx->prof);
+                    launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, (float)beta, N, false, st, &ctx->prof);
                 }
             }
             rep.n_pcg += it;
         }
         rep.t_pcg_ms += t_pcg;
-        // ---- Armijo backtracking
+        // ---- Armijo backtracking; the regularization term of J(v + a x) is
+        // 1/2 <v + a x, Av + a Ax>, a quadratic in a from three dot products
         const double slope = H3 * ctx->dot(g, x, n3);
+        const double xAv = ctx->dot(x, Av, n3), vAx = ctx->dot(v, Ax, n3), xAx = ctx->dot(x, Ax, n3);
         double alpha = 1.0;
         bool ok = false;
         {
             EvTimer t(st, &rep.t_obj_ms);
             for (int ls = 0; ls <= o.max_ls; ++ls) {
                 launch_axpby(vn, 1.f, v, (float)alpha, x, n3, st, &ctx->prof);
-                const double Jt = ctx->objective(vn, nullptr);
+                const double mis = ctx->mismatch_of(ctx->forward(vn));
+                const double reg = 0.5 * H3 * (vAv + alpha * (xAv + vAx) + alpha * alpha * xAx);
+                const double Jt = mis + reg;
                 rep.n_ls++;
                 if (std::isfinite(Jt) && Jt <= J + o.armijo_c1 * alpha * slope) {
                     ok = true;
@@ -647,11 +687,13 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
             break;
         }
         CK(cudaMemcpyAsync(v, vn, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        launch_axpby(Av, 1.f, Av, (float)alpha, Ax, n3, st, &ctx->prof);
         ++k;
         {
             EvTimer t(st, &rep.t_grad_ms);
-            ctx->gradient(v, g, &J, nullptr);
+            ctx->gradient(v, g, &J, nullptr, Av);
         }
+        vAv = ctx->last_vAv;
         gn = std::sqrt(ctx->dot(g, g, n3));
         if (!std::isfinite(gn) || !std::isfinite(J)) {
             status = CLAIRE_ERR_NONFINITE;

@@ -57,21 +57,25 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
                     cudaStream_t st, Profiler *prof);
 
 // ------------------------------------------------------------ transport ----
+// Foot points and the per-axis [min, max] floor range of each displacement
+// field (6 ints each), which fixes the shared-memory box of the SL kernels.
 void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
-                       cudaStream_t st, Profiler *prof);
-void launch_interp(const Dims &d, const float *f, const float *disp, float *out,
+                       int *range_m, int *range_p, cudaStream_t st, Profiler *prof);
+void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream_t st,
+                        Profiler *prof);
+void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int *range,
                    cudaStream_t st, Profiler *prof, int kclass);
 void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
-                           float *cfac, cudaStream_t st, Profiler *prof);
-void launch_state_step(const Dims &d, const float *src, const float *dispm, float *dst,
-                       cudaStream_t st, Profiler *prof);
-void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const float *cfac,
-                         float *dst, cudaStream_t st, Profiler *prof, int kclass);
+                           const int *range_p, float *cfac, cudaStream_t st, Profiler *prof);
+void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
+                       float *dst, cudaStream_t st, Profiler *prof);
+void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
+                         const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass);
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
                           cudaStream_t st, Profiler *prof);
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
-                          const float *vt, const float *gm_next, float *dst, cudaStream_t st,
-                          Profiler *prof);
+                          const int *range_m, const float *vt, const float *gm_next, float *dst,
+                          cudaStream_t st, Profiler *prof);
 void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
                         const float *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
                         Profiler *prof);
@@ -95,6 +99,16 @@ void launch_axpby(float *out, float a, const float *x, float b, const float *y, 
                   cudaStream_t st, Profiler *prof);  // out = a x + b y
 void launch_diff_flag(const float *a, const float *b, long long n, int *flag, cudaStream_t st,
                       Profiler *prof);
+// stats of a vector field [3][N]: dev_out[0] = r.r, dev_out[1..3] = component sums
+void launch_stats(const float *r, long long N, double *partial, double *dev_out, cudaStream_t st,
+                  Profiler *prof);
+// x += a p; Ax += a Ap; r -= a q; then the stats of r into dev_out[0..3]
+void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
+                       const float *q, float alpha, long long N, double *partial, double *dev_out,
+                       cudaStream_t st, Profiler *prof);
+// p = z + b p; Ap = (r - mean r) + b Ap (rsum: device component sums of r)
+void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
+                    float b, long long N, bool init, cudaStream_t st, Profiler *prof);
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
 
 // ------------------------------------------------------------ profiler ----

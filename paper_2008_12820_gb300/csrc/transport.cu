@@ -15,7 +15,7 @@
 // number (no loss of precision at large grid indices).
 //
 // The time-step kernels stage the source field in shared-memory halo boxes
-// (k_sl_tiled); the foot-point kernel gathers v from global memory, one
+// (k_sl_pipe); the foot-point kernel gathers v from global memory, one
 // thread per voxel, a block covering 32 consecutive x3 points of 8 x2 rows.
 #include <cuda_runtime.h>
 
@@ -144,19 +144,8 @@ k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__re
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory tiled semi-Lagrangian step.
-// A block owns T3 x T2 x T1 = 32 x 8 x 4 output voxels (a warp per x2 row,
-// every thread 4 voxels along x1).  Per-step displacements are a few cells, so
-// the 4x4x4 stencils of a block cover a small box of the source field: the
-// block takes the minimum and maximum floor of its displacements per axis,
-// stages that box in shared memory once (coalesced rows, periodic wrap) and
-// reads the 64 taps of every output from there with immediate offsets.  A
-// block whose box exceeds the capacity (large displacements) gathers from
-// global memory instead; the choice is uniform over the block.
+// Arguments shared by the semi-Lagrangian step kernels.
 // ---------------------------------------------------------------------------
-constexpr int T3 = 32, T2 = 8, T1 = 4;
-constexpr int BOX_CAP = 8192;  // floats of shared memory for the box
-
 enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3 };
 
 struct SlArgs {
@@ -171,122 +160,6 @@ struct SlArgs {
 
 __device__ __forceinline__ int floor_int(float x) {
     return (int)fminf(fmaxf(floorf(x), -1.0e6f), 1.0e6f);
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(T3 * T2)
-k_sl_tiled(SlArgs a, Dims d) {
-    extern __shared__ float box[];
-    __shared__ int fmin_s[3], fmax_s[3];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i3 = blockIdx.x * T3 + tx;
-    const int i2 = blockIdx.y * T2 + ty;
-    const int i1b = blockIdx.z * T1;
-    const bool ok23 = (i3 < d.n3) && (i2 < d.n2);
-    const long long N = d.N;
-    if (ty == 0 && tx < 3) {
-        fmin_s[tx] = 0x7fffffff;
-        fmax_s[tx] = -0x7fffffff;
-    }
-    float dd[T1][3];
-    int mn0 = 0x7fffffff, mn1 = 0x7fffffff, mn2 = 0x7fffffff;
-    int mx0 = -0x7fffffff, mx1 = -0x7fffffff, mx2 = -0x7fffffff;
-#pragma unroll
-    for (int t = 0; t < T1; ++t) {
-        const int i1 = i1b + t;
-        if (ok23 && i1 < d.n1) {
-            const long long id = ((long long)i1 * d.n2 + i2) * d.n3 + i3;
-            dd[t][0] = a.disp[id];
-            dd[t][1] = a.disp[N + id];
-            dd[t][2] = a.disp[2 * N + id];
-            const int f0 = floor_int(dd[t][0]), f1 = floor_int(dd[t][1]), f2 = floor_int(dd[t][2]);
-            mn0 = min(mn0, f0); mx0 = max(mx0, f0);
-            mn1 = min(mn1, f1); mx1 = max(mx1, f1);
-            mn2 = min(mn2, f2); mx2 = max(mx2, f2);
-        } else {
-            dd[t][0] = dd[t][1] = dd[t][2] = 0.f;
-        }
-    }
-    __syncthreads();  // fmin_s / fmax_s initialized
-    mn0 = __reduce_min_sync(0xffffffffu, mn0); mx0 = __reduce_max_sync(0xffffffffu, mx0);
-    mn1 = __reduce_min_sync(0xffffffffu, mn1); mx1 = __reduce_max_sync(0xffffffffu, mx1);
-    mn2 = __reduce_min_sync(0xffffffffu, mn2); mx2 = __reduce_max_sync(0xffffffffu, mx2);
-    if (tx == 0) {
-        atomicMin(&fmin_s[0], mn0); atomicMax(&fmax_s[0], mx0);
-        atomicMin(&fmin_s[1], mn1); atomicMax(&fmax_s[1], mx1);
-        atomicMin(&fmin_s[2], mn2); atomicMax(&fmax_s[2], mx2);
-    }
-    __syncthreads();
-    // source box [lo, lo + S) per axis covering every stencil of the block
-    const int lo1 = i1b + fmin_s[0] - 1;
-    const int lo2 = blockIdx.y * T2 + fmin_s[1] - 1;
-    const int lo3 = blockIdx.x * T3 + fmin_s[2] - 1;
-    const long long S1l = (long long)T1 + 3 + fmax_s[0] - fmin_s[0];
-    const long long S2l = (long long)T2 + 3 + fmax_s[1] - fmin_s[1];
-    const long long S3l = (long long)T3 + 3 + fmax_s[2] - fmin_s[2];
-    const bool use_box = S1l * S2l * S3l <= BOX_CAP;
-    const int S2 = (int)S2l, S3 = (int)S3l;
-    if (use_box) {
-        const int rows = (int)(S1l * S2l);
-        for (int r = ty; r < rows; r += T2) {
-            const int z = r / S2, y = r - z * S2;
-            const int g1 = wrap_index(lo1 + z, d.n1), g2 = wrap_index(lo2 + y, d.n2);
-            const float *srow = a.src + ((long long)g1 * d.n2 + g2) * d.n3;
-            float *brow = box + r * S3;
-            for (int x = tx; x < S3; x += T3) brow[x] = __ldg(srow + wrap_index(lo3 + x, d.n3));
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < T1; ++t) {
-        const int i1 = i1b + t;
-        if (!(ok23 && i1 < d.n1)) continue;
-        const long long id = ((long long)i1 * d.n2 + i2) * d.n3 + i3;
-        float val;
-        if (use_box) {
-            const float fl0 = floorf(dd[t][0]), fl1 = floorf(dd[t][1]), fl2 = floorf(dd[t][2]);
-            float w1[4], w2[4], w3[4];
-            lagrange4(dd[t][0] - fl0, w1);
-            lagrange4(dd[t][1] - fl1, w2);
-            lagrange4(dd[t][2] - fl2, w3);
-            const int b1 = i1 + (int)fl0 - 1 - lo1;
-            const int b2 = i2 + (int)fl1 - 1 - lo2;
-            const int b3 = i3 + (int)fl2 - 1 - lo3;
-            const float *p = box + (b1 * S2 + b2) * S3 + b3;
-            float acc = 0.f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float s2 = 0.f;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float *q = p + (i * S2 + j) * S3;
-                    float s3 = w3[0] * q[0];
-                    s3 = fmaf(w3[1], q[1], s3);
-                    s3 = fmaf(w3[2], q[2], s3);
-                    s3 = fmaf(w3[3], q[3], s3);
-                    s2 = fmaf(w2[j], s3, s2);
-                }
-                acc = fmaf(w1[i], s2, acc);
-            }
-            val = acc;
-        } else {
-            Pt p;
-            p.i1 = i1; p.i2 = i2; p.i3 = i3;
-            val = interp_at(a.src, d, p, dd[t][0], dd[t][1], dd[t][2]);
-        }
-        if (MODE == SL_PLAIN) {
-            a.dst[id] = val;
-        } else if (MODE == SL_ADJ) {
-            a.dst[id] = a.aux[id] * val;
-        } else if (MODE == SL_ADJFAC) {
-            const float dx = a.aux[id];
-            a.dst[id] = 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val;
-        } else {
-            const float f = -(a.vt[id] * a.gm[id] + a.vt[N + id] * a.gm[N + id] +
-                              a.vt[2 * N + id] * a.gm[2 * N + id]);
-            a.dst[id] = fmaf(a.dt, f, val);
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -355,13 +228,247 @@ k_sl_lean(SlArgs a, Dims d) {
     }
 }
 
-inline dim3 grid_tiled(const Dims &d) {
-    return dim3((d.n3 + T3 - 1) / T3, (d.n2 + T2 - 1) / T2, (d.n1 + T1 - 1) / T1);
+// ---------------------------------------------------------------------------
+// Software-pipelined tiled semi-Lagrangian step (the production path).
+// Persistent blocks walk the tiles of 32 x 8 x 4 voxels.  The floor range of
+// the displacement field (per axis, over the whole field, from
+// k_floor_range) fixes the geometry of the source box every tile needs, so
+// while a block computes tile k from one shared-memory buffer, cp.async
+// already copies the box of tile k+1 into the other, and the displacements
+// and epilogue inputs of tile k+1 are loaded into registers.  The 64 taps of
+// a voxel are then shared-memory reads with immediate offsets, the same
+// instruction stream for every lane (the periodic wrap happened once, when
+// the box was fetched).  If the range makes the box larger than a buffer, the
+// kernel gathers from global memory instead (the decision is uniform).
+// ---------------------------------------------------------------------------
+constexpr int PT3 = 32, PT2 = 8, PT1 = 4;
+// box geometry, fixed at compile time: floors of the displacement may span
+// BOX_SPAN + 1 consecutive integers per axis (per-step displacements of about
+// a cell); wider ranges take the global-memory gather
+constexpr int BOX_SPAN = 2;
+constexpr int BS1 = PT1 + 3 + BOX_SPAN, BS2 = PT2 + 3 + BOX_SPAN, BS3 = PT3 + 3 + BOX_SPAN;
+constexpr int BOX_PITCH = 64;  // floats per box row: rows start on bank 0
+constexpr int BOX_FLOATS = BS1 * BS2 * BOX_PITCH;
+static_assert(BS3 <= BOX_PITCH && BS3 > PT3, "box row must fit one pitch and exceed a warp");
+
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
+template <int MODE> struct EpiCount { static constexpr int v = MODE == SL_INCSTATE ? 6 : (MODE == SL_PLAIN ? 0 : 1); };
+
+template <int MODE>
+__device__ __forceinline__ void sl_epilogue(const SlArgs &a, long long id, float val, const float *e) {
+    if (MODE == SL_PLAIN) {
+        a.dst[id] = val;
+    } else if (MODE == SL_ADJ) {
+        a.dst[id] = e[0] * val;
+    } else if (MODE == SL_ADJFAC) {
+        const float dx = e[0];
+        a.dst[id] = 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val;
+    } else {
+        const float f = -(e[0] * e[3] + e[1] * e[4] + e[2] * e[5]);
+        a.dst[id] = fmaf(a.dt, f, val);
+    }
 }
 
 template <int MODE>
-void launch_tiled(const Dims &d, const SlArgs &a, cudaStream_t st) {
-    k_sl_lean<MODE><<<dim3((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1), dim3(BX, BY), 0, st>>>(a, d);
+__device__ __forceinline__ void sl_load_epi(const SlArgs &a, long long id, long long N, float *e) {
+    if (MODE == SL_ADJ || MODE == SL_ADJFAC) {
+        e[0] = a.aux[id];
+    } else if (MODE == SL_INCSTATE) {
+        e[0] = a.vt[id]; e[1] = a.vt[N + id]; e[2] = a.vt[2 * N + id];
+        e[3] = a.gm[id]; e[4] = a.gm[N + id]; e[5] = a.gm[2 * N + id];
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(PT3 * PT2, 2)
+k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
+    constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
+    extern __shared__ float smem[];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int fmn0 = range[0], fmn1 = range[2], fmn2 = range[4];
+    const bool use_box = range[1] - fmn0 <= BOX_SPAN && range[3] - fmn1 <= BOX_SPAN &&
+                         range[5] - fmn2 <= BOX_SPAN && fmn0 <= range[1] && fmn1 <= range[3] &&
+                         fmn2 <= range[5];
+    const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
+    const int ntiles = nb3 * nb2 * nb1;
+    const long long N = d.N, plane = (long long)d.n2 * d.n3;
+    int tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    if (!use_box) {
+        for (; tile < ntiles; tile += gridDim.x) {
+            const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
+            const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+            if (i3 >= d.n3 || i2 >= d.n2) continue;
+            for (int t = 0; t < PT1; ++t) {
+                const int i1 = t1 * PT1 + t;
+                if (i1 >= d.n1) break;
+                const long long id = i1 * plane + (long long)i2 * d.n3 + i3;
+                const float val = gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
+                float e[NE];
+                sl_load_epi<MODE>(a, id, N, e);
+                sl_epilogue<MODE>(a, id, val, e);
+            }
+        }
+        return;
+    }
+
+    // copy the box of tile tl: rows (z, y) over the warps, x over the lanes
+    // (every lane one column, the first BS3 - 32 lanes a second one)
+    auto issue_box = [&](int tl, float *buf) {
+        const int t3 = tl % nb3, r = tl / nb3, t2 = r % nb2, t1 = r / nb2;
+        const int lo1 = t1 * PT1 + fmn0 - 1, lo2 = t2 * PT2 + fmn1 - 1, lo3 = t3 * PT3 + fmn2 - 1;
+        const int xa = wrap_index(lo3 + tx, d.n3);
+        const bool two = tx < BS3 - PT3;
+        const int xb = wrap_index(lo3 + tx + PT3, d.n3);
+#pragma unroll
+        for (int yy = 0; yy < (BS2 + PT2 - 1) / PT2; ++yy) {
+            const int y = ty + yy * PT2;
+            if (y < BS2) {
+                const long long g2 = (long long)wrap_index(lo2 + y, d.n2) * d.n3;
+#pragma unroll
+                for (int z = 0; z < BS1; ++z) {
+                    const float *srow = a.src + wrap_index(lo1 + z, d.n1) * plane + g2;
+                    float *brow = buf + (z * BS2 + y) * BOX_PITCH;
+                    cp_async4(brow + tx, srow + xa);
+                    if (two) cp_async4(brow + tx + PT3, srow + xb);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    auto load_regs = [&](int tl, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
+        const int t3 = tl % nb3, r = tl / nb3, t2 = r % nb2, t1 = r / nb2;
+        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+        const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
+#pragma unroll
+        for (int t = 0; t < PT1; ++t) {
+            if (i3 < d.n3 && i2 < d.n2 && t1 * PT1 + t < d.n1) {
+                const long long id = id0 + t * plane;
+                dd[t][0] = a.disp[id];
+                dd[t][1] = a.disp[N + id];
+                dd[t][2] = a.disp[2 * N + id];
+                sl_load_epi<MODE>(a, id, N, ee[t]);
+            }
+        }
+    };
+
+    float nd[PT1][3], ne[PT1][NE];
+    issue_box(tile, smem);
+    load_regs(tile, nd, ne);
+    int cur = 0;
+    for (; tile < ntiles; tile += gridDim.x) {
+        float cd[PT1][3], ce[PT1][NE];
+#pragma unroll
+        for (int t = 0; t < PT1; ++t) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cd[t][c] = nd[t][c];
+#pragma unroll
+            for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
+        }
+        const int next = tile + gridDim.x;
+        if (next < ntiles) {
+            issue_box(next, smem + (cur ^ 1) * BOX_FLOATS);
+            load_regs(next, nd, ne);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *bx = smem + cur * BOX_FLOATS;
+        const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
+        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+        const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
+        if (i3 < d.n3 && i2 < d.n2) {
+#pragma unroll
+            for (int t = 0; t < PT1; ++t) {
+                if (t1 * PT1 + t < d.n1) {
+                    const float fl0 = floorf(cd[t][0]), fl1 = floorf(cd[t][1]), fl2 = floorf(cd[t][2]);
+                    float w1[4], w2[4], w3[4];
+                    lagrange4(cd[t][0] - fl0, w1);
+                    lagrange4(cd[t][1] - fl1, w2);
+                    lagrange4(cd[t][2] - fl2, w3);
+                    // stencil origin inside the box; every tap is an immediate offset
+                    const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2;
+                    const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int ia = 0; ia < 4; ++ia) {
+                        float sa = 0.f;
+#pragma unroll
+                        for (int ib = 0; ib < 4; ++ib) {
+                            const float *q = p + (ia * BS2 + ib) * BOX_PITCH;
+                            float s3 = w3[0] * q[0];
+                            s3 = fmaf(w3[1], q[1], s3);
+                            s3 = fmaf(w3[2], q[2], s3);
+                            s3 = fmaf(w3[3], q[3], s3);
+                            sa = fmaf(w2[ib], s3, sa);
+                        }
+                        acc = fmaf(w1[ia], sa, acc);
+                    }
+                    sl_epilogue<MODE>(a, id0 + t * plane, acc, ce[t]);
+                }
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
+// per-axis [min, max] of floor(disp) over the field (6 ints: min0, max0, ...)
+__global__ void k_range_init(int *range) {
+    if (threadIdx.x < 3) {
+        range[2 * threadIdx.x] = 0x7fffffff;
+        range[2 * threadIdx.x + 1] = -0x7fffffff;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_floor_range(const float *__restrict__ disp, long long N,
+                                                     int *__restrict__ range) {
+    for (int c = 0; c < 3; ++c) {
+        int mn = 0x7fffffff, mx = -0x7fffffff;
+        const float *dc = disp + c * N;
+        for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N; i += (long long)gridDim.x * 256) {
+            const int f = floor_int(dc[i]);
+            mn = min(mn, f);
+            mx = max(mx, f);
+        }
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&range[2 * c], mn);
+            atomicMax(&range[2 * c + 1], mx);
+        }
+    }
+}
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    }
+    return n;
+}
+
+template <int MODE>
+void launch_pipe(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
+    const long long ntiles = (long long)((d.n3 + PT3 - 1) / PT3) * ((d.n2 + PT2 - 1) / PT2) *
+                             ((d.n1 + PT1 - 1) / PT1);
+    const long long want = 2LL * num_sms();
+    const int blocks = (int)(ntiles < want ? ntiles : want);
+    const size_t smem = 2 * BOX_FLOATS * sizeof(float);
+    cudaFuncSetAttribute(k_sl_pipe<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_sl_pipe<MODE><<<blocks, dim3(PT3, PT2), smem, st>>>(a, d, range);
 }
 
 // ----------------------------------------------------------- pointwise ----
@@ -429,42 +536,54 @@ inline int grid1(long long N) {
 
 }  // namespace
 
-void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
-                       cudaStream_t st, Profiler *prof) {
-    const float dt = 1.f / nt;
-    const double two_pi = 6.283185307179586476925286766559;
-    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (dispp ? 36 : 24));
-    k_footpoints<<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt,
-                                                    (float)(d.n1 / two_pi), (float)(d.n2 / two_pi),
-                                                    (float)(d.n3 / two_pi));
+void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream_t st,
+                        Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 12.0 * d.N, 2);
+    k_range_init<<<1, 32, 0, st>>>(range);
+    k_floor_range<<<grid1(d.N), 256, 0, st>>>(disp, d.N, range);
 }
 
-void launch_interp(const Dims &d, const float *f, const float *disp, float *out, cudaStream_t st,
-                   Profiler *prof, int kclass) {
+void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
+                       int *range_m, int *range_p, cudaStream_t st, Profiler *prof) {
+    const float dt = 1.f / nt;
+    const double two_pi = 6.283185307179586476925286766559;
+    {
+        ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (dispp ? 36 : 24));
+        k_footpoints<<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt,
+                                                        (float)(d.n1 / two_pi), (float)(d.n2 / two_pi),
+                                                        (float)(d.n3 / two_pi));
+    }
+    launch_floor_range(d, dispm, range_m, st, prof);
+    if (dispp) launch_floor_range(d, dispp, range_p, st, prof);
+}
+
+void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int *range,
+                   cudaStream_t st, Profiler *prof, int kclass) {
+    launch_floor_range(d, disp, range, st, prof);
     ProfScope ps(prof, kclass, st, 20.0 * d.N);
     SlArgs a{f, disp, out, nullptr, nullptr, nullptr, 0.f};
-    launch_tiled<SL_PLAIN>(d, a, st);
+    launch_pipe<SL_PLAIN>(d, a, range, st);
 }
 
 void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
-                           float *cfac, cudaStream_t st, Profiler *prof) {
+                           const int *range_p, float *cfac, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 20.0 * d.N);
     SlArgs a{divv, dispp, cfac, divv, nullptr, nullptr, 1.f / nt};
-    launch_tiled<SL_ADJFAC>(d, a, st);
+    launch_pipe<SL_ADJFAC>(d, a, range_p, st);
 }
 
-void launch_state_step(const Dims &d, const float *src, const float *dispm, float *dst,
-                       cudaStream_t st, Profiler *prof) {
+void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
+                       float *dst, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_STATE, st, 20.0 * d.N);
     SlArgs a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f};
-    launch_tiled<SL_PLAIN>(d, a, st);
+    launch_pipe<SL_PLAIN>(d, a, range_m, st);
 }
 
-void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const float *cfac,
-                         float *dst, cudaStream_t st, Profiler *prof, int kclass) {
+void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
+                         const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass) {
     ProfScope ps(prof, kclass, st, 24.0 * d.N);
     SlArgs a{src, dispp, dst, cfac, nullptr, nullptr, 0.f};
-    launch_tiled<SL_ADJ>(d, a, st);
+    launch_pipe<SL_ADJ>(d, a, range_p, st);
 }
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
@@ -474,11 +593,11 @@ void launch_incstate_init(const Dims &d, float dt, const float *vt, const float 
 }
 
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
-                          const float *vt, const float *gm_next, float *dst, cudaStream_t st,
-                          Profiler *prof) {
+                          const int *range_m, const float *vt, const float *gm_next, float *dst,
+                          cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_INCSTATE, st, 44.0 * d.N);
     SlArgs a{src, dispm, dst, nullptr, vt, gm_next, dt};
-    launch_tiled<SL_INCSTATE>(d, a, st);
+    launch_pipe<SL_INCSTATE>(d, a, range_m, st);
 }
 
 void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,

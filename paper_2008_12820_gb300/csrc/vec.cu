@@ -133,6 +133,107 @@ __global__ void __launch_bounds__(RT) k_diff_flag(const float *__restrict__ a, c
     if (__syncthreads_or(diff) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
+// four block sums at once (one barrier round)
+__device__ __forceinline__ void block_sum4(double v[4]) {
+    __shared__ double ws4[4][RT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = warp_sum(v[k]);
+        if (lane == 0) ws4[k][w] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double t = (w == 0 && lane < RT / 32) ? ws4[k][lane] : 0.0;
+        v[k] = w == 0 ? warp_sum(t) : 0.0;
+    }
+}
+
+// statistics of a vector field r [3][N]: r.r and the sum of each component
+__device__ __forceinline__ void stats_store(Acc2 &rr, Acc2 *sc, double *partial) {
+    double v[4] = {rr.value(), sc[0].value(), sc[1].value(), sc[2].value()};
+    block_sum4(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partial[4 * blockIdx.x + k] = v[k];
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_stats(const float *__restrict__ r, long long N,
+                                              double *__restrict__ partial) {
+    Acc2 rr, sc[3];
+    const long long stride = (long long)gridDim.x * RT;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
+            const float ri = r[c * N + i];
+            rr.add_prod(ri, ri);
+            sc[c].add(ri, 0.f);
+        }
+    stats_store(rr, sc, partial);
+}
+
+// PCG update with the regularization term carried along (x, A x, r):
+// x += a p; Ax += a Ap; r -= a q; statistics of the new r
+__global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float *__restrict__ Ax,
+                                                   float *__restrict__ r, const float *__restrict__ p,
+                                                   const float *__restrict__ Ap,
+                                                   const float *__restrict__ q, float alpha,
+                                                   long long N, double *__restrict__ partial) {
+    Acc2 rr, sc[3];
+    const long long stride = (long long)gridDim.x * RT;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
+            x[i] = fmaf(alpha, p[i], x[i]);
+            Ax[i] = fmaf(alpha, Ap[i], Ax[i]);
+            const float ri = fmaf(-alpha, q[i], r[i]);
+            r[i] = ri;
+            rr.add_prod(ri, ri);
+            sc[c].add(ri, 0.f);
+        }
+    stats_store(rr, sc, partial);
+}
+
+__global__ void __launch_bounds__(RT) k_finalize4(const double *__restrict__ partial, int nb,
+                                                  double *__restrict__ out) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nb; i += RT)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += partial[4 * i + k];
+    block_sum4(v);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] = v[k];
+}
+
+// new search direction and its image under beta*A without an FFT:
+//   p = z + b p,   Ap = (r - mean r) + b Ap
+// since beta*A z = r - mean(r) for z = (beta*A)^{-1} r (the inverse is the
+// identity on the zero wavenumber, where beta*A vanishes).  init: b = 0 and
+// the old p, Ap are not read.  rsum: device sums of the components of r.
+__global__ void __launch_bounds__(RT) k_pcg_dir(float *__restrict__ p, float *__restrict__ Ap,
+                                                const float *__restrict__ z, const float *__restrict__ r,
+                                                const double *__restrict__ rsum, float b, long long N,
+                                                int init) {
+    const long long stride = (long long)gridDim.x * RT;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float mean = (float)(rsum[c] / (double)N);
+        for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
+            const float ar = r[i] - mean;
+            if (init) {
+                p[i] = z[i];
+                Ap[i] = ar;
+            } else {
+                p[i] = fmaf(b, p[i], z[i]);
+                Ap[i] = fmaf(b, Ap[i], ar);
+            }
+        }
+    }
+}
+
 inline int blocks_for(long long n) {
     long long b = (n + RT - 1) / RT;
     return (int)(b < kReduceBlocks ? b : kReduceBlocks);
@@ -181,6 +282,29 @@ void launch_diff_flag(const float *a, const float *b, long long n, int *flag, cu
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 8.0 * n);
     cudaMemsetAsync(flag, 0, sizeof(int), st);
     k_diff_flag<<<blocks_for(n), RT, 0, st>>>(a, b, n, flag);
+}
+
+void launch_stats(const float *r, long long N, double *partial, double *dev_out, cudaStream_t st,
+                  Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st, 12.0 * N, 2);
+    const int nb = blocks_for(N);
+    k_stats<<<nb, RT, 0, st>>>(r, N, partial);
+    k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
+                       const float *q, float alpha, long long N, double *partial, double *dev_out,
+                       cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * 36, 2);
+    const int nb = blocks_for(N);
+    k_pcg_update<<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial);
+    k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
+                    float b, long long N, bool init, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (init ? 16 : 24));
+    k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, b, N, init ? 1 : 0);
 }
 
 }  // namespace claire
