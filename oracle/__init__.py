@@ -44,14 +44,15 @@ def build(force: bool = False) -> str:
 
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("max_gn", _I), ("max_pcg", _I), ("fixed_pcg", _I), ("eps_n", ctypes.c_double),
-                ("armijo_c1", ctypes.c_double), ("max_ls", _I)]
+                ("armijo_c1", ctypes.c_double), ("max_ls", _I), ("pc", _I),
+                ("eps_h0", ctypes.c_double), ("max_inner", _I)]
 
 
 class _SolveReport(ctypes.Structure):
     _fields_ = [("n_gn", _I), ("n_pcg", _I), ("n_matvec", _I), ("n_precond", _I), ("status", _I),
                 ("J0", ctypes.c_double), ("J", ctypes.c_double), ("g0", ctypes.c_double),
                 ("g", ctypes.c_double), ("grel", ctypes.c_double),
-                ("mismatch_rel", ctypes.c_double)]
+                ("mismatch_rel", ctypes.c_double), ("n_inner", _L)]
 
 
 def lib():
@@ -93,6 +94,16 @@ def lib():
                                ctypes.POINTER(_SolveReport)]
         L.or_solve.restype = _I
         L.or_det_grad_y.argtypes = [_I, _I, _I, _I, _D, _D]
+        L.or_h0_matvec.argtypes = [_I, _I, _I, ctypes.c_double, ctypes.c_double, _D, _D, _D]
+        L.or_invh0.argtypes = [_I, _I, _I, ctypes.c_double, ctypes.c_double, _D, _D, _D,
+                               ctypes.c_double, _L]
+        L.or_invh0.restype = _L
+        L.or_invh0_2l.argtypes = L.or_invh0.argtypes
+        L.or_invh0_2l.restype = _L
+        _I3 = _I * 3
+        L.or_restrict.argtypes = [_I3, _I3, _D, _D]
+        L.or_prolong.argtypes = [_I3, _I3, _D, _D]
+        L.or_highpass.argtypes = [_I3, _I3, _D, _D]
         _lib = L
     return _lib
 
@@ -211,6 +222,53 @@ def det_grad_y(v: np.ndarray, nt: int) -> np.ndarray:
     return out
 
 
+def h0_matvec(s, gm, beta0, gamma):
+    """H0 s = beta0 A s + grad m (grad m . s) (zero-velocity Hessian)."""
+    s, gm = _f64(s), _f64(gm)
+    out = np.empty_like(s)
+    lib().or_h0_matvec(*s.shape[1:], beta0, gamma, _p(gm), _p(s), _p(out))
+    return out
+
+
+def invh0(r, gm, beta0, gamma, tol, maxit=500, two_level=False):
+    """PCG solve of H0 s = r, preconditioned by (beta0 A)^{-1}; two_level solves
+    on the half grid and adds the high-pass part (Algorithm 2)."""
+    r, gm = _f64(r), _f64(gm)
+    out = np.empty_like(r)
+    f = lib().or_invh0_2l if two_level else lib().or_invh0
+    it = f(*r.shape[1:], beta0, gamma, _p(gm), _p(r), _p(out), tol, maxit)
+    return out, int(it)
+
+
+def _resample(fn, f, shape_out):
+    f = _f64(f)
+    out = np.empty(shape_out)
+    n_in = (ctypes.c_int * 3)(*f.shape)
+    n_out = (ctypes.c_int * 3)(*shape_out)
+    fn(n_in, n_out, _p(f), _p(out))
+    return out
+
+
+def restrict(f, shape_c):
+    """Spectral restriction to a coarser grid (|k_d| < nc_d/2 kept)."""
+    return _resample(lib().or_restrict, f, tuple(shape_c))
+
+
+def prolong(fc, shape_f):
+    """Spectral prolongation (zero padding of the coarse band)."""
+    fc = _f64(fc)
+    out = np.empty(tuple(shape_f))
+    lib().or_prolong((ctypes.c_int * 3)(*fc.shape), (ctypes.c_int * 3)(*shape_f), _p(fc), _p(out))
+    return out
+
+
+def highpass(f, shape_c):
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().or_highpass((ctypes.c_int * 3)(*f.shape), (ctypes.c_int * 3)(*shape_c), _p(f), _p(out))
+    return out
+
+
 def pcg_dense(H: np.ndarray, P: np.ndarray, b: np.ndarray, tol: float, maxit: int,
               fixed: bool = False):
     """Run the oracle's PCG routine on dense matrices (for checking PCG itself)."""
@@ -241,6 +299,7 @@ class SolveReport:
     g: float
     grel: float
     mismatch_rel: float
+    n_inner: int
 
 
 class Problem:
@@ -335,9 +394,11 @@ class Problem:
         return out
 
     def solve(self, v0, max_gn=50, max_pcg=100, fixed_pcg=0, eps_n=5e-2, armijo_c1=1e-4,
-              max_ls=12):
+              max_ls=12, pc="invA", eps_h0=1e-3, max_inner=500):
+        """pc: "invA", "invH0" or "2LinvH0" (Section 3 "Preconditioning")."""
         v = _f64(v0).copy()
-        o = _SolveOpts(max_gn, max_pcg, fixed_pcg, eps_n, armijo_c1, max_ls)
+        pcn = {"invA": 0, "invH0": 1, "2LinvH0": 2}[pc]
+        o = _SolveOpts(max_gn, max_pcg, fixed_pcg, eps_n, armijo_c1, max_ls, pcn, eps_h0, max_inner)
         r = _SolveReport()
         lib().or_solve(self._h, _p(v), ctypes.byref(o), ctypes.byref(r))
         rep = SolveReport(**{k: getattr(r, k) for k, _ in _SolveReport._fields_})

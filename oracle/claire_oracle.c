@@ -739,6 +739,26 @@ static void or_precond_cb(void *c, const double *in, double *out) {
     or_precond((or_problem *)c, in, out);
 }
 
+long or_invh0(int n1, int n2, int n3, double beta0, double gamma, const double *gm,
+              const double *r, double *s, double tol, long maxit);
+long or_invh0_2l(int n1, int n2, int n3, double beta0, double gamma, const double *gm,
+                 const double *r, double *s, double tol, long maxit);
+
+/* outer preconditioner of the solver: InvA, InvH0 or two-level InvH0 with
+ * grad m(1) of the current iterate and inner tolerance eps_h0 * eps_K */
+typedef struct { or_problem *P; int pc; double tol; long maxit; long inner; } or_pc_ctx;
+static void or_pc_cb(void *c, const double *in, double *out) {
+    or_pc_ctx *q = (or_pc_ctx *)c;
+    or_problem *P = q->P;
+    if (q->pc == 0) { or_precond(P, in, out); return; }
+    double beta0 = P->beta < 5e-2 ? 5e-2 : P->beta;
+    const double *gm1 = P->gm + (long)P->nt * 3 * P->N;
+    if (q->pc == 1)
+        q->inner += or_invh0(P->n[0], P->n[1], P->n[2], beta0, P->gamma, gm1, in, out, q->tol, q->maxit);
+    else
+        q->inner += or_invh0_2l(P->n[0], P->n[1], P->n[2], beta0, P->gamma, gm1, in, out, q->tol, q->maxit);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Gauss-Newton-Krylov solver with Armijo line search (Algorithm 1, Eq. 3.3)   */
 /* ------------------------------------------------------------------------- */
@@ -749,11 +769,15 @@ typedef struct {
     double eps_n;      /* relative gradient stop, 5e-2 in Algorithm 1 */
     double armijo_c1;  /* sufficient decrease constant */
     int max_ls;        /* max step halvings */
+    int pc;            /* 0: (beta A)^{-1}, 1: InvH0, 2: two-level InvH0 */
+    double eps_h0;     /* inner tolerance factor (1e-3 for the NIREP runs) */
+    int max_inner;     /* max inner PCG iterations */
 } or_solve_opts;
 
 typedef struct {
     int n_gn, n_pcg, n_matvec, n_precond, status;
     double J0, J, g0, g, grel, mismatch_rel;
+    long n_inner;
 } or_solve_report;
 
 /* status: 0 converged (or max_gn / fixed work done), 1 line search failed */
@@ -780,8 +804,10 @@ int or_solve(or_problem *P, double *v, const or_solve_opts *o, or_solve_report *
         for (long i = 0; i < N3; ++i) rhs[i] = -g[i];
         int flag;
         long maxit = o->fixed_pcg > 0 ? o->fixed_pcg : o->max_pcg;
-        long it = or_pcg_core(N3, or_matvec_cb, P, or_precond_cb, P, rhs, vt, epsk, maxit,
+        or_pc_ctx pcc = {P, o->pc, o->eps_h0 * epsk, o->max_inner, 0};
+        long it = or_pcg_core(N3, or_matvec_cb, P, or_pc_cb, &pcc, rhs, vt, epsk, maxit,
                               o->fixed_pcg > 0, &flag, NULL);
+        rep->n_inner += pcc.inner;
         rep->n_pcg += (int)it;
         rep->n_matvec += (int)it;
         rep->n_precond += (int)it;
@@ -855,4 +881,132 @@ void or_det_grad_y(int n1, int n2, int n3, int nt, const double *v, double *det)
                + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
     }
     free(dm); free(u); free(tmp); free(G);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Zero-velocity Hessian preconditioners (Section 3 "Preconditioning",        */
+/* Algorithm 2).                                                              */
+/*   H0 s = beta0 A s + grad m (grad m . s),   beta0 = max(beta, 5e-2)        */
+/* with grad m the gradient of the deformed template m(1) at the current      */
+/* iterate.  InvH0 solves H0 s = r by PCG with preconditioner (beta0 A)^{-1}  */
+/* from s = 0 to relative residual tol (the left-preconditioned system of     */
+/* Algorithm 2 has the same solution).  The two-level variant solves the      */
+/* same system on a grid of half the resolution for the restricted residual   */
+/* and restricted grad m, prolongs the solution and adds the high-pass part   */
+/* of (beta0 A)^{-1} r.                                                        */
+/* ------------------------------------------------------------------------- */
+
+void or_h0_matvec(int n1, int n2, int n3, double beta0, double gamma, const double *gm,
+                  const double *s, double *out) {
+    long N = (long)n1 * n2 * n3;
+    or_apply_A(n1, n2, n3, beta0, gamma, s, out);
+    #pragma omp parallel for schedule(static)
+    for (long i = 0; i < N; ++i) {
+        double gs = gm[i] * s[i] + gm[N + i] * s[N + i] + gm[2 * N + i] * s[2 * N + i];
+        for (int d = 0; d < 3; ++d) out[d * N + i] += gm[d * N + i] * gs;
+    }
+}
+
+typedef struct { int n[3]; double beta0, gamma; const double *gm; } or_h0_ctx;
+static void or_h0_cb(void *c, const double *in, double *out) {
+    or_h0_ctx *h = (or_h0_ctx *)c;
+    or_h0_matvec(h->n[0], h->n[1], h->n[2], h->beta0, h->gamma, h->gm, in, out);
+}
+static void or_ainv_cb(void *c, const double *in, double *out) {
+    or_h0_ctx *h = (or_h0_ctx *)c;
+    or_apply_Ainv(h->n[0], h->n[1], h->n[2], h->beta0, h->gamma, in, out);
+}
+
+/* s = H0^{-1} r by PCG; returns the iteration count */
+long or_invh0(int n1, int n2, int n3, double beta0, double gamma, const double *gm,
+              const double *r, double *s, double tol, long maxit) {
+    or_h0_ctx h = {{n1, n2, n3}, beta0, gamma, gm};
+    int flag;
+    return or_pcg_core(3L * n1 * n2 * n3, or_h0_cb, &h, or_ainv_cb, &h, r, s, tol, maxit, 0, &flag,
+                       NULL);
+}
+
+/* Spectral restriction of a field on an n grid to an nc grid (nc <= n per
+ * axis): keep the wavenumbers with |k_d| < nc_d/2 (the coarse Nyquist mode is
+ * dropped), rescale for the coarse transform length. */
+void or_restrict(const int n[3], const int nc[3], const double *f, double *fc) {
+    long N = (long)n[0] * n[1] * n[2], Nc = (long)nc[0] * nc[1] * nc[2];
+    cplx *F = or_spectrum(n, f);
+    cplx *G = (cplx *)calloc((size_t)Nc, sizeof(cplx));
+    for (int i1 = 0; i1 < nc[0]; ++i1)
+        for (int i2 = 0; i2 < nc[1]; ++i2)
+            for (int i3 = 0; i3 < nc[2]; ++i3) {
+                const int ic[3] = {i1, i2, i3};
+                long src[3];
+                int keep = 1;
+                for (int d = 0; d < 3; ++d) {
+                    double k = or_wavenumber(ic[d], nc[d]);
+                    if (2.0 * fabs(k) >= nc[d]) keep = 0;
+                    src[d] = k < 0 ? (long)(n[d] + k) : (long)k;
+                }
+                if (keep) G[or_idx(nc, i1, i2, i3)] = F[or_idx(n, src[0], src[1], src[2])] * ((double)Nc / (double)N);
+            }
+    or_field(nc, G, fc);
+    free(F);
+    free(G);
+}
+
+/* Spectral prolongation from an nc grid to an n grid: the coarse wavenumbers
+ * with |k_d| < nc_d/2 are placed into the fine spectrum (zero elsewhere). */
+void or_prolong(const int nc[3], const int n[3], const double *fc, double *f) {
+    long N = (long)n[0] * n[1] * n[2], Nc = (long)nc[0] * nc[1] * nc[2];
+    cplx *G = or_spectrum(nc, fc);
+    cplx *F = (cplx *)calloc((size_t)N, sizeof(cplx));
+    for (int i1 = 0; i1 < nc[0]; ++i1)
+        for (int i2 = 0; i2 < nc[1]; ++i2)
+            for (int i3 = 0; i3 < nc[2]; ++i3) {
+                const int ic[3] = {i1, i2, i3};
+                long dst[3];
+                int keep = 1;
+                for (int d = 0; d < 3; ++d) {
+                    double k = or_wavenumber(ic[d], nc[d]);
+                    if (2.0 * fabs(k) >= nc[d]) keep = 0;
+                    dst[d] = k < 0 ? (long)(n[d] + k) : (long)k;
+                }
+                if (keep) F[or_idx(n, dst[0], dst[1], dst[2])] = G[or_idx(nc, i1, i2, i3)] * ((double)N / (double)Nc);
+            }
+    or_field(n, F, f);
+    free(F);
+    free(G);
+}
+
+/* the part of f that the half grid does not represent: f - P(R(f)) */
+void or_highpass(const int n[3], const int nc[3], const double *f, double *out) {
+    long N = (long)n[0] * n[1] * n[2], Nc = (long)nc[0] * nc[1] * nc[2];
+    double *c = (double *)malloc(sizeof(double) * (size_t)Nc);
+    or_restrict(n, nc, f, c);
+    or_prolong(nc, n, c, out);
+    for (long i = 0; i < N; ++i) out[i] = f[i] - out[i];
+    free(c);
+}
+
+/* two-level InvH0 (Algorithm 2, second function); returns coarse iterations */
+long or_invh0_2l(int n1, int n2, int n3, double beta0, double gamma, const double *gm,
+                 const double *r, double *s, double tol, long maxit) {
+    const int n[3] = {n1, n2, n3};
+    const int nc[3] = {n1 / 2, n2 / 2, n3 / 2};
+    long N = (long)n1 * n2 * n3, Nc = (long)nc[0] * nc[1] * nc[2];
+    double *sf = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *hp = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *rc = (double *)malloc(sizeof(double) * 3 * (size_t)Nc);
+    double *gmc = (double *)malloc(sizeof(double) * 3 * (size_t)Nc);
+    double *sc = (double *)malloc(sizeof(double) * 3 * (size_t)Nc);
+    or_apply_Ainv(n1, n2, n3, beta0, gamma, r, sf);
+    for (int d = 0; d < 3; ++d) {
+        or_highpass(n, nc, sf + d * N, hp + d * N);
+        or_restrict(n, nc, r + d * N, rc + d * Nc);
+        or_restrict(n, nc, gm + d * N, gmc + d * Nc);
+    }
+    long it = or_invh0(nc[0], nc[1], nc[2], beta0, gamma, gmc, rc, sc, tol, maxit);
+    for (int d = 0; d < 3; ++d) {
+        or_prolong(nc, n, sc + d * Nc, s + d * N);
+        for (long i = 0; i < N; ++i) s[d * N + i] += hp[d * N + i];
+    }
+    free(sf); free(hp); free(rc); free(gmc); free(sc);
+    return it;
 }
