@@ -84,6 +84,25 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_ranks(ms_local, n_vox_local, world_size, device=None):
+    """Job-level numbers of the replica run: the slowest rank's time per step
+    (max over ranks) and the voxels all ranks registered per second.  Each rank
+    solves its own registration, so the only collective is this reduction."""
+    import torch
+    if world_size > 1:
+        import torch.distributed as dist
+        t = torch.tensor([float(ms_local), float(n_vox_local)], dtype=torch.float64,
+                         device=device)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = t.clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms, vox = float(mx[0].item()), float(tot[1].item())
+    else:
+        ms, vox = float(ms_local), float(n_vox_local)
+    return ms, vox / (ms * 1e-3) / 1e9
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -220,11 +239,7 @@ def run_ours(args):
     clk = clocks.stop()
     prof = {k: reg.profile_read(i) for i, k in enumerate(KCLASS)}
     reg.profile_enable(False)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * N / (ms * 1e-3) / 1e9
+    ms, value = aggregate_ranks(ms, N, ws, device="cuda")
     rep = reports[-1]
 
     # ---- Hessian matvec throughput at the solution (own events loop) -------

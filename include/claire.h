@@ -114,6 +114,22 @@ int claire_hess_matvec(claire_ctx *ctx, const float *v, const float *vt, float *
  * identity on the zero wavenumber.  r, s: float[3][N]; s may equal r. */
 int claire_precond(claire_ctx *ctx, const float *r, float *s);
 
+/* Zero-velocity Hessian preconditioner InvH0 (Section 3 "Preconditioning",
+ * Algorithm 2): s = H0^{-1} r with H0 = beta0 A + grad m (x) grad m, where
+ * beta0 = max(beta, 5e-2) and grad m = grad m(., 1) of the cached
+ * linearization (the deformed template at the current iterate).  Solved by
+ * PCG preconditioned with (beta0 A)^{-1} from s = 0 until the residual drops
+ * to tol times the initial one, or for exactly maxit iterations if tol == 0.
+ * two_level != 0 selects the two-level variant: r and grad m are restricted
+ * spectrally to the grid of half the resolution (wavenumbers |k_d| < n_d/4
+ * kept), the system is solved there, and the prolonged solution is added to
+ * the high-pass part of (beta0 A)^{-1} r (needs even sizes whose halves are
+ * valid, >= 4).  r, s: float[3][N], distinct.  *iterations (nullable) gets
+ * the (inner) iteration count.  CLAIRE_ERR_STATE without a linearization.
+ * Synchronizes. */
+int claire_precond_h0(claire_ctx *ctx, const float *r, float *s, double tol, int maxit,
+                      int two_level, int *iterations);
+
 /* ---- single operators (for checks and composition) ------------------- */
 
 /* Spectral gradient of a scalar field (Section 3): g_d = F^-1[i k_d F f].
@@ -150,6 +166,9 @@ int claire_get_field(claire_ctx *ctx, int which, int j, float *out);
 
 /* ---- Gauss-Newton-Krylov solver (Algorithm 1, Eq. 3.3) --------------- */
 
+/* preconditioners of the Gauss-Newton system (Section 3 "Preconditioning") */
+enum { CLAIRE_PC_INVA = 0, CLAIRE_PC_INVH0 = 1, CLAIRE_PC_2LINVH0 = 2 };
+
 typedef struct {
     int max_gn;        /* max Gauss-Newton iterations (default 50) */
     int max_pcg;       /* max PCG iterations per GN step (default 100) */
@@ -157,6 +176,9 @@ typedef struct {
     double eps_n;      /* stop when ||g_k|| / ||g_0|| <= eps_n (default 5e-2) */
     double armijo_c1;  /* sufficient decrease constant (default 1e-4) */
     int max_ls;        /* max step halvings in the line search (default 12) */
+    int precond;       /* CLAIRE_PC_INVA (default), CLAIRE_PC_INVH0, CLAIRE_PC_2LINVH0 */
+    double eps_h0;     /* InvH0 inner tolerance factor: inner tol = eps_h0 * eps_K (1e-3) */
+    int max_inner;     /* max inner PCG iterations per InvH0 application (500) */
 } claire_solve_opts;
 
 typedef struct {
@@ -170,6 +192,7 @@ typedef struct {
     double g0, g;      /* ||g|| (2-norm over the grid) at the initial and final v */
     double grel;       /* g / g0 */
     double mismatch_rel; /* ||m(1) - m1|| / ||m0 - m1|| at the final v */
+    long n_inner;      /* inner PCG iterations of InvH0 over the solve */
     double t_grad_ms, t_hess_ms, t_pc_ms, t_obj_ms, t_pcg_ms, t_total_ms; /* CUDA-event times */
 } claire_solve_report;
 
@@ -186,6 +209,18 @@ void claire_solve_opts_default(claire_solve_opts *opts);
  * then holds the last accepted iterate). */
 int claire_solve(claire_ctx *ctx, float *v_inout, const claire_solve_opts *opts,
                  claire_solve_report *report);
+
+/* Parameter continuation in beta (Section 3 "Preconditioning", last
+ * paragraph): Gauss-Newton solves for beta_k = max(beta_target,
+ * beta_start * factor^k), k = 0, 1, ..., each started from the previous
+ * velocity in v_inout.  Levels with beta_k > 5e-1 use the spectral
+ * preconditioner, the others opts->precond.  The report accumulates the
+ * counts and times of all levels and holds the last level's objective and
+ * gradient values; *levels (nullable) gets the number of levels.  Leaves the
+ * context's beta at beta_target.  Needs 0 < factor < 1, beta_start > 0. */
+int claire_solve_continuation(claire_ctx *ctx, float *v_inout, double beta_target,
+                              double beta_start, double factor, const claire_solve_opts *opts,
+                              claire_solve_report *report, int *levels);
 
 /* ---- instrumentation -------------------------------------------------- */
 

@@ -104,6 +104,14 @@ def lib():
         L.or_restrict.argtypes = [_I3, _I3, _D, _D]
         L.or_prolong.argtypes = [_I3, _I3, _D, _D]
         L.or_highpass.argtypes = [_I3, _I3, _D, _D]
+        L.or_set_discretization.argtypes = [ctypes.c_void_p, _I, _I]
+        L.or_grad_fd8.argtypes = [_I, _I, _I, _D, _D]
+        L.or_div_fd8.argtypes = [_I, _I, _I, _D, _D]
+        L.or_lerp.argtypes = [_I, _I, _I, _D, _L, _D, _D, _D, _D]
+        L.or_solve_continuation.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.POINTER(_SolveOpts),
+                                            ctypes.POINTER(_SolveReport), ctypes.POINTER(_I)]
+        L.or_solve_continuation.restype = _I
         _lib = L
     return _lib
 
@@ -160,6 +168,31 @@ def apply_Ainv(v: np.ndarray, beta: float, gamma: float) -> np.ndarray:
     v = _f64(v)
     out = np.empty_like(v)
     lib().or_apply_Ainv(*v.shape[1:], beta, gamma, _p(v), _p(out))
+    return out
+
+
+def grad_fd8(f: np.ndarray) -> np.ndarray:
+    """Eighth-order central-difference gradient (Section 4.2)."""
+    f = _f64(f)
+    out = np.empty((3,) + f.shape)
+    lib().or_grad_fd8(*f.shape, _p(f), _p(out))
+    return out
+
+
+def div_fd8(v: np.ndarray) -> np.ndarray:
+    v = _f64(v)
+    out = np.empty(v.shape[1:])
+    lib().or_div_fd8(*v.shape[1:], _p(v), _p(out))
+    return out
+
+
+def lerp(f: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """Periodic trilinear interpolation of f at points q[3, ...] (index units)."""
+    f = _f64(f)
+    q = _f64(q).reshape(3, -1)
+    q1, q2, q3 = (np.ascontiguousarray(q[d]) for d in range(3))
+    out = np.empty(q.shape[1])
+    lib().or_lerp(*f.shape, _p(f), q.shape[1], _p(q1), _p(q2), _p(q3), _p(out))
     return out
 
 
@@ -312,6 +345,11 @@ class Problem:
         self.nt, self.beta, self.gamma = nt, beta, gamma
         self._h = lib().or_create(*self.shape, nt, beta, gamma, _p(m0), _p(m1))
 
+    def set_discretization(self, interp="cubic", deriv="spectral"):
+        """interp: "cubic" | "linear"; deriv: "spectral" | "fd8" (Sections 4.1, 4.2)."""
+        lib().or_set_discretization(self._h, 1 if interp == "linear" else 3,
+                                    1 if deriv == "fd8" else 0)
+
     def close(self):
         if self._h:
             lib().or_destroy(self._h)
@@ -403,3 +441,23 @@ class Problem:
         lib().or_solve(self._h, _p(v), ctypes.byref(o), ctypes.byref(r))
         rep = SolveReport(**{k: getattr(r, k) for k, _ in _SolveReport._fields_})
         return v, rep
+
+    def solve_continuation(self, v0, beta_target, beta_start=1.0, factor=0.1, pc="invH0",
+                           **kw):
+        """beta-continuation: GN solves for beta_k = max(target, start * factor^k),
+        warm-started; InvA while beta_k > 0.5, pc below.  Returns (v, report,
+        levels); the problem's beta is left at the target."""
+        v = _f64(v0).copy()
+        opts = dict(max_gn=50, max_pcg=100, fixed_pcg=0, eps_n=5e-2, armijo_c1=1e-4, max_ls=12,
+                    eps_h0=1e-3, max_inner=500)
+        opts.update(kw)
+        pcn = {"invA": 0, "invH0": 1, "2LinvH0": 2}[pc]
+        o = _SolveOpts(opts["max_gn"], opts["max_pcg"], opts["fixed_pcg"], opts["eps_n"],
+                       opts["armijo_c1"], opts["max_ls"], pcn, opts["eps_h0"], opts["max_inner"])
+        r = _SolveReport()
+        lev = _I(0)
+        lib().or_solve_continuation(self._h, _p(v), beta_target, beta_start, factor,
+                                    ctypes.byref(o), ctypes.byref(r), ctypes.byref(lev))
+        self.beta = beta_target
+        rep = SolveReport(**{k: getattr(r, k) for k, _ in _SolveReport._fields_})
+        return v, rep, int(lev.value)

@@ -355,9 +355,19 @@ void or_interp(int n1, int n2, int n3, const double *f, long npts,
     }
 }
 
+double or_lerp_at(const int n[3], const double *f, const double q[3]);
+void or_grad_fd8(int n1, int n2, int n3, const double *f, double *g);
+void or_div_fd8(int n1, int n2, int n3, const double *v, double *out);
+
+/* interpolant of the given order: 3 = cubic Lagrange, 1 = trilinear */
+static double or_interp_o(int order, const int n[3], const double *f, const double q[3]) {
+    return order == 1 ? or_lerp_at(n, f, q) : or_interp_at(n, f, q);
+}
+
 /* interpolate f at the foot points of all grid points: the foot point of grid
  * point (i1,i2,i3) is (i1,i2,i3) + disp(i1,i2,i3) in index units */
-static void or_interp_grid(const int n[3], const double *f, const double *disp, double *out) {
+static void or_interp_grid_o(int order, const int n[3], const double *f, const double *disp,
+                             double *out) {
     long N = (long)n[0] * n[1] * n[2];
     #pragma omp parallel for collapse(2) schedule(static)
     for (int i1 = 0; i1 < n[0]; ++i1)
@@ -365,7 +375,7 @@ static void or_interp_grid(const int n[3], const double *f, const double *disp, 
             for (int i3 = 0; i3 < n[2]; ++i3) {
                 long id = or_idx(n, i1, i2, i3);
                 double q[3] = {i1 + disp[id], i2 + disp[N + id], i3 + disp[2 * N + id]};
-                out[id] = or_interp_at(n, f, q);
+                out[id] = or_interp_o(order, n, f, q);
             }
 }
 
@@ -377,7 +387,8 @@ static void or_interp_grid(const int n[3], const double *f, const double *disp, 
 /* v is in domain units; the result is the displacement X - x in index units.  */
 /* sign = -1 gives X-, sign = +1 gives X+.                                     */
 /* ------------------------------------------------------------------------- */
-void or_footpoints(int n1, int n2, int n3, int nt, const double *v, int sign, double *disp) {
+static void or_footpoints_o(int order, int n1, int n2, int n3, int nt, const double *v, int sign,
+                            double *disp) {
     const int n[3] = {n1, n2, n3};
     long N = (long)n1 * n2 * n3;
     double dt = 1.0 / nt;
@@ -392,11 +403,15 @@ void or_footpoints(int n1, int n2, int n3, int nt, const double *v, int sign, do
                 for (int d = 0; d < 3; ++d) vx[d] = v[d * N + id];
                 /* predictor (explicit Euler), in index units */
                 for (int d = 0; d < 3; ++d) ystar[d] = ii[d] + sign * dt * vx[d] / h[d];
-                for (int d = 0; d < 3; ++d) vy[d] = or_interp_at(n, v + d * N, ystar);
+                for (int d = 0; d < 3; ++d) vy[d] = or_interp_o(order, n, v + d * N, ystar);
                 /* corrector (trapezoid) */
                 for (int d = 0; d < 3; ++d)
                     disp[d * N + id] = sign * 0.5 * dt * (vx[d] + vy[d]) / h[d];
             }
+}
+
+void or_footpoints(int n1, int n2, int n3, int nt, const double *v, int sign, double *disp) {
+    or_footpoints_o(3, n1, n2, n3, nt, v, sign, disp);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -408,12 +423,16 @@ static double or_trap_w(int j, int nt) { return (j == 0 || j == nt) ? 0.5 : 1.0;
 
 /* state equation (Eq. 2.1b): d_t m + v.grad m = 0, m(0) = m0.
  * Semi-Lagrangian: m^{j+1}(x) = m^j(X-(x)).  mhist holds m^0..m^nt. */
-void or_state(int n1, int n2, int n3, int nt, const double *dispm, const double *m0, double *mhist) {
+static void or_state_o(int order, int n1, int n2, int n3, int nt, const double *dispm,
+                       const double *m0, double *mhist) {
     const int n[3] = {n1, n2, n3};
     long N = (long)n1 * n2 * n3;
     memcpy(mhist, m0, sizeof(double) * (size_t)N);
     for (int j = 0; j < nt; ++j)
-        or_interp_grid(n, mhist + (long)j * N, dispm, mhist + (long)(j + 1) * N);
+        or_interp_grid_o(order, n, mhist + (long)j * N, dispm, mhist + (long)(j + 1) * N);
+}
+void or_state(int n1, int n2, int n3, int nt, const double *dispm, const double *m0, double *mhist) {
+    or_state_o(3, n1, n2, n3, nt, dispm, m0, mhist);
 }
 
 /* Adjoint-type equation (Eqs. (3.2) and (3.6)): -d_t l - div(l v) = 0,
@@ -423,15 +442,15 @@ void or_state(int n1, int n2, int n3, int nt, const double *dispm, const double 
  *   predictor:  l*       = l^j(X+) + dt * l^j(X+) d(X+)
  *   corrector:  l^{j-1}(x) = l^j(X+) + dt/2 [ l^j(X+) d(X+) + l* d(x) ]
  * d = div v on the grid, dp = d interpolated at X+.  lhist holds l^0..l^nt. */
-void or_adjoint(int n1, int n2, int n3, int nt, const double *dispp, const double *d,
-                const double *dp, const double *lfinal, double *lhist) {
+static void or_adjoint_o(int order, int n1, int n2, int n3, int nt, const double *dispp,
+                         const double *d, const double *dp, const double *lfinal, double *lhist) {
     const int n[3] = {n1, n2, n3};
     long N = (long)n1 * n2 * n3;
     double dt = 1.0 / nt;
     double *lx = (double *)malloc(sizeof(double) * (size_t)N);
     memcpy(lhist + (long)nt * N, lfinal, sizeof(double) * (size_t)N);
     for (int j = nt; j >= 1; --j) {
-        or_interp_grid(n, lhist + (long)j * N, dispp, lx);
+        or_interp_grid_o(order, n, lhist + (long)j * N, dispp, lx);
         double *out = lhist + (long)(j - 1) * N;
         #pragma omp parallel for schedule(static)
         for (long i = 0; i < N; ++i) {
@@ -448,8 +467,8 @@ void or_adjoint(int n1, int n2, int n3, int nt, const double *dispp, const doubl
  * (foot point X-), trapezoid for the source:
  *   mt^{j+1}(x) = mt^j(X-) + dt/2 [ f^j(X-) + f^{j+1}(x) ].
  * gmhist holds grad m^j (3N per level).  mthist holds mt^0..mt^nt. */
-void or_incstate(int n1, int n2, int n3, int nt, const double *dispm, const double *gmhist,
-                 const double *vt, double *mthist) {
+static void or_incstate_o(int order, int n1, int n2, int n3, int nt, const double *dispm,
+                          const double *gmhist, const double *vt, double *mthist) {
     const int n[3] = {n1, n2, n3};
     long N = (long)n1 * n2 * n3;
     double dt = 1.0 / nt;
@@ -463,8 +482,8 @@ void or_incstate(int n1, int n2, int n3, int nt, const double *dispm, const doub
     double *b = (double *)malloc(sizeof(double) * (size_t)N);
     memset(mthist, 0, sizeof(double) * (size_t)N);
     for (int j = 0; j < nt; ++j) {
-        or_interp_grid(n, mthist + (long)j * N, dispm, a);
-        or_interp_grid(n, f + (long)j * N, dispm, b);
+        or_interp_grid_o(order, n, mthist + (long)j * N, dispm, a);
+        or_interp_grid_o(order, n, f + (long)j * N, dispm, b);
         double *out = mthist + (long)(j + 1) * N;
         #pragma omp parallel for schedule(static)
         for (long i = 0; i < N; ++i)
@@ -473,6 +492,15 @@ void or_incstate(int n1, int n2, int n3, int nt, const double *dispm, const doub
     free(a);
     free(b);
     free(f);
+}
+
+void or_adjoint(int n1, int n2, int n3, int nt, const double *dispp, const double *d,
+                const double *dp, const double *lfinal, double *lhist) {
+    or_adjoint_o(3, n1, n2, n3, nt, dispp, d, dp, lfinal, lhist);
+}
+void or_incstate(int n1, int n2, int n3, int nt, const double *dispm, const double *gmhist,
+                 const double *vt, double *mthist) {
+    or_incstate_o(3, n1, n2, n3, nt, dispm, gmhist, vt, mthist);
 }
 
 /* body force (time integral in Eqs. (3.1) and (3.3)) by the trapezoidal rule:
@@ -508,7 +536,26 @@ typedef struct {
     double *d;     /* N, div v */
     double *dp;    /* N, div v at X+ */
     long n_pde;    /* transport solves done, for reports */
+    int interp_order; /* 3: cubic Lagrange (default), 1: trilinear */
+    int deriv_fd8;    /* 0: spectral first derivatives (default), 1: FD8 */
 } or_problem;
+
+/* discretization of the problem: interpolation order (3 or 1) and first
+ * derivatives (0 spectral, 1 eighth-order finite differences) */
+void or_set_discretization(or_problem *P, int interp_order, int deriv_fd8) {
+    P->interp_order = interp_order == 1 ? 1 : 3;
+    P->deriv_fd8 = deriv_fd8 ? 1 : 0;
+    P->have_lin = 0;
+}
+
+static void or_grad_p(const or_problem *P, const double *f, double *g) {
+    if (P->deriv_fd8) or_grad_fd8(P->n[0], P->n[1], P->n[2], f, g);
+    else or_grad(P->n[0], P->n[1], P->n[2], f, g);
+}
+static void or_div_p(const or_problem *P, const double *v, double *out) {
+    if (P->deriv_fd8) or_div_fd8(P->n[0], P->n[1], P->n[2], v, out);
+    else or_div(P->n[0], P->n[1], P->n[2], v, out);
+}
 
 or_problem *or_create(int n1, int n2, int n3, int nt, double beta, double gamma,
                       const double *m0, const double *m1) {
@@ -518,6 +565,7 @@ or_problem *or_create(int n1, int n2, int n3, int nt, double beta, double gamma,
     P->nt = nt;
     P->beta = beta;
     P->gamma = gamma;
+    P->interp_order = 3;
     size_t N = (size_t)P->N;
     P->m0 = (double *)malloc(sizeof(double) * N);
     P->m1 = (double *)malloc(sizeof(double) * N);
@@ -556,13 +604,13 @@ void or_linearize(or_problem *P, const double *v) {
     int *n = P->n;
     long N = P->N;
     memcpy(P->v, v, sizeof(double) * 3 * N);
-    or_footpoints(n[0], n[1], n[2], P->nt, v, -1, P->dispm);
-    or_footpoints(n[0], n[1], n[2], P->nt, v, +1, P->dispp);
-    or_state(n[0], n[1], n[2], P->nt, P->dispm, P->m0, P->m);
-    for (int j = 0; j <= P->nt; ++j)
-        or_grad(n[0], n[1], n[2], P->m + (long)j * N, P->gm + (long)j * 3 * N);
-    or_div(n[0], n[1], n[2], v, P->d);
-    or_interp_grid(n, P->d, P->dispp, P->dp);
+    const int o = P->interp_order;
+    or_footpoints_o(o, n[0], n[1], n[2], P->nt, v, -1, P->dispm);
+    or_footpoints_o(o, n[0], n[1], n[2], P->nt, v, +1, P->dispp);
+    or_state_o(o, n[0], n[1], n[2], P->nt, P->dispm, P->m0, P->m);
+    for (int j = 0; j <= P->nt; ++j) or_grad_p(P, P->m + (long)j * N, P->gm + (long)j * 3 * N);
+    or_div_p(P, v, P->d);
+    or_interp_grid_o(o, n, P->d, P->dispp, P->dp);
     P->have_lin = 1;
     P->n_pde += 1;
 }
@@ -586,8 +634,8 @@ double or_objective(or_problem *P, const double *v, double *mismatch, double *re
     double *dm = (double *)malloc(sizeof(double) * 3 * N);
     double *mh = (double *)malloc(sizeof(double) * N * (P->nt + 1));
     double *Av = (double *)malloc(sizeof(double) * 3 * N);
-    or_footpoints(n[0], n[1], n[2], P->nt, v, -1, dm);
-    or_state(n[0], n[1], n[2], P->nt, dm, P->m0, mh);
+    or_footpoints_o(P->interp_order, n[0], n[1], n[2], P->nt, v, -1, dm);
+    or_state_o(P->interp_order, n[0], n[1], n[2], P->nt, dm, P->m0, mh);
     const double *m1t = mh + (long)P->nt * N;
     double mis = 0.0;
     for (long i = 0; i < N; ++i) mis += (m1t[i] - P->m1[i]) * (m1t[i] - P->m1[i]);
@@ -615,7 +663,7 @@ void or_gradient(or_problem *P, const double *v, double *g, double *J, double *l
     double *Av = (double *)malloc(sizeof(double) * 3 * (size_t)N);
     const double *mT = P->m + (long)nt * N;
     for (long i = 0; i < N; ++i) lfinal[i] = P->m1[i] - mT[i];
-    or_adjoint(n[0], n[1], n[2], nt, P->dispp, P->d, P->dp, lfinal, lh);
+    or_adjoint_o(P->interp_order, n[0], n[1], n[2], nt, P->dispp, P->d, P->dp, lfinal, lh);
     or_bodyforce(N, nt, lh, P->gm, g);
     or_apply_A(n[0], n[1], n[2], P->beta, P->gamma, v, Av);
     for (long i = 0; i < 3 * N; ++i) g[i] += Av[i];
@@ -642,9 +690,9 @@ int or_matvec(or_problem *P, const double *vt, double *Hvt, double *mt_final, do
     double *lth = (double *)malloc(sizeof(double) * (size_t)N * (nt + 1));
     double *lfinal = (double *)malloc(sizeof(double) * (size_t)N);
     double *Av = (double *)malloc(sizeof(double) * 3 * (size_t)N);
-    or_incstate(n[0], n[1], n[2], nt, P->dispm, P->gm, vt, mth);
+    or_incstate_o(P->interp_order, n[0], n[1], n[2], nt, P->dispm, P->gm, vt, mth);
     for (long i = 0; i < N; ++i) lfinal[i] = -mth[(long)nt * N + i];
-    or_adjoint(n[0], n[1], n[2], nt, P->dispp, P->d, P->dp, lfinal, lth);
+    or_adjoint_o(P->interp_order, n[0], n[1], n[2], nt, P->dispp, P->d, P->dp, lfinal, lth);
     or_bodyforce(N, nt, lth, P->gm, Hvt);
     or_apply_A(n[0], n[1], n[2], P->beta, P->gamma, vt, Av);
     for (long i = 0; i < 3 * N; ++i) Hvt[i] += Av[i];
@@ -734,9 +782,6 @@ long or_pcg_dense(long n, const double *Hm, const double *Pm, const double *b, d
 
 static void or_matvec_cb(void *c, const double *in, double *out) {
     or_matvec((or_problem *)c, in, out, NULL, NULL);
-}
-static void or_precond_cb(void *c, const double *in, double *out) {
-    or_precond((or_problem *)c, in, out);
 }
 
 long or_invh0(int n1, int n2, int n3, double beta0, double gamma, const double *gm,
@@ -865,7 +910,7 @@ void or_det_grad_y(int n1, int n2, int n3, int nt, const double *v, double *det)
     or_footpoints(n1, n2, n3, nt, v, -1, dm);
     for (int j = 0; j < nt; ++j)
         for (int d = 0; d < 3; ++d) {
-            or_interp_grid(n, u + d * N, dm, tmp);
+            or_interp_grid_o(3, n, u + d * N, dm, tmp);
             for (long i = 0; i < N; ++i) u[d * N + i] = tmp[i] + dm[d * N + i];
         }
     /* u in domain units, then J_ab = delta_ab + d_b u_a */
@@ -1009,4 +1054,116 @@ long or_invh0_2l(int n1, int n2, int n3, double beta0, double gamma, const doubl
     }
     free(sf); free(hp); free(rc); free(gmc); free(sc);
     return it;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Parameter continuation in beta (Section 3 "Preconditioning", last          */
+/* paragraph): solve for beta_k = max(beta_target, beta_start * factor^k),    */
+/* k = 0, 1, ..., each level started from the previous velocity; the spectral */
+/* preconditioner is used while beta_k > 5e-1, the selected zero-velocity     */
+/* preconditioner (o->pc) below.  Returns the status of the last level; the   */
+/* report accumulates counts and holds the last level's values.               */
+/* ------------------------------------------------------------------------- */
+int or_solve_continuation(or_problem *P, double *v, double beta_target, double beta_start,
+                          double factor, const or_solve_opts *o, or_solve_report *rep, int *levels) {
+    or_solve_report r, acc;
+    memset(&acc, 0, sizeof(acc));
+    double b = beta_start > beta_target ? beta_start : beta_target;
+    int nlev = 0, status = 0;
+    for (;;) {
+        or_solve_opts ol = *o;
+        if (b > 5e-1) ol.pc = 0;
+        P->beta = b;
+        P->have_lin = 0;
+        status = or_solve(P, v, &ol, &r);
+        ++nlev;
+        acc.n_gn += r.n_gn;
+        acc.n_pcg += r.n_pcg;
+        acc.n_matvec += r.n_matvec;
+        acc.n_precond += r.n_precond;
+        acc.n_inner += r.n_inner;
+        if (nlev == 1) { acc.J0 = r.J0; acc.g0 = r.g0; }
+        acc.J = r.J; acc.g = r.g; acc.grel = r.grel; acc.mismatch_rel = r.mismatch_rel;
+        if (status != 0 || b <= beta_target) break;
+        b = b * factor;
+        if (b <= beta_target * (1.0 + 1e-9)) b = beta_target;  /* land exactly on the target */
+    }
+    acc.status = status;
+    *rep = acc;
+    if (levels) *levels = nlev;
+    return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The paper's GPU discretization options (Sections 4.1, 4.2): eighth-order   */
+/* central finite differences for first derivatives and trilinear             */
+/* interpolation.  Selected per problem with or_set_discretization.           */
+/* ------------------------------------------------------------------------- */
+
+/* d/dx of a periodic line sample by the 8th-order central difference:
+ * f'(x) ~ (1/h) sum_{j=1..4} c_j (f(x + j h) - f(x - j h)),
+ * c = (4/5, -1/5, 4/105, -1/280) */
+static const double or_fd8_c[4] = {4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
+
+void or_grad_fd8(int n1, int n2, int n3, const double *f, double *g) {
+    const int n[3] = {n1, n2, n3};
+    long N = (long)n1 * n2 * n3;
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int i1 = 0; i1 < n1; ++i1)
+        for (int i2 = 0; i2 < n2; ++i2)
+            for (int i3 = 0; i3 < n3; ++i3) {
+                const int ii[3] = {i1, i2, i3};
+                long id = or_idx(n, i1, i2, i3);
+                for (int d = 0; d < 3; ++d) {
+                    double h = 2 * OR_PI / n[d], s = 0.0;
+                    for (int j = 1; j <= 4; ++j) {
+                        int ip[3] = {i1, i2, i3}, im[3] = {i1, i2, i3};
+                        ip[d] = (int)or_wrap(ii[d] + j, n[d]);
+                        im[d] = (int)or_wrap(ii[d] - j, n[d]);
+                        s += or_fd8_c[j - 1] * (f[or_idx(n, ip[0], ip[1], ip[2])] - f[or_idx(n, im[0], im[1], im[2])]);
+                    }
+                    g[d * N + id] = s / h;
+                }
+            }
+}
+
+void or_div_fd8(int n1, int n2, int n3, const double *v, double *out) {
+    long N = (long)n1 * n2 * n3;
+    double *g = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    for (long i = 0; i < N; ++i) out[i] = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        or_grad_fd8(n1, n2, n3, v + d * N, g);
+        for (long i = 0; i < N; ++i) out[i] += g[d * N + i];
+    }
+    free(g);
+}
+
+/* trilinear (first-order Lagrange) periodic interpolation at index point q */
+double or_lerp_at(const int n[3], const double *f, const double q[3]) {
+    long base[3];
+    double t[3];
+    for (int d = 0; d < 3; ++d) {
+        double fl = floor(q[d]);
+        base[d] = (long)fl;
+        t[d] = q[d] - fl;
+    }
+    double s = 0.0;
+    for (int a = 0; a <= 1; ++a)
+        for (int b = 0; b <= 1; ++b)
+            for (int c = 0; c <= 1; ++c) {
+                double w = (a ? t[0] : 1 - t[0]) * (b ? t[1] : 1 - t[1]) * (c ? t[2] : 1 - t[2]);
+                s += w * f[or_idx(n, or_wrap(base[0] + a, n[0]), or_wrap(base[1] + b, n[1]),
+                                  or_wrap(base[2] + c, n[2]))];
+            }
+    return s;
+}
+
+void or_lerp(int n1, int n2, int n3, const double *f, long npts, const double *q1,
+             const double *q2, const double *q3, double *out) {
+    const int n[3] = {n1, n2, n3};
+    #pragma omp parallel for schedule(static)
+    for (long p = 0; p < npts; ++p) {
+        double q[3] = {q1[p], q2[p], q3[p]};
+        out[p] = or_lerp_at(n, f, q);
+    }
 }

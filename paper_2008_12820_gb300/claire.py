@@ -36,6 +36,7 @@ EXPORTED = [
     "claire_apply_A", "claire_interp", "claire_get_field", "claire_solve_opts_default",
     "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
+    "claire_precond_h0", "claire_solve_continuation",
 ]
 
 
@@ -48,7 +49,8 @@ class ClaireError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("max_gn", ctypes.c_int), ("max_pcg", ctypes.c_int), ("fixed_pcg", ctypes.c_int),
                 ("eps_n", ctypes.c_double), ("armijo_c1", ctypes.c_double),
-                ("max_ls", ctypes.c_int)]
+                ("max_ls", ctypes.c_int), ("precond", ctypes.c_int), ("eps_h0", ctypes.c_double),
+                ("max_inner", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -56,7 +58,8 @@ class SolveReport(ctypes.Structure):
                 ("n_precond", ctypes.c_int), ("n_ls", ctypes.c_int), ("status", ctypes.c_int),
                 ("J0", ctypes.c_double), ("J", ctypes.c_double), ("g0", ctypes.c_double),
                 ("g", ctypes.c_double), ("grel", ctypes.c_double),
-                ("mismatch_rel", ctypes.c_double), ("t_grad_ms", ctypes.c_double),
+                ("mismatch_rel", ctypes.c_double), ("n_inner", ctypes.c_long),
+                ("t_grad_ms", ctypes.c_double),
                 ("t_hess_ms", ctypes.c_double), ("t_pc_ms", ctypes.c_double),
                 ("t_obj_ms", ctypes.c_double), ("t_pcg_ms", ctypes.c_double),
                 ("t_total_ms", ctypes.c_double)]
@@ -93,6 +96,9 @@ def load(path: str = LIB_PATH):
         "claire_launch_count": [P, ctypes.POINTER(ctypes.c_long)],
         "claire_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
         "claire_precond_noalloc": [I, I, I, D, D, V, V, V],
+        "claire_precond_h0": [P, V, V, D, I, I, ctypes.POINTER(ctypes.c_int)],
+        "claire_solve_continuation": [P, V, D, D, D, ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(SolveReport), ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -136,6 +142,7 @@ class Report:
     g: float
     grel: float
     mismatch_rel: float
+    n_inner: int
     t_grad_ms: float
     t_hess_ms: float
     t_pc_ms: float
@@ -242,6 +249,15 @@ class Registration:
         self._c("claire_precond", _ptr(r), _ptr(s))
         return s
 
+    def precond_h0(self, r, out=None, tol=1e-3, maxit=500, two_level=False):
+        """InvH0 or its two-level variant: (s, inner iterations) with
+        s = H0^{-1} r at the cached linearization."""
+        s = out if out is not None else self._new(3)
+        it = ctypes.c_int(0)
+        self._c("claire_precond_h0", _ptr(r), _ptr(s), float(tol), int(maxit), int(bool(two_level)),
+                ctypes.byref(it))
+        return s, it.value
+
     def grad(self, f):
         g = self._new(3)
         self._c("claire_grad", _ptr(f), _ptr(g))
@@ -276,13 +292,36 @@ class Registration:
             setattr(o, k, val)
         return o
 
+    PRECOND = {"invA": 0, "invH0": 1, "2LinvH0": 2}
+
     def solve(self, v_inout, check=True, **opts):
+        """opts: max_gn, max_pcg, fixed_pcg, eps_n, armijo_c1, max_ls,
+        precond ("invA" | "invH0" | "2LinvH0" or the enum value), eps_h0, max_inner."""
+        if isinstance(opts.get("precond"), str):
+            opts["precond"] = self.PRECOND[opts["precond"]]
         o = self.default_opts(**opts)
         rep = SolveReport()
         rc = load().claire_solve(self._h, _ptr(v_inout), ctypes.byref(o), ctypes.byref(rep))
         if check and rc not in (CLAIRE_OK,):
             _check(self._h, rc)
         return Report(**rep.as_dict())
+
+    def solve_continuation(self, v_inout, beta_target, beta_start=1.0, factor=0.1, check=True,
+                           **opts):
+        """beta-continuation (InvA while beta > 0.5, opts["precond"] below);
+        returns (report, levels).  The context's beta ends at beta_target."""
+        if isinstance(opts.get("precond"), str):
+            opts["precond"] = self.PRECOND[opts["precond"]]
+        o = self.default_opts(**opts)
+        rep = SolveReport()
+        lev = ctypes.c_int(0)
+        rc = load().claire_solve_continuation(self._h, _ptr(v_inout), float(beta_target),
+                                              float(beta_start), float(factor), ctypes.byref(o),
+                                              ctypes.byref(rep), ctypes.byref(lev))
+        if check and rc != CLAIRE_OK:
+            _check(self._h, rc)
+        self.beta = beta_target
+        return Report(**rep.as_dict()), lev.value
 
     def profile_enable(self, on=True):
         self._c("claire_profile_enable", 1 if on else 0)

@@ -148,7 +148,13 @@ struct claire_ctx {
         const double tp = 6.283185307179586476925286766559;
         return (tp / d.n1) * (tp / d.n2) * (tp / d.n3);
     }
-    SpecParams sp() const { return SpecParams{(float)beta, (float)gamma, (float)(1.0 / (double)d.N)}; }
+    SpecParams sp(double b = -1) const {
+        return SpecParams{(float)(b > 0 ? b : beta), (float)gamma, (float)(1.0 / (double)d.N)};
+    }
+    // beta inside the zero-velocity Hessian H0 (Section 3 "Preconditioning":
+    // floored at 5e-2 so the preconditioner stays effective for small beta)
+    double beta_h0() const { return beta < 5e-2 ? 5e-2 : beta; }
+    float *ih = nullptr;  // inner PCG vectors: r, z, p, q, Ap (5 x 3N)
 
     double fetch(int slot = 0) {
         double h = 0;
@@ -162,8 +168,131 @@ struct claire_ctx {
     }
 
     // ---- operators ------------------------------------------------------
-    void spectral(SpecOp op, const float *in, float *out, const float *add) {
-        spectral_apply(d, ax, op, sp(), in, out, add, spec, st, &prof);
+    void spectral(SpecOp op, const float *in, float *out, const float *add, double b = -1) {
+        spectral_apply(d, ax, op, sp(b), in, out, add, spec, st, &prof);
+    }
+
+    // FFT resources of one grid (the context's grid, or its half-resolution
+    // grid for the two-level preconditioner)
+    struct Grid {
+        Dims d{};
+        const FftPlan *ax = nullptr;
+        float2 *spec = nullptr;
+    };
+    Grid fine() const { return Grid{d, ax, spec}; }
+
+    // half-resolution grid of the two-level preconditioner, made on first use
+    struct Coarse {
+        Dims d{};
+        FftPlan ax[3]{};
+        float2 *spec = nullptr;
+        float *gm = nullptr, *r = nullptr, *s = nullptr, *work = nullptr;
+        bool gm_valid = false;
+        bool ready = false;
+    } co;
+
+    void make_coarse() {
+        if (co.ready) return;
+        const int ns[3] = {d.n1 / 2, d.n2 / 2, d.n3 / 2};
+        for (int a = 0; a < 3; ++a)
+            if ((2 * ns[a] != (a == 0 ? d.n1 : a == 1 ? d.n2 : d.n3)) || !valid_n(ns[a]))
+                throw Error(CLAIRE_ERR_ARG, "two-level preconditioner needs even grid sizes >= 8 whose halves are valid FFT lengths");
+        co.d.n1 = ns[0];
+        co.d.n2 = ns[1];
+        co.d.n3 = ns[2];
+        co.d.N = (long long)ns[0] * ns[1] * ns[2];
+        co.d.h3 = ns[2] / 2 + 1;
+        co.d.p3 = (co.d.h3 + 3) / 4 * 4;
+        for (int a = 0; a < 3; ++a) {
+            co.ax[a] = make_plan(ns[a]);
+            std::vector<float2> tw(ns[a]);
+            for (int t = 0; t < ns[a]; ++t) {
+                const double ang = 6.283185307179586476925286766559 * (double)t / (double)ns[a];
+                tw[t] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+            }
+            float2 *dtw = (float2 *)alloc_bytes(ns[a] * sizeof(float2));
+            CK(cudaMemcpy(dtw, tw.data(), ns[a] * sizeof(float2), cudaMemcpyHostToDevice));
+            co.ax[a].tw = dtw;
+        }
+        const size_t Nc = co.d.N;
+        co.spec = (float2 *)alloc_bytes((size_t)3 * ns[0] * ns[1] * co.d.p3 * sizeof(float2));
+        co.gm = alloc_f(3 * Nc);
+        co.r = alloc_f(3 * Nc);
+        co.s = alloc_f(3 * Nc);
+        co.work = alloc_f(15 * Nc);
+        co.ready = true;
+    }
+
+    // s = H0^{-1} r on grid g by PCG preconditioned with (beta0 A)^{-1},
+    // x0 = 0, stop at ||r_i|| <= tol ||r_0|| (or after exactly maxit
+    // iterations if fixed); H0 = beta0 A + gm (x) gm.  beta0 A p is carried by
+    // the same recurrence as in the outer PCG.  work: 5 vectors of g.  Uses
+    // result slots dres[4..7] so the caller's residual sums survive.
+    int invh0_on(const Grid &g, const float *gm, const float *r, float *s, double tol, int maxit,
+                 bool fixed, float *work) {
+        const long long N = g.d.N, n3 = 3 * N;
+        float *ir = work, *iz = ir + n3, *ip = iz + n3, *iq = ip + n3, *iAp = iq + n3;
+        const double b0 = beta_h0();
+        const SpecParams spb{(float)b0, (float)gamma, (float)(1.0 / (double)N)};
+        double *slot = dres + 4;
+        CK(cudaMemsetAsync(s, 0, n3 * sizeof(float), st));
+        CK(cudaMemcpyAsync(ir, r, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        launch_stats(ir, N, partial, slot, st, &prof);
+        const double r0 = std::sqrt(fetch(4));
+        if (!(r0 > 0)) return 0;
+        spectral_apply(g.d, g.ax, OP_AINV, spb, ir, iz, nullptr, g.spec, st, &prof);
+        launch_pcg_dir(ip, iAp, iz, ir, slot + 1, nullptr, 0.f, N, true, st, &prof);
+        double rz = dot(ir, iz, n3);
+        int it = 0;
+        while (it < maxit) {
+            launch_h0_apply(iq, iAp, gm, ip, N, st, &prof);
+            const double pq = dot(ip, iq, n3);
+            if (!(pq > 0)) break;
+            launch_pcg_update(s, nullptr, ir, ip, iAp, iq, (float)(rz / pq), N, partial, slot, st, &prof);
+            ++it;
+            const double rn = std::sqrt(fetch(4));
+            if (!fixed && rn <= tol * r0) break;
+            if (it >= maxit) break;
+            spectral_apply(g.d, g.ax, OP_AINV, spb, ir, iz, nullptr, g.spec, st, &prof);
+            const double rz_new = dot(ir, iz, n3);
+            const float bb = (float)(rz_new / rz);
+            rz = rz_new;
+            launch_pcg_dir(ip, iAp, iz, ir, slot + 1, nullptr, bb, N, false, st, &prof);
+        }
+        check_launch("invh0");
+        return it;
+    }
+
+    // InvH0 (Section 3 "Preconditioning") with grad m(1) of the linearization
+    int invh0(const float *r, float *s, double tol, int maxit, bool fixed) {
+        if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
+        if (!ih) ih = alloc_f((size_t)15 * d.N);
+        return invh0_on(fine(), hist(gmhist, nt, 3), r, s, tol, maxit, fixed, ih);
+    }
+
+    // two-level InvH0 (Algorithm 2): restrict r and grad m(1) spectrally to the
+    // half grid, solve there, prolong, and add the high-pass part of
+    // (beta0 A)^{-1} r -- the last two in one pass over the fine spectrum
+    int invh0_2l(const float *r, float *s, double tol, int maxit, bool fixed) {
+        if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
+        make_coarse();
+        const Grid cg{co.d, co.ax, co.spec};
+        const float c2f = (float)((double)d.N / (double)co.d.N), f2c = 1.f / c2f;
+        if (!co.gm_valid) {
+            spectral_forward3(d, ax, hist(gmhist, nt, 3), spec, st, &prof);
+            launch_spec_restrict(d, spec, co.d, co.spec, f2c, st, &prof);
+            spectral_inverse3(co.d, co.ax, co.spec, co.gm, (float)(1.0 / (double)co.d.N), st, &prof);
+            co.gm_valid = true;
+        }
+        spectral_forward3(d, ax, r, spec, st, &prof);
+        launch_spec_restrict(d, spec, co.d, co.spec, f2c, st, &prof);
+        spectral_inverse3(co.d, co.ax, co.spec, co.r, (float)(1.0 / (double)co.d.N), st, &prof);
+        const int it = invh0_on(cg, co.gm, co.r, co.s, tol, maxit, fixed, co.work);
+        spectral_forward3(co.d, co.ax, co.s, co.spec, st, &prof);
+        launch_spec_twolevel(d, spec, co.d, co.spec, c2f, (float)beta_h0(), (float)gamma, st, &prof);
+        spectral_inverse3(d, ax, spec, s, (float)(1.0 / (double)d.N), st, &prof);
+        check_launch("invh0_2l");
+        return it;
     }
 
     void linearize(const float *v) {
@@ -179,6 +308,7 @@ struct claire_ctx {
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
         have_lin = true;
+        co.gm_valid = false;
     }
 
     // adjoint solve + body force + beta A v; J into *J when asked.  Av, if
@@ -462,6 +592,19 @@ int claire_precond(claire_ctx *ctx, const float *r, float *s) {
     API_END(ctx)
 }
 
+int claire_precond_h0(claire_ctx *ctx, const float *r, float *s, double tol, int maxit,
+                      int two_level, int *iterations) {
+    API_BEGIN(ctx)
+    need(r, "r");
+    need(s, "s");
+    if (r == s) throw Error(CLAIRE_ERR_ARG, "r and s may not alias");
+    if (maxit < 1 || !(tol >= 0)) throw Error(CLAIRE_ERR_ARG, "need maxit >= 1 and tol >= 0");
+    const int it = two_level ? ctx->invh0_2l(r, s, tol, maxit, tol == 0.0)
+                             : ctx->invh0(r, s, tol, maxit, tol == 0.0);
+    if (iterations) *iterations = it;
+    API_END(ctx)
+}
+
 int claire_grad(claire_ctx *ctx, const float *f, float *g) {
     API_BEGIN(ctx)
     need(f, "f");
@@ -536,6 +679,9 @@ void claire_solve_opts_default(claire_solve_opts *o) {
     o->eps_n = 5e-2;
     o->armijo_c1 = 1e-4;
     o->max_ls = 12;
+    o->precond = CLAIRE_PC_INVA;
+    o->eps_h0 = 1e-3;
+    o->max_inner = 500;
 }
 
 namespace {
@@ -560,12 +706,12 @@ struct EvTimer {
 };
 }  // namespace
 
-int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, claire_solve_report *rep_out) {
-    API_BEGIN(ctx)
-    need(v, "v_inout");
-    claire_solve_opts o;
-    if (opts) o = *opts; else claire_solve_opts_default(&o);
-    if (o.max_gn < 0 || o.max_pcg < 1 || o.fixed_pcg < 0 || !(o.eps_n >= 0) || o.max_ls < 0)
+// One Gauss-Newton-Krylov solve (Algorithm 1) at the context's beta; returns
+// CLAIRE_OK, CLAIRE_ERR_LINESEARCH or CLAIRE_ERR_NONFINITE (v then holds the
+// last accepted iterate); other failures throw.
+static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, claire_solve_report *rep_out) {
+    if (o.max_gn < 0 || o.max_pcg < 1 || o.fixed_pcg < 0 || !(o.eps_n >= 0) || o.max_ls < 0 ||
+        o.precond < CLAIRE_PC_INVA || o.precond > CLAIRE_PC_2LINVH0 || !(o.eps_h0 > 0) || o.max_inner < 1)
         throw Error(CLAIRE_ERR_ARG, "invalid solve options");
     claire_solve_report rep;
     std::memset(&rep, 0, sizeof(rep));
@@ -615,13 +761,24 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
             const double r0 = std::sqrt(ctx->fetch(0));
             const int maxit = o.fixed_pcg > 0 ? o.fixed_pcg : o.max_pcg;
             int it = 0;
-            if (r0 > 0) {
-                {
-                    EvTimer t(st, &rep.t_pc_ms);
-                    ctx->spectral(OP_AINV, r, z, nullptr);
-                }
+            // preconditioner z = M r; Az = beta*A z (NULL: the recurrence holds)
+            auto apply_pc = [&]() -> const float * {
+                EvTimer t(st, &rep.t_pc_ms);
                 rep.n_precond++;
-                launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, 0.f, N, true, st, &ctx->prof);
+                if (o.precond == CLAIRE_PC_INVA) {
+                    ctx->spectral(OP_AINV, r, z, nullptr);
+                    return nullptr;
+                }
+                if (o.precond == CLAIRE_PC_INVH0)
+                    rep.n_inner += ctx->invh0(r, z, o.eps_h0 * epsk, o.max_inner, false);
+                else
+                    rep.n_inner += ctx->invh0_2l(r, z, o.eps_h0 * epsk, o.max_inner, false);
+                ctx->spectral(OP_A, z, q, nullptr);
+                return q;
+            };
+            if (r0 > 0) {
+                const float *Az = apply_pc();
+                launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, Az, 0.f, N, true, st, &ctx->prof);
                 double rz = ctx->dot(r, z, n3);
                 while (it < maxit) {
                     {
@@ -647,15 +804,11 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
                     const double rn = std::sqrt(ctx->fetch(0));
                     if (o.fixed_pcg == 0 && rn <= epsk * r0) break;
                     if (it >= maxit) break;
-                    {
-                        EvTimer t(st, &rep.t_pc_ms);
-                        ctx->spectral(OP_AINV, r, z, nullptr);
-                    }
-                    rep.n_precond++;
+                    const float *Az = apply_pc();
                     const double rz_new = ctx->dot(r, z, n3);
                     const double beta = rz_new / rz;
                     rz = rz_new;
-                    launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, (float)beta, N, false, st, &ctx->prof);
+                    launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, Az, (float)beta, N, false, st, &ctx->prof);
                 }
             }
             rep.n_pcg += it;
@@ -721,10 +874,72 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
         rep.t_total_ms = ms;
     }
     if (rep_out) *rep_out = rep;
-    if (status != CLAIRE_OK) {
+    if (status != CLAIRE_OK)
         ctx->err = status == CLAIRE_ERR_LINESEARCH ? "line search failed" : "non-finite gradient";
-        return status;
+    return status;
+}
+
+int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, claire_solve_report *rep_out) {
+    API_BEGIN(ctx)
+    need(v, "v_inout");
+    claire_solve_opts o;
+    if (opts) o = *opts; else claire_solve_opts_default(&o);
+    const int status = do_solve(ctx, v, o, rep_out);
+    if (status != CLAIRE_OK) return status;
+    API_END(ctx)
+}
+
+int claire_solve_continuation(claire_ctx *ctx, float *v, double beta_target, double beta_start,
+                              double factor, const claire_solve_opts *opts,
+                              claire_solve_report *rep_out, int *levels) {
+    API_BEGIN(ctx)
+    need(v, "v_inout");
+    check_params(beta_target, ctx->gamma);
+    if (!(beta_start > 0) || !std::isfinite(beta_start) || !(factor > 0 && factor < 1))
+        throw Error(CLAIRE_ERR_ARG, "need beta_start > 0 and 0 < factor < 1");
+    claire_solve_opts o;
+    if (opts) o = *opts; else claire_solve_opts_default(&o);
+    claire_solve_report acc, r;
+    std::memset(&acc, 0, sizeof(acc));
+    double b = beta_start > beta_target ? beta_start : beta_target;
+    int nlev = 0, status = CLAIRE_OK;
+    for (;;) {
+        claire_solve_opts ol = o;
+        if (b > 5e-1) ol.precond = CLAIRE_PC_INVA;  // spectral preconditioner for large beta
+        ctx->beta = b;
+        ctx->have_lin = false;
+        std::memset(&r, 0, sizeof(r));
+        status = do_solve(ctx, v, ol, &r);
+        ++nlev;
+        acc.n_gn += r.n_gn;
+        acc.n_pcg += r.n_pcg;
+        acc.n_matvec += r.n_matvec;
+        acc.n_precond += r.n_precond;
+        acc.n_ls += r.n_ls;
+        acc.n_inner += r.n_inner;
+        acc.t_grad_ms += r.t_grad_ms;
+        acc.t_hess_ms += r.t_hess_ms;
+        acc.t_pc_ms += r.t_pc_ms;
+        acc.t_obj_ms += r.t_obj_ms;
+        acc.t_pcg_ms += r.t_pcg_ms;
+        acc.t_total_ms += r.t_total_ms;
+        if (nlev == 1) {
+            acc.J0 = r.J0;
+            acc.g0 = r.g0;
+        }
+        acc.J = r.J;
+        acc.g = r.g;
+        acc.grel = r.grel;
+        acc.mismatch_rel = r.mismatch_rel;
+        if (status != CLAIRE_OK || b <= beta_target) break;
+        b *= factor;
+        if (b <= beta_target * (1.0 + 1e-9)) b = beta_target;  // land exactly on the target
     }
+    acc.status = status;
+    ctx->beta = beta_target;
+    if (rep_out) *rep_out = acc;
+    if (levels) *levels = nlev;
+    if (status != CLAIRE_OK) return status;
     API_END(ctx)
 }
 

@@ -40,7 +40,9 @@ struct Dims {
 };
 
 // spectral operators applied in the fused x1 pass
-enum SpecOp { OP_GRAD = 0, OP_DIV = 1, OP_A = 2, OP_AINV = 3 };
+enum SpecOp { OP_GRAD = 0, OP_DIV = 1, OP_A = 2, OP_AINV = 3,
+              // three components, x1 pass forward only / scale then inverse only
+              OP_X1FWD = 4, OP_X1INV = 5 };
 
 // epilogues of the inverse x3 pass
 enum C2rEpi { EPI_STORE = 0, EPI_ADD = 1 };
@@ -55,6 +57,22 @@ struct SpecParams {
 void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParams &sp,
                     const float *in, float *out, const float *add, float2 *spec,
                     cudaStream_t st, Profiler *prof);
+
+// forward 3D transform of three components into spec (unnormalized), and the
+// inverse from spec (scaled by sp.scale) into real fields; spec is consumed
+void spectral_forward3(const Dims &d, const FftPlan *ax, const float *in, float2 *spec,
+                       cudaStream_t st, Profiler *prof);
+void spectral_inverse3(const Dims &d, const FftPlan *ax, float2 *spec, float *out, float scale,
+                       cudaStream_t st, Profiler *prof);
+// restriction of a fine half spectrum to a coarse grid (modes |k_d| < nc_d/2,
+// times scale; others zero) for three components
+void launch_spec_restrict(const Dims &df, const float2 *specf, const Dims &dc, float2 *specc,
+                          float scale, cudaStream_t st, Profiler *prof);
+// two-level combination on the fine spectrum, in place: modes the coarse grid
+// holds take scale * coarse spectrum, the others become (beta0 A)^{-1} of
+// themselves (the high-pass part of (beta0 A)^{-1} r)
+void launch_spec_twolevel(const Dims &df, float2 *specf, const Dims &dc, const float2 *specc,
+                          float scale, float beta0, float gamma, cudaStream_t st, Profiler *prof);
 
 // ------------------------------------------------------------ transport ----
 // Foot points and the per-axis [min, max] floor range of each displacement
@@ -106,9 +124,14 @@ void launch_stats(const float *r, long long N, double *partial, double *dev_out,
 void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
                        cudaStream_t st, Profiler *prof);
-// p = z + b p; Ap = (r - mean r) + b Ap (rsum: device component sums of r)
+// p = z + b p; Ap = (r - mean r) + b Ap (rsum: device component sums of r);
+// with Az given (beta*A z), Ap = Az + b Ap instead.  x += a p skips Ax if NULL.
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
-                    float b, long long N, bool init, cudaStream_t st, Profiler *prof);
+                    const float *Az, float b, long long N, bool init, cudaStream_t st,
+                    Profiler *prof);
+// q = Ap + gm (gm . p): the zero-velocity Hessian given beta0*A p
+void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
+                     cudaStream_t st, Profiler *prof);
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
 
 // ------------------------------------------------------------ profiler ----

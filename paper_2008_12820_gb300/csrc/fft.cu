@@ -339,6 +339,7 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
     constexpr int NIN = (OP == OP_GRAD) ? 1 : 3;
     constexpr int NOUT = (OP == OP_DIV) ? 1 : 3;
     constexpr int NB = NIN > NOUT ? NIN : NOUT;
+    constexpr bool FWD = OP != OP_X1INV, INV = OP != OP_X1FWD;
     extern __shared__ float2 sm[];
     const int n1 = Fft<N>::size(p1);
     const int tile = n1 * TK;
@@ -358,10 +359,12 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
         }
     }
     __syncthreads();
+    if (FWD) {
 #pragma unroll
-    for (int c = 0; c < NIN; ++c) {
-        float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, -1.f);
-        if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
+        for (int c = 0; c < NIN; ++c) {
+            float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, -1.f);
+            if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
+        }
     }
     // multiplier at (k1, k2, k3)
     const float k2 = wavenumber(i2, n2), k2d = wavenumber_d1(i2, n2);
@@ -371,7 +374,15 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
         const float k1 = wavenumber(e, n1), k1d = wavenumber_d1(e, n1);
         const float k3 = (float)i3, k3d = ((n3 & 1) == 0 && 2 * i3 == n3) ? 0.f : k3;
         const int id = e * TK + l;
-        if (OP == OP_GRAD) {
+        if (OP == OP_X1FWD) {
+            // forward only: no multiplier
+        } else if (OP == OP_X1INV) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 f = buf[c][id];
+                buf[c][id] = make_float2(f.x * sp.scale, f.y * sp.scale);
+            }
+        } else if (OP == OP_GRAD) {
             const float2 f = buf[0][id];
             // i k_d f * scale
             buf[0][id] = make_float2(-k1d * f.y * sp.scale, k1d * f.x * sp.scale);
@@ -413,10 +424,12 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
         }
     }
     __syncthreads();
+    if (INV) {
 #pragma unroll
-    for (int c = 0; c < NOUT; ++c) {
-        float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, +1.f);
-        if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
+        for (int c = 0; c < NOUT; ++c) {
+            float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, +1.f);
+            if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
+        }
     }
     for (int c = 0; c < NOUT; ++c) {
         for (int t = threadIdx.x; t < tile; t += blockDim.x) {
@@ -637,6 +650,67 @@ void c2r_x3(const Dims &d, const FftPlan &p, const float2 *in, float *out, const
     }
 }
 
+// ------------------------------------------------------ grid resampling ---
+__device__ __forceinline__ bool in_coarse_band(float k, int nc) { return 2.f * fabsf(k) < (float)nc; }
+__device__ __forceinline__ int index_of(float k, int n) { return k < 0.f ? n + (int)k : (int)k; }
+
+// thread per coarse (component, i1, i2, k3)
+__global__ void k_spec_restrict(const float2 *__restrict__ sf, Dims df, float2 *__restrict__ sc,
+                                Dims dc, float scale) {
+    const long long per_c = (long long)dc.n1 * dc.n2 * dc.h3;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 3 * per_c) return;
+    const int c = (int)(t / per_c);
+    long long r = t - c * per_c;
+    const int k3 = (int)(r % dc.h3);
+    r /= dc.h3;
+    const int i2 = (int)(r % dc.n2), i1 = (int)(r / dc.n2);
+    const float k1 = wavenumber(i1, dc.n1), k2 = wavenumber(i2, dc.n2);
+    float2 v = make_float2(0.f, 0.f);
+    if (in_coarse_band(k1, dc.n1) && in_coarse_band(k2, dc.n2) && in_coarse_band((float)k3, dc.n3)) {
+        const long long src = (((long long)c * df.n1 + index_of(k1, df.n1)) * df.n2 + index_of(k2, df.n2)) *
+                              df.p3 + k3;
+        const float2 f = sf[src];
+        v = make_float2(f.x * scale, f.y * scale);
+    }
+    sc[(((long long)c * dc.n1 + i1) * dc.n2 + i2) * dc.p3 + k3] = v;
+}
+
+// thread per fine (i1, i2, k3), all three components (the inverse couples them)
+__global__ void k_spec_twolevel(float2 *__restrict__ sf, Dims df, const float2 *__restrict__ sc,
+                                Dims dc, float scale, float beta0, float gamma) {
+    const long long per_c = (long long)df.n1 * df.n2 * df.h3;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= per_c) return;
+    long long r = t;
+    const int k3i = (int)(r % df.h3);
+    r /= df.h3;
+    const int i2 = (int)(r % df.n2), i1 = (int)(r / df.n2);
+    const long long cs = (long long)df.n1 * df.n2 * df.p3;
+    const long long id = ((long long)i1 * df.n2 + i2) * df.p3 + k3i;
+    const float k1 = wavenumber(i1, df.n1), k2 = wavenumber(i2, df.n2), k3 = (float)k3i;
+    if (in_coarse_band(k1, dc.n1) && in_coarse_band(k2, dc.n2) && in_coarse_band(k3, dc.n3)) {
+        const long long ccs = (long long)dc.n1 * dc.n2 * dc.p3;
+        const long long src = ((long long)index_of(k1, dc.n1) * dc.n2 + index_of(k2, dc.n2)) * dc.p3 + k3i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 f = sc[c * ccs + src];
+            sf[c * cs + id] = make_float2(f.x * scale, f.y * scale);
+        }
+    } else {
+        // (beta0 A)^{-1} by Sherman-Morrison (never k = 0 here)
+        const float k1d = wavenumber_d1(i1, df.n1), k2d = wavenumber_d1(i2, df.n2);
+        const float k3d = ((df.n3 & 1) == 0 && 2 * k3i == df.n3) ? 0.f : k3;
+        const float kk = k1 * k1 + k2 * k2 + k3 * k3, kd2 = k1d * k1d + k2d * k2d + k3d * k3d;
+        const float bk = beta0 * kk, diag = 1.f / bk, coup = -gamma * diag / (bk + gamma * kd2);
+        const float2 a = sf[id], b = sf[cs + id], c = sf[2 * cs + id];
+        const float2 kv = make_float2(k1d * a.x + k2d * b.x + k3d * c.x, k1d * a.y + k2d * b.y + k3d * c.y);
+        sf[id] = make_float2(diag * a.x + coup * k1d * kv.x, diag * a.y + coup * k1d * kv.y);
+        sf[cs + id] = make_float2(diag * b.x + coup * k2d * kv.x, diag * b.y + coup * k2d * kv.y);
+        sf[2 * cs + id] = make_float2(diag * c.x + coup * k3d * kv.x, diag * c.y + coup * k3d * kv.y);
+    }
+}
+
 }  // namespace
 
 void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParams &sp,
@@ -660,7 +734,8 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
             case OP_GRAD: mul_x1_op<OP_GRAD>(d, ax[0], spec, sp, st); break;
             case OP_DIV: mul_x1_op<OP_DIV>(d, ax[0], spec, sp, st); break;
             case OP_A: mul_x1_op<OP_A>(d, ax[0], spec, sp, st); break;
-            default: mul_x1_op<OP_AINV>(d, ax[0], spec, sp, st); break;
+            case OP_AINV: mul_x1_op<OP_AINV>(d, ax[0], spec, sp, st); break;
+            default: break;
         }
     }
     {
@@ -671,6 +746,59 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
         ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, nout * (R + C + (add ? R : 0.0)));
         c2r_x3(d, ax[2], spec, out, add, nout, st);
     }
+}
+
+}  // namespace claire
+
+namespace claire {
+
+void spectral_forward3(const Dims &d, const FftPlan *ax, const float *in, float2 *spec,
+                       cudaStream_t st, Profiler *prof) {
+    const double R = 4.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_R2C, st, 3 * (R + C));
+        r2c_x3(d, ax[2], in, spec, 3, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_C2C, st, 3 * 2 * C);
+        c2c_x2(d, ax[1], spec, 3, -1.f, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, 6 * C);
+        mul_x1_op<OP_X1FWD>(d, ax[0], spec, SpecParams{0.f, 0.f, 1.f}, st);
+    }
+}
+
+void spectral_inverse3(const Dims &d, const FftPlan *ax, float2 *spec, float *out, float scale,
+                       cudaStream_t st, Profiler *prof) {
+    const double R = 4.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, 6 * C);
+        mul_x1_op<OP_X1INV>(d, ax[0], spec, SpecParams{0.f, 0.f, scale}, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_C2C, st, 3 * 2 * C);
+        c2c_x2(d, ax[1], spec, 3, +1.f, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, 3 * (R + C));
+        c2r_x3(d, ax[2], spec, out, nullptr, 3, st);
+    }
+}
+
+void launch_spec_restrict(const Dims &df, const float2 *specf, const Dims &dc, float2 *specc,
+                          float scale, cudaStream_t st, Profiler *prof) {
+    const long long n = 3LL * dc.n1 * dc.n2 * dc.h3;
+    ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, 16.0 * n);
+    k_spec_restrict<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(specf, df, specc, dc, scale);
+}
+
+void launch_spec_twolevel(const Dims &df, float2 *specf, const Dims &dc, const float2 *specc,
+                          float scale, float beta0, float gamma, cudaStream_t st, Profiler *prof) {
+    const long long n = (long long)df.n1 * df.n2 * df.h3;
+    ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, 48.0 * n);
+    k_spec_twolevel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(specf, df, specc, dc, scale, beta0,
+                                                                 gamma);
 }
 
 }  // namespace claire

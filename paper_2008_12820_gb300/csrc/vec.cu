@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float 
     for (int c = 0; c < 3; ++c)
         for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
             x[i] = fmaf(alpha, p[i], x[i]);
-            Ax[i] = fmaf(alpha, Ap[i], Ax[i]);
+            if (Ax) Ax[i] = fmaf(alpha, Ap[i], Ax[i]);
             const float ri = fmaf(-alpha, q[i], r[i]);
             r[i] = ri;
             rr.add_prod(ri, ri);
@@ -213,16 +213,18 @@ __global__ void __launch_bounds__(RT) k_finalize4(const double *__restrict__ par
 // since beta*A z = r - mean(r) for z = (beta*A)^{-1} r (the inverse is the
 // identity on the zero wavenumber, where beta*A vanishes).  init: b = 0 and
 // the old p, Ap are not read.  rsum: device sums of the components of r.
+// With a preconditioner other than (beta*A)^{-1}, Az (= beta*A z, applied
+// spectrally by the caller) replaces r - mean r.
 __global__ void __launch_bounds__(RT) k_pcg_dir(float *__restrict__ p, float *__restrict__ Ap,
                                                 const float *__restrict__ z, const float *__restrict__ r,
-                                                const double *__restrict__ rsum, float b, long long N,
-                                                int init) {
+                                                const double *__restrict__ rsum, const float *__restrict__ Az,
+                                                float b, long long N, int init) {
     const long long stride = (long long)gridDim.x * RT;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float mean = (float)(rsum[c] / (double)N);
+        const float mean = Az ? 0.f : (float)(rsum[c] / (double)N);
         for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
-            const float ar = r[i] - mean;
+            const float ar = Az ? Az[i] : r[i] - mean;
             if (init) {
                 p[i] = z[i];
                 Ap[i] = ar;
@@ -231,6 +233,20 @@ __global__ void __launch_bounds__(RT) k_pcg_dir(float *__restrict__ p, float *__
                 Ap[i] = fmaf(b, Ap[i], ar);
             }
         }
+    }
+}
+
+// zero-velocity Hessian applied to p given beta0*A p:  q = Ap + gm (gm . p)
+__global__ void __launch_bounds__(RT) k_h0_apply(float *__restrict__ q, const float *__restrict__ Ap,
+                                                 const float *__restrict__ gm, const float *__restrict__ p,
+                                                 long long N) {
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
+        const float g1 = gm[i], g2 = gm[N + i], g3 = gm[2 * N + i];
+        const float gp = g1 * p[i] + g2 * p[N + i] + g3 * p[2 * N + i];
+        q[i] = fmaf(g1, gp, Ap[i]);
+        q[N + i] = fmaf(g2, gp, Ap[N + i]);
+        q[2 * N + i] = fmaf(g3, gp, Ap[2 * N + i]);
     }
 }
 
@@ -295,16 +311,23 @@ void launch_stats(const float *r, long long N, double *partial, double *dev_out,
 void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
                        cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * 36, 2);
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (Ax ? 36 : 24), 2);
     const int nb = blocks_for(N);
     k_pcg_update<<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial);
     k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
-                    float b, long long N, bool init, cudaStream_t st, Profiler *prof) {
+                    const float *Az, float b, long long N, bool init, cudaStream_t st,
+                    Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (init ? 16 : 24));
-    k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, b, N, init ? 1 : 0);
+    k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0);
+}
+
+void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
+                     cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 48.0 * N);
+    k_h0_apply<<<blocks_for(N), RT, 0, st>>>(q, Ap, gm, p, N);
 }
 
 }  // namespace claire

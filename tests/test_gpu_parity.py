@@ -355,3 +355,104 @@ def test_full_size_integer_shift_is_exact(claire, big):
         mT = host(reg.field("state", nt))
         ref = np.roll(w["m0"], shift=tuple(nt * si for si in s), axis=(0, 1, 2))
         assert rel(mT, ref) < 1e-6
+
+
+# ------------------------------------------------ InvH0 preconditioner -----
+
+@pytest.mark.parametrize("shape,beta", [((32, 32, 32), 1e-2), ((48, 40, 36), 0.2)])
+def test_invh0_fixed_iterations(claire, shape, beta):
+    """InvH0 (Section 3 "Preconditioning", Algorithm 2) at the linearization
+    of a nonzero velocity: 8 inner PCG iterations on each side (tol = 0),
+    beta floored at 5e-2 inside H0."""
+    nt, gamma = 4, 1.0
+    m0, m1, v = make_problem(shape, nt)
+    rng = np.random.default_rng(5)
+    r = synth.smooth_direction(shape, 6, kmax=8) + 0.1 * rng.standard_normal((3,) + shape).astype(np.float32)
+    P = O.Problem(m0, m1, nt, beta, gamma)
+    P.linearize(v)
+    gm1 = P.grad_state_history()[nt]
+    ref, it_o = O.invh0(r, gm1, max(beta, 5e-2), gamma, 0.0, maxit=8)
+    assert it_o == 8
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        reg.linearize(dev(v))
+        s, it = reg.precond_h0(dev(r), tol=0.0, maxit=8)
+        assert it == 8
+        assert rel(host(s), ref) < TOL_SOLVE, rel(host(s), ref)
+
+
+def test_solve_with_invh0_matches_oracle(claire):
+    """Full solve with the InvH0 preconditioner: same GN count, objective and
+    relative gradient as the oracle's solve with the same preconditioner."""
+    w = synth.workload("sin32")
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    P = O.Problem(w["m0"], w["m1"], nt, beta, gamma)
+    vo, ro = P.solve(np.zeros((3,) + shape), pc="invH0", eps_h0=1e-3)
+    _, ra = P.solve(np.zeros((3,) + shape), pc="invA")
+    assert ro.n_pcg < ra.n_pcg
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        v = torch.zeros((3,) + shape, device="cuda")
+        rep = reg.solve(v, precond="invH0", eps_h0=1e-3)
+        assert rep.status == 0 and rep.grel <= 5e-2
+        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg
+        assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
+        assert abs(rep.grel - ro.grel) / ro.grel < 1e-3
+        assert rel(host(v), vo) < 1e-3
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 40, 36)])
+def test_invh0_two_level_fixed_iterations(claire, shape):
+    """Two-level InvH0 (Algorithm 2): spectral restriction of r and grad m(1)
+    to the half grid, 8 coarse PCG iterations, prolongation plus the
+    high-pass part of (beta0 A)^{-1} r."""
+    nt, beta, gamma = 4, 1e-2, 1.0
+    m0, m1, v = make_problem(shape, nt)
+    rng = np.random.default_rng(6)
+    r = synth.smooth_direction(shape, 8, kmax=8) + 0.1 * rng.standard_normal((3,) + shape).astype(np.float32)
+    P = O.Problem(m0, m1, nt, beta, gamma)
+    P.linearize(v)
+    gm1 = P.grad_state_history()[nt]
+    ref, it_o = O.invh0(r, gm1, 5e-2, gamma, 0.0, maxit=8, two_level=True)
+    assert it_o == 8
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        reg.linearize(dev(v))
+        for _ in range(2):  # the second call reuses the cached coarse grad m
+            s, it = reg.precond_h0(dev(r), tol=0.0, maxit=8, two_level=True)
+            assert it == 8
+            assert rel(host(s), ref) < TOL_SOLVE, rel(host(s), ref)
+
+
+def test_solve_with_two_level_invh0(claire):
+    w = synth.workload("sin32")
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    P = O.Problem(w["m0"], w["m1"], nt, beta, gamma)
+    vo, ro = P.solve(np.zeros((3,) + shape), pc="2LinvH0", eps_h0=1e-3)
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        v = torch.zeros((3,) + shape, device="cuda")
+        rep = reg.solve(v, precond="2LinvH0", eps_h0=1e-3)
+        assert rep.status == 0 and rep.grel <= 5e-2
+        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg
+        assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
+        assert rel(host(v), vo) < 1e-3
+
+
+def test_beta_continuation_matches_oracle(claire):
+    """beta-continuation 1 -> 0.1 -> 0.01 with InvA above 0.5 and InvH0 below
+    (Section 3 "Preconditioning", last paragraph)."""
+    w = synth.workload("sin32")
+    shape, nt, gamma = w["shape"], w["nt"], w["gamma"]
+    P = O.Problem(w["m0"], w["m1"], nt, 1.0, gamma)
+    vo, ro, lev_o = P.solve_continuation(np.zeros((3,) + shape), 1e-2, beta_start=1.0, factor=0.1,
+                                         pc="invH0")
+    with claire.Registration(shape, nt, 1.0, gamma) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        v = torch.zeros((3,) + shape, device="cuda")
+        rep, lev = reg.solve_continuation(v, 1e-2, beta_start=1.0, factor=0.1, precond="invH0")
+        assert lev == lev_o == 3
+        assert rep.status == 0 and rep.grel <= 5e-2
+        assert rep.n_gn == ro.n_gn
+        assert abs(rep.J - ro.J) / abs(ro.J) < 1e-3
+        assert rel(host(v), vo) < 1e-2

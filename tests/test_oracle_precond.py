@@ -91,3 +91,22 @@ def test_zero_velocity_preconditioners_cut_outer_pcg_iterations():
         assert r.status == 0 and r.grel <= 5e-2
     assert rh.n_pcg < ra.n_pcg and r2.n_pcg < ra.n_pcg
     assert rh.n_inner > 0 and r2.n_inner > 0
+
+
+def test_beta_continuation():
+    """Section 3: a decreasing sequence of beta, each level warm-started; with
+    the start at the target it is exactly one solve."""
+    n = 16
+    w = synth.workload("sin32", shape=(n, n, n))
+    P = O.Problem(w["m0"], w["m1"], 4, 1e-2, 1.0)
+    v1, r1 = P.solve(np.zeros((3, n, n, n)), pc="invH0")
+    v2, r2, lev = P.solve_continuation(np.zeros((3, n, n, n)), 1e-2, beta_start=1e-2, pc="invH0")
+    assert lev == 1 and np.array_equal(v1, v2) and r1.J == r2.J
+    v3, r3, lev = P.solve_continuation(np.zeros((3, n, n, n)), 1e-2, beta_start=1.0, factor=0.1,
+                                       pc="invH0")
+    assert lev == 3 and r3.status == 0 and r3.grel <= 5e-2
+    # the target-level objective at the continuation's result matches a direct
+    # solve to the GN tolerance (both are stationary points of the same J)
+    P.beta = 1e-2
+    J3, _, _ = P.objective(v3)
+    assert abs(J3 - r1.J) / r1.J < 0.05
