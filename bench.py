@@ -50,17 +50,17 @@ CPU_SAMPLE_N = 64        # oracle solves the same generator on a 64^3 grid
 ERR_CHECK_N = 128        # GPU vs oracle gradient / matvec on a 128^3 instance
 
 KCLASS = ["footpoint", "state", "adjoint", "incstate", "incadj", "bodyforce", "fft_r2c",
-          "fft_c2c", "fft_mul", "fft_c2r", "reduce", "vector", "interp"]
+          "fft_c2c", "fft_mul", "fft_c2r", "reduce", "vector", "interp", "fd"]
 # kernel function names of each class (for the ncu summaries); the template
 # argument of k_sl_pipe is the step kind: 0 plain, 1 adjoint, 2 incremental
 # state, 3 adjoint factor
-KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3>",
-          "state": "k_sl_pipe<0>", "adjoint": "k_sl_pipe<1>", "incstate": "k_sl_pipe<2>",
-          "incadj": "k_sl_pipe<1>", "bodyforce": "k_bodyforce", "fft_r2c": "k_r2c_x3",
+KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3, *>",
+          "state": "k_sl_pipe<0, *>", "adjoint": "k_sl_pipe<1, *>", "incstate": "k_sl_pipe<2, *>",
+          "incadj": "k_sl_pipe<1, *>", "bodyforce": "k_bodyforce", "fft_r2c": "k_r2c_x3",
           "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1", "fft_c2r": "k_c2r_x3",
           "reduce": "k_reduce2, k_stats, k_finalize, k_finalize4",
           "vector": "k_pcg_update, k_pcg_dir, k_axpby, k_sub, k_incstate_init, k_incadj_init",
-          "interp": "k_sl_pipe<0>"}
+          "interp": "k_sl_pipe<0, *>", "fd": "k_grad_fd8, k_div_fd8"}
 
 
 def parse():

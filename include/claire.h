@@ -76,6 +76,16 @@ int claire_set_stream(claire_ctx *ctx, void *stream);
  * cached gradient/objective values. */
 int claire_set_params(claire_ctx *ctx, double beta, double gamma);
 
+/* Discretization (Sections 4.1 and 4.2): interp_order 3 = periodic cubic
+ * Lagrange interpolation (default), 1 = trilinear; deriv
+ * CLAIRE_DERIV_SPECTRAL (default) or CLAIRE_DERIV_FD8 (eighth-order central
+ * differences) for the first derivatives grad m and div v -- the paper's GPU
+ * configuration is trilinear with FD8.  The regularization operator and its
+ * inverse stay spectral.  claire_grad and claire_div follow the setting.
+ * Invalidates the cached linearization. */
+enum { CLAIRE_DERIV_SPECTRAL = 0, CLAIRE_DERIV_FD8 = 1 };
+int claire_set_discretization(claire_ctx *ctx, int interp_order, int deriv);
+
 /* Copy template m0 and reference m1 (device, float[N] each) into ctx.
  * Invalidates the cached linearization. */
 int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1);
@@ -86,6 +96,24 @@ int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1);
  * *mismatch = 1/2 ||m(.,1) - m1||^2_{L2} (nullable; synchronizes if given).
  * Does not touch the cached linearization. */
 int claire_forward(claire_ctx *ctx, const float *v, float *m_final, double *mismatch);
+
+/* Differentiable forward (Eq. 2.1b): m(1) from m0 along the characteristics
+ * of v, keeping the state only every checkpoint_stride time steps (and at
+ * t = 1); *mismatch = 1/2 ||m(1) - m1||^2_{L2} (nullable; synchronizes).
+ * m_final: float[N] (nullable).  The first call fixes the stride of ctx.
+ * Leaves the Gauss-Newton linearization invalid. */
+int claire_mismatch_forward(claire_ctx *ctx, const float *v, float *m_final, double *mismatch,
+                            int checkpoint_stride);
+
+/* Backward of the last claire_mismatch_forward (same v): the adjoint of
+ * Eq. 3.2 from lambda(1) = grad_mismatch * (m1 - m(1)) - grad_m_final / h^3
+ * (grad_m_final: float[N] upstream gradient of m(1), nullable), each segment
+ * of the state recomputed from its checkpoint, and the body force
+ * int lambda grad m dt by the trapezoidal rule.  Writes the Euclidean gradient
+ * grad_v = hx*hy*hz * int lambda grad m dt (float[3][N]) of
+ * grad_mismatch * mismatch + <grad_m_final, m(1)>. */
+int claire_mismatch_backward(claire_ctx *ctx, double grad_mismatch, const float *grad_m_final,
+                             float *grad_v);
 
 /* Objective J(v) of Eq. 2.1a: mismatch term plus 1/2 <beta*A v, v>_{L2}.
  * Synchronizes. */
@@ -132,11 +160,12 @@ int claire_precond_h0(claire_ctx *ctx, const float *r, float *s, double tol, int
 
 /* ---- single operators (for checks and composition) ------------------- */
 
-/* Spectral gradient of a scalar field (Section 3): g_d = F^-1[i k_d F f].
- * f: float[N], g: float[3][N]. */
+/* Gradient of a scalar field (Section 3): spectral, g_d = F^-1[i k_d F f],
+ * or FD8 after claire_set_discretization.  f: float[N], g: float[3][N]. */
 int claire_grad(claire_ctx *ctx, const float *f, float *g);
 
-/* Spectral divergence of a vector field: out = sum_d F^-1[i k_d F v_d]. */
+/* Divergence of a vector field: spectral, out = sum_d F^-1[i k_d F v_d], or
+ * FD8 after claire_set_discretization. */
 int claire_div(claire_ctx *ctx, const float *v, float *out);
 
 /* beta*A applied to a vector field (Eq. 3.1 regularization term). */
@@ -230,7 +259,7 @@ enum {
     CLAIRE_K_INCSTATE = 3, CLAIRE_K_INCADJ = 4, CLAIRE_K_BODYFORCE = 5,
     CLAIRE_K_FFT_R2C = 6, CLAIRE_K_FFT_C2C = 7, CLAIRE_K_FFT_MUL = 8,
     CLAIRE_K_FFT_C2R = 9, CLAIRE_K_REDUCE = 10, CLAIRE_K_VECTOR = 11,
-    CLAIRE_K_INTERP = 12, CLAIRE_K_COUNT = 13
+    CLAIRE_K_INTERP = 12, CLAIRE_K_FD = 13, CLAIRE_K_COUNT = 14
 };
 
 /* Enable (1) or disable (0) per-launch CUDA-event timing of every kernel the

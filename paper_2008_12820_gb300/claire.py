@@ -27,7 +27,7 @@ STATUS = {0: "CLAIRE_OK", 1: "CLAIRE_ERR_ARG", 2: "CLAIRE_ERR_OOM", 3: "CLAIRE_E
 
 FIELD = dict(dispm=0, dispp=1, state=2, gradm=3, divv=4, adjf=5, adj=6, incadj=7, incst=8)
 KERNEL = dict(footpoint=0, state=1, adjoint=2, incstate=3, incadj=4, bodyforce=5, fft_r2c=6,
-              fft_c2c=7, fft_mul=8, fft_c2r=9, reduce=10, vector=11, interp=12)
+              fft_c2c=7, fft_mul=8, fft_c2r=9, reduce=10, vector=11, interp=12, fd=13)
 
 EXPORTED = [
     "claire_create", "claire_destroy", "claire_set_stream", "claire_set_params",
@@ -36,7 +36,8 @@ EXPORTED = [
     "claire_apply_A", "claire_interp", "claire_get_field", "claire_solve_opts_default",
     "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
-    "claire_precond_h0", "claire_solve_continuation",
+    "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization",
+    "claire_mismatch_forward", "claire_mismatch_backward",
 ]
 
 
@@ -97,6 +98,9 @@ def load(path: str = LIB_PATH):
         "claire_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
         "claire_precond_noalloc": [I, I, I, D, D, V, V, V],
         "claire_precond_h0": [P, V, V, D, I, I, ctypes.POINTER(ctypes.c_int)],
+        "claire_set_discretization": [P, I, I],
+        "claire_mismatch_forward": [P, V, V, pd, I],
+        "claire_mismatch_backward": [P, D, V, V],
         "claire_solve_continuation": [P, V, D, D, D, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveReport), ctypes.POINTER(ctypes.c_int)],
     }
@@ -216,6 +220,11 @@ class Registration:
         self._c("claire_set_params", float(beta), float(gamma))
         self.beta, self.gamma = beta, gamma
 
+    def set_discretization(self, interp="cubic", deriv="spectral"):
+        """interp "cubic" | "linear"; deriv "spectral" | "fd8" (Sections 4.1, 4.2)."""
+        self._c("claire_set_discretization", 1 if interp == "linear" else 3,
+                1 if deriv == "fd8" else 0)
+
     def set_images(self, m0, m1):
         self._c("claire_set_images", _ptr(m0), _ptr(m1))
 
@@ -224,6 +233,20 @@ class Registration:
         mis = ctypes.c_double(0)
         self._c("claire_forward", _ptr(v), _ptr(m), ctypes.byref(mis) if want_mismatch else None)
         return m, mis.value
+
+    def mismatch_forward(self, v, checkpoint_stride=2, m_final=None):
+        """(m(1), mismatch) keeping the state every checkpoint_stride steps."""
+        m = m_final if m_final is not None else self._new()
+        mis = ctypes.c_double(0)
+        self._c("claire_mismatch_forward", _ptr(v), _ptr(m), ctypes.byref(mis), int(checkpoint_stride))
+        return m, mis.value
+
+    def mismatch_backward(self, grad_mismatch, grad_m_final=None, out=None):
+        """Euclidean gradient w.r.t. v of grad_mismatch * mismatch +
+        <grad_m_final, m(1)> at the last mismatch_forward."""
+        g = out if out is not None else self._new(3)
+        self._c("claire_mismatch_backward", float(grad_mismatch), _ptr(grad_m_final), _ptr(g))
+        return g
 
     def objective(self, v):
         J, mis = ctypes.c_double(0), ctypes.c_double(0)

@@ -127,6 +127,7 @@ struct claire_ctx {
     float *sv = nullptr;
 
     bool have_images = false, have_lin = false;
+    bool deriv_fd8 = false;  // first derivatives by FD8 instead of spectral
     double last_vAv = 0;  // <v, beta A v> (grid sum) of the last gradient with J
 
     float *alloc_f(size_t n) { return (float *)alloc_bytes(n * sizeof(float)); }
@@ -295,6 +296,16 @@ struct claire_ctx {
         return it;
     }
 
+    // first derivatives by the selected discretization
+    void grad(const float *f, float *g) {
+        if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
+        else spectral(OP_GRAD, f, g, nullptr);
+    }
+    void div(const float *v, float *out) {
+        if (deriv_fd8) launch_div_fd8(d, v, out, st, &prof);
+        else spectral(OP_DIV, v, out, nullptr);
+    }
+
     void linearize(const float *v) {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
         const size_t N = d.N;
@@ -303,8 +314,8 @@ struct claire_ctx {
         CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         for (int j = 0; j < nt; ++j)
             launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
-        for (int j = 0; j <= nt; ++j) spectral(OP_GRAD, hist(mhist, j), hist(gmhist, j, 3), nullptr);
-        spectral(OP_DIV, vlin, divv, nullptr);
+        for (int j = 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
+        div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
         have_lin = true;
@@ -359,6 +370,89 @@ struct claire_ctx {
             spectral(OP_A, vt, Hvt, Hvt);
         }
         check_launch("hess_matvec");
+    }
+
+    // ---- differentiable transport with state checkpointing -----------------
+    // checkpoints m^j at j = 0, k, 2k, ... and nt; segment buffers for the
+    // recomputation in the backward pass
+    float *ck = nullptr, *seg_m = nullptr, *seg_g = nullptr, *bacc = nullptr, *lam2 = nullptr;
+    int ck_stride = 0;
+    bool ck_valid = false;
+    int n_ck() const { return (nt + ck_stride - 1) / ck_stride + 1; }
+    int ck_slot(int j) const { return j == nt ? n_ck() - 1 : j / ck_stride; }
+
+    void ensure_ck(int stride) {
+        if (stride != ck_stride) {
+            if (ck) throw Error(CLAIRE_ERR_STATE, "checkpoint stride is fixed after the first differentiable forward");
+            ck_stride = stride;
+            ck = alloc_f((size_t)n_ck() * d.N);
+            seg_m = alloc_f((size_t)(stride + 1) * d.N);
+            seg_g = alloc_f((size_t)(stride + 1) * 3 * d.N);
+            bacc = alloc_f(3 * (size_t)d.N);
+            lam2 = alloc_f(2 * (size_t)d.N);
+        }
+    }
+
+    // forward transport keeping only checkpoints; X-, X+ and c at v kept for
+    // the backward; returns the mismatch 1/2 ||m(1) - m1||^2
+    double diff_forward(const float *v, float *m_final, int stride) {
+        if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
+        ensure_ck(stride);
+        const size_t N = d.N;
+        if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        have_lin = false;  // the full history is not kept on this path
+        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
+        div(vlin, divv);
+        launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
+        CK(cudaMemcpyAsync(ck, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        const float *src = m0;
+        float *a = s1a, *b = s1b;
+        for (int j = 0; j < nt; ++j) {
+            const int jn = j + 1;
+            float *dst = (jn % ck_stride == 0 || jn == nt) ? ck + (size_t)ck_slot(jn) * N : a;
+            launch_state_step(d, src, dispm, rng_m(), dst, st, &prof);
+            src = dst;
+            if (dst == a) { float *t = a; a = b; b = t; }
+        }
+        ck_valid = true;
+        const float *mT = ck + (size_t)ck_slot(nt) * N;
+        if (m_final) CK(cudaMemcpyAsync(m_final, mT, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        check_launch("mismatch_forward");
+        return mismatch_of(mT);
+    }
+
+    // backward of (mismatch, m(1)) -> v: adjoint from l(1) = gmis (m1 - m(1))
+    // - gm_final / h^3, segments recomputed from the checkpoints, body force
+    // accumulated by the trapezoidal rule; grad_v = h^3 b (Euclidean)
+    void diff_backward(double gmis, const float *gm_final, float *grad_v) {
+        if (!ck_valid) throw Error(CLAIRE_ERR_STATE, "no differentiable forward at this point");
+        const size_t N = d.N;
+        const double H3 = h3();
+        const float dt = 1.f / nt;
+        float *lam = lam2, *lam_next = lam2 + N;
+        launch_adjoint_final(d, lam, m1, ck + (size_t)ck_slot(nt) * N, gm_final, (float)gmis,
+                             (float)(1.0 / H3), st, &prof);
+        CK(cudaMemsetAsync(bacc, 0, 3 * N * sizeof(float), st));
+        const int nseg = (nt + ck_stride - 1) / ck_stride;
+        for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+            const int j0 = sgi * ck_stride, j1 = std::min(j0 + ck_stride, nt);
+            // recompute m^j, j0..j1, and their gradients
+            CK(cudaMemcpyAsync(seg_m, ck + (size_t)ck_slot(j0) * N, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            for (int j = j0; j < j1; ++j)
+                launch_state_step(d, seg_m + (size_t)(j - j0) * N, dispm, rng_m(), seg_m + (size_t)(j + 1 - j0) * N,
+                                  st, &prof);
+            for (int j = j0; j <= j1; ++j) grad(seg_m + (size_t)(j - j0) * N, seg_g + (size_t)(j - j0) * 3 * N);
+            // adjoint steps j1 -> j0, body force of levels j1 .. j0+1 (and j0 = 0)
+            for (int j = j1; j > j0; --j) {
+                const float w = (j == nt ? 0.5f : 1.f) * dt;
+                launch_bodyforce_acc(d, bacc, lam, seg_g + (size_t)(j - j0) * 3 * N, w, st, &prof);
+                launch_adjoint_step(d, lam, dispp, rng_p(), cfac, lam_next, st, &prof, CLAIRE_K_ADJOINT);
+                float *t = lam; lam = lam_next; lam_next = t;
+            }
+            if (j0 == 0) launch_bodyforce_acc(d, bacc, lam, seg_g, 0.5f * dt, st, &prof);
+        }
+        launch_axpby(grad_v, (float)H3, bacc, 0.f, nullptr, 3 * (long long)N, st, &prof);
+        check_launch("mismatch_backward");
     }
 
     // m(1) for v into mout (N); uses fdisp, s1a, s1b; leaves the cache alone
@@ -592,6 +686,26 @@ int claire_precond(claire_ctx *ctx, const float *r, float *s) {
     API_END(ctx)
 }
 
+int claire_mismatch_forward(claire_ctx *ctx, const float *v, float *m_final, double *mismatch,
+                            int checkpoint_stride) {
+    API_BEGIN(ctx)
+    need(v, "v");
+    if (checkpoint_stride < 1 || checkpoint_stride > ctx->nt)
+        throw Error(CLAIRE_ERR_ARG, "checkpoint_stride must be in [1, nt]");
+    const double mis = ctx->diff_forward(v, m_final, checkpoint_stride);
+    if (mismatch) *mismatch = mis;
+    API_END(ctx)
+}
+
+int claire_mismatch_backward(claire_ctx *ctx, double grad_mismatch, const float *grad_m_final,
+                             float *grad_v) {
+    API_BEGIN(ctx)
+    need(grad_v, "grad_v");
+    if (!std::isfinite(grad_mismatch)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite upstream gradient");
+    ctx->diff_backward(grad_mismatch, grad_m_final, grad_v);
+    API_END(ctx)
+}
+
 int claire_precond_h0(claire_ctx *ctx, const float *r, float *s, double tol, int maxit,
                       int two_level, int *iterations) {
     API_BEGIN(ctx)
@@ -605,11 +719,21 @@ int claire_precond_h0(claire_ctx *ctx, const float *r, float *s, double tol, int
     API_END(ctx)
 }
 
+int claire_set_discretization(claire_ctx *ctx, int interp_order, int deriv) {
+    API_BEGIN(ctx)
+    if (interp_order != 1 && interp_order != 3) throw Error(CLAIRE_ERR_ARG, "interp_order must be 1 or 3");
+    if (deriv != CLAIRE_DERIV_SPECTRAL && deriv != CLAIRE_DERIV_FD8) throw Error(CLAIRE_ERR_ARG, "unknown derivative scheme");
+    ctx->d.iorder = interp_order;
+    ctx->deriv_fd8 = deriv == CLAIRE_DERIV_FD8;
+    ctx->have_lin = false;
+    API_END(ctx)
+}
+
 int claire_grad(claire_ctx *ctx, const float *f, float *g) {
     API_BEGIN(ctx)
     need(f, "f");
     need(g, "g");
-    ctx->spectral(OP_GRAD, f, g, nullptr);
+    ctx->grad(f, g);
     check_launch("grad");
     API_END(ctx)
 }
@@ -618,7 +742,7 @@ int claire_div(claire_ctx *ctx, const float *v, float *out) {
     API_BEGIN(ctx)
     need(v, "v");
     need(out, "out");
-    ctx->spectral(OP_DIV, v, out, nullptr);
+    ctx->div(v, out);
     check_launch("div");
     API_END(ctx)
 }

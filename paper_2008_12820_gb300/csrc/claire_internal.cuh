@@ -37,6 +37,7 @@ struct Dims {
     int n1, n2, n3;
     long long N;     // n1*n2*n3
     int h3, p3;      // half-spectrum length and pitch along x3
+    int iorder = 3;  // interpolation of the SL steps: 3 cubic Lagrange, 1 trilinear
 };
 
 // spectral operators applied in the fused x1 pass
@@ -74,6 +75,11 @@ void launch_spec_restrict(const Dims &df, const float2 *specf, const Dims &dc, f
 void launch_spec_twolevel(const Dims &df, float2 *specf, const Dims &dc, const float2 *specc,
                           float scale, float beta0, float gamma, cudaStream_t st, Profiler *prof);
 
+// eighth-order central finite differences (Section 4.2): gradient of a
+// scalar field [N] -> [3][N], divergence of a vector field [3][N] -> [N]
+void launch_grad_fd8(const Dims &d, const float *f, float *g, cudaStream_t st, Profiler *prof);
+void launch_div_fd8(const Dims &d, const float *v, float *out, cudaStream_t st, Profiler *prof);
+
 // ------------------------------------------------------------ transport ----
 // Foot points and the per-axis [min, max] floor range of each displacement
 // field (6 ints each), which fixes the shared-memory box of the SL kernels.
@@ -99,6 +105,13 @@ void launch_incadj_init(const Dims &d, float dt, const float *u_last, const floa
                         Profiler *prof);
 void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
                 Profiler *prof);  // out = a - b
+// b += w * l * gm
+void launch_bodyforce_acc(const Dims &d, float *b, const float *l, const float *gm, float w,
+                          cudaStream_t st, Profiler *prof);
+// l = gmis * (m1 - m) - gm_final * inv_h3 (gm_final nullable)
+void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float *m,
+                          const float *gm_final, float gmis, float inv_h3, cudaStream_t st,
+                          Profiler *prof);
 void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,
                       const float *add, float *out, cudaStream_t st, Profiler *prof);
 

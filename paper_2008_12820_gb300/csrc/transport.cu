@@ -88,6 +88,27 @@ __device__ __forceinline__ float gather64(const float *__restrict__ f, const Axi
     return acc;
 }
 
+// trilinear (first-order Lagrange) periodic interpolation at i + disp
+__device__ __forceinline__ float gather8(const float *__restrict__ f, const Dims &d, int i1, int i2,
+                                         int i3, float d1, float d2, float d3) {
+    const float fl1 = floorf(d1), fl2 = floorf(d2), fl3 = floorf(d3);
+    const float t1 = d1 - fl1, t2 = d2 - fl2, t3 = d3 - fl3;
+    const int a0 = wrap_index(i1 + (int)fminf(fmaxf(fl1, -1.0e6f), 1.0e6f), d.n1);
+    const int b0 = wrap_index(i2 + (int)fminf(fmaxf(fl2, -1.0e6f), 1.0e6f), d.n2);
+    const int c0 = wrap_index(i3 + (int)fminf(fmaxf(fl3, -1.0e6f), 1.0e6f), d.n3);
+    const int a1 = a0 + 1 == d.n1 ? 0 : a0 + 1, b1 = b0 + 1 == d.n2 ? 0 : b0 + 1;
+    const int c1 = c0 + 1 == d.n3 ? 0 : c0 + 1;
+    const long long s1 = (long long)d.n2 * d.n3, s2 = d.n3;
+    const float *r00 = f + a0 * s1 + b0 * s2, *r01 = f + a0 * s1 + b1 * s2;
+    const float *r10 = f + a1 * s1 + b0 * s2, *r11 = f + a1 * s1 + b1 * s2;
+    const float x00 = fmaf(t3, __ldg(r00 + c1) - __ldg(r00 + c0), __ldg(r00 + c0));
+    const float x01 = fmaf(t3, __ldg(r01 + c1) - __ldg(r01 + c0), __ldg(r01 + c0));
+    const float x10 = fmaf(t3, __ldg(r10 + c1) - __ldg(r10 + c0), __ldg(r10 + c0));
+    const float x11 = fmaf(t3, __ldg(r11 + c1) - __ldg(r11 + c0), __ldg(r11 + c0));
+    const float y0 = fmaf(t2, x01 - x00, x00), y1 = fmaf(t2, x11 - x10, x10);
+    return fmaf(t1, y1 - y0, y0);
+}
+
 struct Pt {
     int i1, i2, i3;
     long long id;
@@ -117,6 +138,7 @@ __device__ __forceinline__ float interp_at(const float *__restrict__ f, const Di
 // foot points: Heun (RK2) backward (sign -1) and forward (sign +1) in one pass
 //   y* = x + s dt v(x);  X = x + s dt/2 (v(x) + v(y*));  disp = (X - x)/h
 // ---------------------------------------------------------------------------
+template <int ORDER>
 __global__ void __launch_bounds__(BX * BY)
 k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__restrict__ dispp,
              Dims d, float dt, float ih1, float ih2, float ih3) {
@@ -128,13 +150,20 @@ k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__re
     for (int s = 0; s < nsides; ++s) {
         const float sg = s == 0 ? -1.f : 1.f;
         const float q1 = sg * dt * v1 * ih1, q2 = sg * dt * v2 * ih2, q3 = sg * dt * v3 * ih3;
-        Axis4 a1, a2, a3;
-        axis_stencil(p.i1, q1, d.n1, d.n2 * d.n3, a1);
-        axis_stencil(p.i2, q2, d.n2, d.n3, a2);
-        axis_stencil(p.i3, q3, d.n3, 1, a3);
-        const float w1 = gather64(v, a1, a2, a3);
-        const float w2 = gather64(v + N, a1, a2, a3);
-        const float w3 = gather64(v + 2 * N, a1, a2, a3);
+        float w1, w2, w3;
+        if (ORDER == 1) {
+            w1 = gather8(v, d, p.i1, p.i2, p.i3, q1, q2, q3);
+            w2 = gather8(v + N, d, p.i1, p.i2, p.i3, q1, q2, q3);
+            w3 = gather8(v + 2 * N, d, p.i1, p.i2, p.i3, q1, q2, q3);
+        } else {
+            Axis4 a1, a2, a3;
+            axis_stencil(p.i1, q1, d.n1, d.n2 * d.n3, a1);
+            axis_stencil(p.i2, q2, d.n2, d.n3, a2);
+            axis_stencil(p.i3, q3, d.n3, 1, a3);
+            w1 = gather64(v, a1, a2, a3);
+            w2 = gather64(v + N, a1, a2, a3);
+            w3 = gather64(v + 2 * N, a1, a2, a3);
+        }
         float *out = s == 0 ? dispm : dispp;
         const float hs = 0.5f * sg * dt;
         out[p.id] = hs * (v1 + w1) * ih1;
@@ -204,30 +233,6 @@ __device__ __forceinline__ float gather_lean(const float *__restrict__ f, const 
     return gather64(f, a1, a2, a3);
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(BX * BY)
-k_sl_lean(SlArgs a, Dims d) {
-    const int i3 = blockIdx.x * BX + threadIdx.x;
-    const int i2 = blockIdx.y * BY + threadIdx.y;
-    const int i1 = blockIdx.z;
-    if (i3 >= d.n3 || i2 >= d.n2) return;
-    const long long N = d.N;
-    const long long id = ((long long)i1 * d.n2 + i2) * d.n3 + i3;
-    const float val = gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
-    if (MODE == SL_PLAIN) {
-        a.dst[id] = val;
-    } else if (MODE == SL_ADJ) {
-        a.dst[id] = a.aux[id] * val;
-    } else if (MODE == SL_ADJFAC) {
-        const float dx = a.aux[id];
-        a.dst[id] = 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val;
-    } else {
-        const float f = -(a.vt[id] * a.gm[id] + a.vt[N + id] * a.gm[N + id] +
-                          a.vt[2 * N + id] * a.gm[2 * N + id]);
-        a.dst[id] = fmaf(a.dt, f, val);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Software-pipelined tiled semi-Lagrangian step (the production path).
 // Persistent blocks walk the tiles of 32 x 8 x 4 voxels.  The floor range of
@@ -288,7 +293,7 @@ __device__ __forceinline__ void sl_load_epi(const SlArgs &a, long long id, long 
     }
 }
 
-template <int MODE>
+template <int MODE, int ORDER>
 __global__ void __launch_bounds__(PT3 * PT2, 2)
 k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
     constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
@@ -312,7 +317,9 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
                 const int i1 = t1 * PT1 + t;
                 if (i1 >= d.n1) break;
                 const long long id = i1 * plane + (long long)i2 * d.n3 + i3;
-                const float val = gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
+                const float val = ORDER == 1
+                    ? gather8(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id])
+                    : gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
                 float e[NE];
                 sl_load_epi<MODE>(a, id, N, e);
                 sl_epilogue<MODE>(a, id, val, e);
@@ -392,6 +399,21 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
             for (int t = 0; t < PT1; ++t) {
                 if (t1 * PT1 + t < d.n1) {
                     const float fl0 = floorf(cd[t][0]), fl1 = floorf(cd[t][1]), fl2 = floorf(cd[t][2]);
+                    float acc;
+                    if (ORDER == 1) {
+                        // trilinear: nodes floor and floor + 1, one cell above the cubic origin
+                        const float u1 = cd[t][0] - fl0, u2 = cd[t][1] - fl1, u3 = cd[t][2] - fl2;
+                        const int b1 = t + (int)fl0 - fmn0 + 1, b2 = ty + (int)fl1 - fmn1 + 1;
+                        const int b3 = tx + (int)fl2 - fmn2 + 1;
+                        const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
+                        const float x00 = fmaf(u3, p[1] - p[0], p[0]);
+                        const float x01 = fmaf(u3, p[BOX_PITCH + 1] - p[BOX_PITCH], p[BOX_PITCH]);
+                        const float *p1 = p + BS2 * BOX_PITCH;
+                        const float x10 = fmaf(u3, p1[1] - p1[0], p1[0]);
+                        const float x11 = fmaf(u3, p1[BOX_PITCH + 1] - p1[BOX_PITCH], p1[BOX_PITCH]);
+                        const float y0 = fmaf(u2, x01 - x00, x00), y1 = fmaf(u2, x11 - x10, x10);
+                        acc = fmaf(u1, y1 - y0, y0);
+                    } else {
                     float w1[4], w2[4], w3[4];
                     lagrange4(cd[t][0] - fl0, w1);
                     lagrange4(cd[t][1] - fl1, w2);
@@ -399,7 +421,7 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
                     // stencil origin inside the box; every tap is an immediate offset
                     const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2;
                     const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
-                    float acc = 0.f;
+                    acc = 0.f;
 #pragma unroll
                     for (int ia = 0; ia < 4; ++ia) {
                         float sa = 0.f;
@@ -413,6 +435,7 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
                             sa = fmaf(w2[ib], s3, sa);
                         }
                         acc = fmaf(w1[ia], sa, acc);
+                    }
                     }
                     sl_epilogue<MODE>(a, id0 + t * plane, acc, ce[t]);
                 }
@@ -460,15 +483,21 @@ int num_sms() {
     return n;
 }
 
-template <int MODE>
-void launch_pipe(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
+template <int MODE, int ORDER>
+void launch_pipe_o(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
     const long long ntiles = (long long)((d.n3 + PT3 - 1) / PT3) * ((d.n2 + PT2 - 1) / PT2) *
                              ((d.n1 + PT1 - 1) / PT1);
     const long long want = 2LL * num_sms();
     const int blocks = (int)(ntiles < want ? ntiles : want);
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
-    cudaFuncSetAttribute(k_sl_pipe<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_sl_pipe<MODE><<<blocks, dim3(PT3, PT2), smem, st>>>(a, d, range);
+    cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_sl_pipe<MODE, ORDER><<<blocks, dim3(PT3, PT2), smem, st>>>(a, d, range);
+}
+
+template <int MODE>
+void launch_pipe(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
+    if (d.iorder == 1) launch_pipe_o<MODE, 1>(d, a, range, st);
+    else launch_pipe_o<MODE, 3>(d, a, range, st);
 }
 
 // ----------------------------------------------------------- pointwise ----
@@ -525,6 +554,30 @@ __global__ void k_bodyforce(const float *__restrict__ lh, const float *__restric
     }
 }
 
+// b += w * l * gm (three components), the streaming form of the body force
+// used when the state history is recomputed segment by segment
+__global__ void k_bodyforce_acc(float *__restrict__ b, const float *__restrict__ l,
+                                const float *__restrict__ gm, float w, long long N) {
+    for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
+        const float wl = w * l[i];
+        b[i] = fmaf(wl, gm[i], b[i]);
+        b[N + i] = fmaf(wl, gm[N + i], b[N + i]);
+        b[2 * N + i] = fmaf(wl, gm[2 * N + i], b[2 * N + i]);
+    }
+}
+
+// final condition of the adjoint for an upstream gradient:
+// l = gmis * (m1 - m) - gm_final * inv_h3   (gm_final may be NULL)
+__global__ void k_adjoint_final(float *__restrict__ l, const float *__restrict__ m1,
+                                const float *__restrict__ m, const float *__restrict__ gmf,
+                                float gmis, float inv_h3, long long N) {
+    for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
+        float r = gmis * (m1[i] - m[i]);
+        if (gmf) r = fmaf(-inv_h3, gmf[i], r);
+        l[i] = r;
+    }
+}
+
 inline dim3 grid3(const Dims &d) {
     return dim3((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
 }
@@ -549,9 +602,11 @@ void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, floa
     const double two_pi = 6.283185307179586476925286766559;
     {
         ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (dispp ? 36 : 24));
-        k_footpoints<<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt,
-                                                        (float)(d.n1 / two_pi), (float)(d.n2 / two_pi),
-                                                        (float)(d.n3 / two_pi));
+        const float i1 = (float)(d.n1 / two_pi), i2 = (float)(d.n2 / two_pi), i3 = (float)(d.n3 / two_pi);
+        if (d.iorder == 1)
+            k_footpoints<1><<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
+        else
+            k_footpoints<3><<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
     }
     launch_floor_range(d, dispm, range_m, st, prof);
     if (dispp) launch_floor_range(d, dispp, range_p, st, prof);
@@ -611,6 +666,19 @@ void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaS
                 Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 12.0 * d.N);
     k_sub<<<grid1(d.N), PT, 0, st>>>(a, b, out, d.N);
+}
+
+void launch_bodyforce_acc(const Dims &d, float *b, const float *l, const float *gm, float w,
+                          cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, 40.0 * d.N);
+    k_bodyforce_acc<<<grid1(d.N), PT, 0, st>>>(b, l, gm, w, d.N);
+}
+
+void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float *m,
+                          const float *gm_final, float gmis, float inv_h3, cudaStream_t st,
+                          Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)d.N * (gm_final ? 16 : 12));
+    k_adjoint_final<<<grid1(d.N), PT, 0, st>>>(l, m1, m, gm_final, gmis, inv_h3, d.N);
 }
 
 void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,

@@ -456,3 +456,51 @@ def test_beta_continuation_matches_oracle(claire):
         assert rep.n_gn == ro.n_gn
         assert abs(rep.J - ro.J) / abs(ro.J) < 1e-3
         assert rel(host(v), vo) < 1e-2
+
+
+# ------------------------------- the paper's GPU discretization (FD8, linear) ---
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (20, 27, 45)])
+def test_fd8_operators(claire, shape):
+    rng = np.random.default_rng(9)
+    f = rng.standard_normal(shape).astype(np.float32)
+    v = rng.standard_normal((3,) + shape).astype(np.float32)
+    with claire.Registration(shape, 4, 1e-2, 1.0) as reg:
+        reg.set_discretization(interp="linear", deriv="fd8")
+        assert rel(host(reg.grad(dev(f))), O.grad_fd8(f)) < TOL
+        assert rel(host(reg.div(dev(v))), O.div_fd8(v)) < TOL
+
+
+@pytest.mark.parametrize("interp,deriv", [("linear", "fd8"), ("linear", "spectral"), ("cubic", "fd8")])
+def test_gradient_and_matvec_other_discretizations(claire, interp, deriv):
+    shape, nt = (48, 40, 36), 4
+    m0, m1, v = make_problem(shape, nt)
+    vt = synth.smooth_direction(shape, 11)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    P.set_discretization(interp=interp, deriv=deriv)
+    go, Jo = P.gradient(v)
+    Ho = P.matvec(vt)
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_discretization(interp=interp, deriv=deriv)
+        reg.set_images(dev(m0), dev(m1))
+        g, J = reg.gradient(dev(v))
+        assert rel(host(g), go) < TOL and abs(J - Jo) / abs(Jo) < TOL
+        assert rel(host(reg.field("dispm")), P.dispm()) < TOL
+        assert rel(host(reg.hess_matvec(None, dev(vt))), Ho) < TOL
+
+
+def test_solve_paper_gpu_configuration(claire):
+    """trilinear interpolation + FD8 derivatives, fixed work 1 GN x 10 PCG"""
+    w = synth.workload("sin32")
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    P = O.Problem(w["m0"], w["m1"], nt, beta, gamma)
+    P.set_discretization(interp="linear", deriv="fd8")
+    vo, ro = P.solve(np.zeros((3,) + shape), max_gn=1, fixed_pcg=10)
+    with claire.Registration(shape, nt, beta, gamma) as reg:
+        reg.set_discretization(interp="linear", deriv="fd8")
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        v = torch.zeros((3,) + shape, device="cuda")
+        rep = reg.solve(v, max_gn=1, fixed_pcg=10)
+        assert rep.n_pcg == ro.n_pcg == 10
+        assert rel(host(v), vo) < TOL_SOLVE
+        assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
