@@ -212,7 +212,7 @@ def gaussian_smooth(img, sigma_vox):
     g1 = np.exp(-0.5 * (sigma_vox * w[0]) ** 2)[:, None, None]
     g2 = np.exp(-0.5 * (sigma_vox * w[1]) ** 2)[None, :, None]
     g3 = np.exp(-0.5 * (sigma_vox * w[2]) ** 2)[None, None, :]
-    return np.fft.irfftn(F * g1 * g2 * g3, s=shape)
+    return np.fft.irfftn(F * g1 * g2 * g3, s=shape, axes=(0, 1, 2))
 
 
 def blob_pair(shape, seed, n_blobs=12, sigma_vox=2.0, vel_kmax=6, max_disp_vox=4.0):
