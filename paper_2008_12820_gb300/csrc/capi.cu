@@ -350,7 +350,8 @@ struct claire_ctx {
 
     // Hvt = beta A vt + int lt grad m dt.  Avt, if given, is beta*A vt already
     // at hand (PCG carries it along); otherwise it is applied spectrally.
-    void matvec(const float *vt, float *Hvt, const float *Avt = nullptr) {
+    // With Avt and want_dot, dres[0] receives vt . Hvt from the same pass.
+    void matvec(const float *vt, float *Hvt, const float *Avt = nullptr, bool want_dot = false) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
         const float dt = 1.f / nt;
         float *u = s1a, *un = s1b;
@@ -363,7 +364,9 @@ struct claire_ctx {
         for (int j = nt; j >= 1; --j)
             launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
                                 CLAIRE_K_INCADJ);
-        if (Avt) {
+        if (Avt && want_dot) {
+            launch_bodyforce_dot(d.N, nt, lhist, gmhist, Avt, vt, Hvt, partial, dres, st, &prof);
+        } else if (Avt) {
             launch_bodyforce(d, nt, lhist, gmhist, Avt, Hvt, st, &prof);
         } else {
             launch_bodyforce(d, nt, lhist, gmhist, nullptr, Hvt, st, &prof);
@@ -907,10 +910,10 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                 while (it < maxit) {
                     {
                         EvTimer t(st, &rep.t_hess_ms);
-                        ctx->matvec(p, q, Ap);
+                        ctx->matvec(p, q, Ap, true);
                     }
                     rep.n_matvec++;
-                    const double pq = ctx->dot(p, q, n3);
+                    const double pq = ctx->fetch(0);
                     if (!std::isfinite(pq)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite p.Hp in PCG");
                     if (pq <= 0) {
                         if (it == 0) {

@@ -142,6 +142,10 @@ void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const floa
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
                     const float *Az, float b, long long N, bool init, cudaStream_t st,
                     Profiler *prof);
+// q = Ap + body force of (lhist, gmhist); dev_out[0] = p . q (fused curvature)
+void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
+                          const float *Ap, const float *p, float *q, double *partial,
+                          double *dev_out, cudaStream_t st, Profiler *prof);
 // q = Ap + gm (gm . p): the zero-velocity Hessian given beta0*A p
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
                      cudaStream_t st, Profiler *prof);

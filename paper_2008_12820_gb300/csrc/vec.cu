@@ -250,6 +250,41 @@ __global__ void __launch_bounds__(RT) k_h0_apply(float *__restrict__ q, const fl
     }
 }
 
+// Body force of the Hessian matvec plus the carried beta*A p, and p . q:
+//   q_d = Ap_d + dt sum_j w_j l^j d_d m^j,   partial sums of sum_d p_d q_d
+// (fuses the PCG curvature product into the pass that writes q)
+__global__ void __launch_bounds__(RT) k_bodyforce_dot(const float *__restrict__ lh,
+                                                      const float *__restrict__ gmh,
+                                                      const float *__restrict__ Ap,
+                                                      const float *__restrict__ p,
+                                                      float *__restrict__ q, long long N, int nt,
+                                                      float dt, double *__restrict__ partial) {
+    Acc2 acc;
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
+        float b1 = 0.f, b2 = 0.f, b3 = 0.f;
+        for (int j = 0; j <= nt; ++j) {
+            const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
+            const float l = w * lh[(long long)j * N + i];
+            const float *g = gmh + (long long)j * 3 * N;
+            b1 = fmaf(l, g[i], b1);
+            b2 = fmaf(l, g[N + i], b2);
+            b3 = fmaf(l, g[2 * N + i], b3);
+        }
+        b1 += Ap[i];
+        b2 += Ap[N + i];
+        b3 += Ap[2 * N + i];
+        q[i] = b1;
+        q[N + i] = b2;
+        q[2 * N + i] = b3;
+        acc.add_prod(p[i], b1);
+        acc.add_prod(p[N + i], b2);
+        acc.add_prod(p[2 * N + i], b3);
+    }
+    const double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 inline int blocks_for(long long n) {
     long long b = (n + RT - 1) / RT;
     return (int)(b < kReduceBlocks ? b : kReduceBlocks);
@@ -322,6 +357,15 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
                     Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (init ? 16 : 24));
     k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0);
+}
+
+void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
+                          const float *Ap, const float *p, float *q, double *partial,
+                          double *dev_out, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, (double)N * (16.0 * (nt + 1) + 36), 2);
+    const int nb = blocks_for(N);
+    k_bodyforce_dot<<<nb, RT, 0, st>>>(lhist, gmhist, Ap, p, q, N, nt, 1.f / nt, partial);
+    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
