@@ -14,6 +14,7 @@
 #include <exception>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "claire.h"
@@ -118,15 +119,23 @@ struct claire_ctx {
     double *partial = nullptr, *dres = nullptr;
     int *dflag = nullptr;
     // floor ranges of the displacement fields: X-, X+, forward-only X-, interp
+    // (the X- and forward-only slots swap when a line-search trial is adopted)
     int *rng = nullptr;
-    int *rng_m() { return rng; }
+    int off_m = 0, off_f = 12;
+    int *rng_m() { return rng + off_m; }
     int *rng_p() { return rng + 6; }
-    int *rng_f() { return rng + 12; }
+    int *rng_f() { return rng + off_f; }
     int *rng_i() { return rng + 18; }
     // solver vectors, allocated on the first solve
     float *sv = nullptr;
+    // state history of the line search's trial velocity (solver only): an
+    // accepted trial becomes the next linearization's state as it stands
+    float *mhist_t = nullptr;
 
     bool have_images = false, have_lin = false;
+    // grad m^0 = grad m0 in gmhist slot 0 is current (m0 and the derivative
+    // scheme unchanged since it was computed; a solve recomputes it once)
+    bool gm0_valid = false;
     bool deriv_fd8 = false;  // first derivatives by FD8 instead of spectral
     double last_vAv = 0;  // <v, beta A v> (grid sum) of the last gradient with J
 
@@ -306,15 +315,22 @@ struct claire_ctx {
         else spectral(OP_DIV, v, out, nullptr);
     }
 
-    void linearize(const float *v) {
+    // With state_ready, mhist and dispm already hold the state and the X- foot
+    // points of v (an adopted line-search trial); only X+ is computed here.
+    void linearize(const float *v, bool state_ready = false) {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
-        CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        for (int j = 0; j < nt; ++j)
-            launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
-        for (int j = 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
+        if (state_ready) {
+            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), st, &prof);
+        } else {
+            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
+            CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            for (int j = 0; j < nt; ++j)
+                launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
+        }
+        for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
+        gm0_valid = true;
         div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
@@ -325,8 +341,9 @@ struct claire_ctx {
     // adjoint solve + body force + beta A v; J into *J when asked.  Av, if
     // given, is beta*A v already at hand (the solver carries it along);
     // otherwise it is applied spectrally.
-    void gradient(const float *v, float *g, double *J, double *mis_out, const float *Av = nullptr) {
-        linearize(v);
+    void gradient(const float *v, float *g, double *J, double *mis_out, const float *Av = nullptr,
+                  bool state_ready = false) {
+        linearize(v, state_ready);
         const size_t N = d.N;
         launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
         for (int j = nt; j >= 1; --j)
@@ -471,6 +488,27 @@ struct claire_ctx {
         }
         check_launch("forward");
         return src;
+    }
+
+    // the forward solve of the line search: m^j for v into mhist_t (j >= 1)
+    // with the X- foot points in fdisp; returns m(1)
+    const float *forward_trial(const float *v) {
+        if (!mhist_t) mhist_t = alloc_f((size_t)(nt + 1) * d.N);
+        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
+        const float *src = m0;
+        for (int j = 0; j < nt; ++j) {
+            launch_state_step(d, src, fdisp, rng_f(), hist(mhist_t, j + 1), st, &prof);
+            src = hist(mhist_t, j + 1);
+        }
+        check_launch("forward_trial");
+        return src;
+    }
+    // the last trial's state and foot points become those of the linearization
+    void adopt_trial() {
+        std::swap(mhist, mhist_t);
+        std::swap(dispm, fdisp);
+        std::swap(off_m, off_f);
+        CK(cudaMemcpyAsync(mhist, m0, d.N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
 
     double mismatch_of(const float *mfinal) {
@@ -624,6 +662,7 @@ int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1) {
     CK(cudaMemcpyAsync(ctx->m1, m1, b, cudaMemcpyDeviceToDevice, ctx->st));
     ctx->have_images = true;
     ctx->have_lin = false;
+    ctx->gm0_valid = false;
     API_END(ctx)
 }
 
@@ -729,6 +768,7 @@ int claire_set_discretization(claire_ctx *ctx, int interp_order, int deriv) {
     ctx->d.iorder = interp_order;
     ctx->deriv_fd8 = deriv == CLAIRE_DERIV_FD8;
     ctx->have_lin = false;
+    ctx->gm0_valid = false;
     API_END(ctx)
 }
 
@@ -859,6 +899,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         ~EvFree() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } evfree{ev0, ev1};
     CK(cudaEventRecord(ev0, st));
+    ctx->gm0_valid = false;  // grad m0 is computed once per solve
     double J = 0;
     {
         EvTimer t(st, &rep.t_grad_ms);
@@ -951,7 +992,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             EvTimer t(st, &rep.t_obj_ms);
             for (int ls = 0; ls <= o.max_ls; ++ls) {
                 launch_axpby(vn, 1.f, v, (float)alpha, x, n3, st, &ctx->prof);
-                const double mis = ctx->mismatch_of(ctx->forward(vn));
+                const double mis = ctx->mismatch_of(ctx->forward_trial(vn));
                 const double reg = 0.5 * H3 * (vAv + alpha * (xAv + vAx) + alpha * alpha * xAx);
                 const double Jt = mis + reg;
                 rep.n_ls++;
@@ -968,10 +1009,11 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         }
         CK(cudaMemcpyAsync(v, vn, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
         launch_axpby(Av, 1.f, Av, (float)alpha, Ax, n3, st, &ctx->prof);
+        ctx->adopt_trial();
         ++k;
         {
             EvTimer t(st, &rep.t_grad_ms);
-            ctx->gradient(v, g, &J, nullptr, Av);
+            ctx->gradient(v, g, &J, nullptr, Av, true);
         }
         vAv = ctx->last_vAv;
         gn = std::sqrt(ctx->dot(g, g, n3));

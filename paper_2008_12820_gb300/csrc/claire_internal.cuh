@@ -83,6 +83,7 @@ void launch_div_fd8(const Dims &d, const float *v, float *out, cudaStream_t st, 
 // ------------------------------------------------------------ transport ----
 // Foot points and the per-axis [min, max] floor range of each displacement
 // field (6 ints each), which fixes the shared-memory box of the SL kernels.
+// Either of dispm (X-) and dispp (X+) may be null; that side is skipped.
 void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
                        int *range_m, int *range_p, cudaStream_t st, Profiler *prof);
 void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream_t st,

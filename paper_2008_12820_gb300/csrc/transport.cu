@@ -17,6 +17,9 @@
 // The time-step kernels stage the source field in shared-memory halo boxes
 // (k_sl_pipe); the foot-point kernel gathers v from global memory, one
 // thread per voxel, a block covering 32 consecutive x3 points of 8 x2 rows.
+// (A shared-memory box version of the foot points measured no faster: its
+// three 64-tap sums per voxel load the shared-memory pipe as much as the L1
+// gathers do, and the box copies come on top.)
 #include <cuda_runtime.h>
 
 #include "claire_internal.cuh"
@@ -109,6 +112,7 @@ __device__ __forceinline__ float gather8(const float *__restrict__ f, const Dims
     return fmaf(t1, y1 - y0, y0);
 }
 
+
 struct Pt {
     int i1, i2, i3;
     long long id;
@@ -125,15 +129,6 @@ __device__ __forceinline__ Pt this_point(const Dims &d) {
     return p;
 }
 
-__device__ __forceinline__ float interp_at(const float *__restrict__ f, const Dims &d, const Pt &p,
-                                           float d1, float d2, float d3) {
-    Axis4 a1, a2, a3;
-    axis_stencil(p.i1, d1, d.n1, d.n2 * d.n3, a1);
-    axis_stencil(p.i2, d2, d.n2, d.n3, a2);
-    axis_stencil(p.i3, d3, d.n3, 1, a3);
-    return gather64(f, a1, a2, a3);
-}
-
 // ---------------------------------------------------------------------------
 // foot points: Heun (RK2) backward (sign -1) and forward (sign +1) in one pass
 //   y* = x + s dt v(x);  X = x + s dt/2 (v(x) + v(y*));  disp = (X - x)/h
@@ -146,8 +141,8 @@ k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__re
     if (!p.ok) return;
     const long long N = d.N;
     const float v1 = v[p.id], v2 = v[N + p.id], v3 = v[2 * N + p.id];
-    const int nsides = dispp ? 2 : 1;  // X+ is skipped when not wanted
-    for (int s = 0; s < nsides; ++s) {
+    // X- (side 0) and X+ (side 1); a side whose output is null is skipped
+    for (int s = dispm ? 0 : 1; s < (dispp ? 2 : 1); ++s) {
         const float sg = s == 0 ? -1.f : 1.f;
         const float q1 = sg * dt * v1 * ih1, q2 = sg * dt * v2 * ih2, q3 = sg * dt * v3 * ih3;
         float w1, w2, w3;
@@ -293,12 +288,117 @@ __device__ __forceinline__ void sl_load_epi(const SlArgs &a, long long id, long 
     }
 }
 
+// Box copy of tile rows [lo1, lo1 + BS1) x [lo2, lo2 + BS2) x [lo3, lo3 + BS3)
+// of a periodic field.  Chunked (n3 a multiple of 4 and a 16-byte aligned
+// field): 16-byte cp.async of 40 floats per row from lo3 rounded down to a
+// multiple of 4, three rows per warp instruction; the stencil columns then sit
+// box_shift() floats further right.  Otherwise one float per lane and column.
+constexpr int BOX_CH = 10;  // 16-byte chunks per box row
+constexpr int BOX_ROWS = BS1 * BS2;
+static_assert(4 * BOX_CH >= BS3 + 3 && 4 * BOX_CH <= BOX_PITCH, "chunked box row must cover the shifted row");
+
+__device__ __forceinline__ void cp_async16(float *smem, const float *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ int box_shift(int lo3, bool chunked) { return chunked ? lo3 - (lo3 & ~3) : 0; }
+
+__device__ __forceinline__ void box_copy(const float *__restrict__ src, const Dims &d, long long plane, int lo1,
+                                         int lo2, int lo3, float *buf, bool chunked) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (chunked) {
+        const int lrow = tx / BOX_CH, lch = tx - lrow * BOX_CH;
+        if (tx < 3 * BOX_CH) {
+            const int gx = wrap_index((lo3 & ~3) + 4 * lch, d.n3);
+#pragma unroll
+            for (int i = 0; i < (BOX_ROWS + 3 * PT2 - 1) / (3 * PT2); ++i) {
+                const int row = 3 * (ty + PT2 * i) + lrow;
+                if (row < BOX_ROWS) {
+                    const int z = row / BS2, y = row - z * BS2;
+                    cp_async16(buf + row * BOX_PITCH + 4 * lch,
+                               src + wrap_index(lo1 + z, d.n1) * plane + (long long)wrap_index(lo2 + y, d.n2) * d.n3 + gx);
+                }
+            }
+        }
+    } else {
+        const int xa = wrap_index(lo3 + tx, d.n3);
+        const bool two = tx < BS3 - PT3;
+        const int xb = wrap_index(lo3 + tx + PT3, d.n3);
+#pragma unroll
+        for (int yy = 0; yy < (BS2 + PT2 - 1) / PT2; ++yy) {
+            const int y = ty + yy * PT2;
+            if (y < BS2) {
+                const long long g2 = (long long)wrap_index(lo2 + y, d.n2) * d.n3;
+#pragma unroll
+                for (int z = 0; z < BS1; ++z) {
+                    const float *srow = src + wrap_index(lo1 + z, d.n1) * plane + g2;
+                    float *brow = buf + (z * BS2 + y) * BOX_PITCH;
+                    cp_async4(brow + tx, srow + xa);
+                    if (two) cp_async4(brow + tx + PT3, srow + xb);
+                }
+            }
+        }
+    }
+    cp_async_commit();
+}
+
+// 64-tap tricubic sum from a box position; pairs of rows go through the
+// paired FP32 instructions (FMUL2/FFMA2), the x2 and x1 contractions too
+__device__ __forceinline__ float box_cubic(const float *p, const float w1[4], const float w2[4], const float w3[4]) {
+    const float2 c0 = make_float2(w3[0], w3[0]), c1 = make_float2(w3[1], w3[1]);
+    const float2 c2 = make_float2(w3[2], w3[2]), c3 = make_float2(w3[3], w3[3]);
+    const float2 w2a = make_float2(w2[0], w2[1]), w2b = make_float2(w2[2], w2[3]);
+    float2 u = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ia = 0; ia < 4; ++ia) {
+        float2 sr[2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const float *q0 = p + (ia * BS2 + 2 * m) * BOX_PITCH, *q1 = q0 + BOX_PITCH;
+            float2 t = __fmul2_rn(c0, make_float2(q0[0], q1[0]));
+            t = __ffma2_rn(c1, make_float2(q0[1], q1[1]), t);
+            t = __ffma2_rn(c2, make_float2(q0[2], q1[2]), t);
+            t = __ffma2_rn(c3, make_float2(q0[3], q1[3]), t);
+            sr[m] = t;
+        }
+        const float2 tr = __ffma2_rn(sr[1], w2b, __fmul2_rn(sr[0], w2a));
+        const float2 wa = make_float2(w1[ia], w1[ia]);
+        u = ia == 0 ? __fmul2_rn(tr, wa) : __ffma2_rn(tr, wa, u);
+    }
+    return u.x + u.y;
+}
+
+// trilinear sum from the cubic stencil origin p (nodes floor and floor + 1)
+__device__ __forceinline__ float box_linear(const float *p, float u1, float u2, float u3) {
+    p += (BS2 + 1) * BOX_PITCH + 1;
+    const float x00 = fmaf(u3, p[1] - p[0], p[0]);
+    const float x01 = fmaf(u3, p[BOX_PITCH + 1] - p[BOX_PITCH], p[BOX_PITCH]);
+    const float *p1 = p + BS2 * BOX_PITCH;
+    const float x10 = fmaf(u3, p1[1] - p1[0], p1[0]);
+    const float x11 = fmaf(u3, p1[BOX_PITCH + 1] - p1[BOX_PITCH], p1[BOX_PITCH]);
+    const float y0 = fmaf(u2, x01 - x00, x00), y1 = fmaf(u2, x11 - x10, x10);
+    return fmaf(u1, y1 - y0, y0);
+}
+
+// resident blocks per SM: the incremental-state step carries six epilogue
+// inputs per voxel and keeps two; the others fit three
+template <int MODE> struct SlOcc { static constexpr int v = MODE == SL_INCSTATE ? 2 : 3; };
+
+// tiles of block b: a contiguous range, so neighbouring tiles (which share
+// halo rows in L2) run on the same block one after the other
+__device__ __forceinline__ void tile_range(int ntiles, int &tbeg, int &tend) {
+    tbeg = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+    tend = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+}
+
 template <int MODE, int ORDER>
-__global__ void __launch_bounds__(PT3 * PT2, 2)
-k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
+__global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE>::v)
+k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
     constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
     extern __shared__ float smem[];
     const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool chunked = chunked_in != 0;
     const int fmn0 = range[0], fmn1 = range[2], fmn2 = range[4];
     const bool use_box = range[1] - fmn0 <= BOX_SPAN && range[3] - fmn1 <= BOX_SPAN &&
                          range[5] - fmn2 <= BOX_SPAN && fmn0 <= range[1] && fmn1 <= range[3] &&
@@ -306,10 +406,11 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
     const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
     const int ntiles = nb3 * nb2 * nb1;
     const long long N = d.N, plane = (long long)d.n2 * d.n3;
-    int tile = blockIdx.x;
-    if (tile >= ntiles) return;
+    int tbeg, tend;
+    tile_range(ntiles, tbeg, tend);
+    if (tbeg >= tend) return;
     if (!use_box) {
-        for (; tile < ntiles; tile += gridDim.x) {
+        for (int tile = tbeg; tile < tend; ++tile) {
             const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
             const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
             if (i3 >= d.n3 || i2 >= d.n2) continue;
@@ -328,32 +429,10 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
         return;
     }
 
-    // copy the box of tile tl: rows (z, y) over the warps, x over the lanes
-    // (every lane one column, the first BS3 - 32 lanes a second one)
-    auto issue_box = [&](int tl, float *buf) {
-        const int t3 = tl % nb3, r = tl / nb3, t2 = r % nb2, t1 = r / nb2;
-        const int lo1 = t1 * PT1 + fmn0 - 1, lo2 = t2 * PT2 + fmn1 - 1, lo3 = t3 * PT3 + fmn2 - 1;
-        const int xa = wrap_index(lo3 + tx, d.n3);
-        const bool two = tx < BS3 - PT3;
-        const int xb = wrap_index(lo3 + tx + PT3, d.n3);
-#pragma unroll
-        for (int yy = 0; yy < (BS2 + PT2 - 1) / PT2; ++yy) {
-            const int y = ty + yy * PT2;
-            if (y < BS2) {
-                const long long g2 = (long long)wrap_index(lo2 + y, d.n2) * d.n3;
-#pragma unroll
-                for (int z = 0; z < BS1; ++z) {
-                    const float *srow = a.src + wrap_index(lo1 + z, d.n1) * plane + g2;
-                    float *brow = buf + (z * BS2 + y) * BOX_PITCH;
-                    cp_async4(brow + tx, srow + xa);
-                    if (two) cp_async4(brow + tx + PT3, srow + xb);
-                }
-            }
-        }
-        cp_async_commit();
+    auto issue_box = [&](int t1, int t2, int t3, float *buf) {
+        box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
     };
-    auto load_regs = [&](int tl, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
-        const int t3 = tl % nb3, r = tl / nb3, t2 = r % nb2, t1 = r / nb2;
+    auto load_regs = [&](int t1, int t2, int t3, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
         const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
         const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
 #pragma unroll
@@ -368,11 +447,18 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
         }
     };
 
+    // tile counters of the next tile to fetch (x3 fastest)
+    int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
     float nd[PT1][3], ne[PT1][NE];
-    issue_box(tile, smem);
-    load_regs(tile, nd, ne);
+    issue_box(c1, c2, c3, smem);
+    load_regs(c1, c2, c3, nd, ne);
     int cur = 0;
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (int tile = tbeg; tile < tend; ++tile) {
+        const int t1 = c1, t2 = c2, t3 = c3;
+        if (++c3 == nb3) {
+            c3 = 0;
+            if (++c2 == nb2) { c2 = 0; ++c1; }
+        }
         float cd[PT1][3], ce[PT1][NE];
 #pragma unroll
         for (int t = 0; t < PT1; ++t) {
@@ -381,61 +467,35 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range) {
 #pragma unroll
             for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
         }
-        const int next = tile + gridDim.x;
-        if (next < ntiles) {
-            issue_box(next, smem + (cur ^ 1) * BOX_FLOATS);
-            load_regs(next, nd, ne);
+        if (tile + 1 < tend) {
+            issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
+            load_regs(c1, c2, c3, nd, ne);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
         }
         __syncthreads();
         const float *bx = smem + cur * BOX_FLOATS;
-        const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
         const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
         const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
+        const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
         if (i3 < d.n3 && i2 < d.n2) {
 #pragma unroll
             for (int t = 0; t < PT1; ++t) {
                 if (t1 * PT1 + t < d.n1) {
                     const float fl0 = floorf(cd[t][0]), fl1 = floorf(cd[t][1]), fl2 = floorf(cd[t][2]);
+                    // stencil origin inside the box; every tap is an immediate offset
+                    const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
+                    const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
                     float acc;
                     if (ORDER == 1) {
-                        // trilinear: nodes floor and floor + 1, one cell above the cubic origin
-                        const float u1 = cd[t][0] - fl0, u2 = cd[t][1] - fl1, u3 = cd[t][2] - fl2;
-                        const int b1 = t + (int)fl0 - fmn0 + 1, b2 = ty + (int)fl1 - fmn1 + 1;
-                        const int b3 = tx + (int)fl2 - fmn2 + 1;
-                        const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
-                        const float x00 = fmaf(u3, p[1] - p[0], p[0]);
-                        const float x01 = fmaf(u3, p[BOX_PITCH + 1] - p[BOX_PITCH], p[BOX_PITCH]);
-                        const float *p1 = p + BS2 * BOX_PITCH;
-                        const float x10 = fmaf(u3, p1[1] - p1[0], p1[0]);
-                        const float x11 = fmaf(u3, p1[BOX_PITCH + 1] - p1[BOX_PITCH], p1[BOX_PITCH]);
-                        const float y0 = fmaf(u2, x01 - x00, x00), y1 = fmaf(u2, x11 - x10, x10);
-                        acc = fmaf(u1, y1 - y0, y0);
+                        acc = box_linear(p, cd[t][0] - fl0, cd[t][1] - fl1, cd[t][2] - fl2);
                     } else {
-                    float w1[4], w2[4], w3[4];
-                    lagrange4(cd[t][0] - fl0, w1);
-                    lagrange4(cd[t][1] - fl1, w2);
-                    lagrange4(cd[t][2] - fl2, w3);
-                    // stencil origin inside the box; every tap is an immediate offset
-                    const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2;
-                    const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
-                    acc = 0.f;
-#pragma unroll
-                    for (int ia = 0; ia < 4; ++ia) {
-                        float sa = 0.f;
-#pragma unroll
-                        for (int ib = 0; ib < 4; ++ib) {
-                            const float *q = p + (ia * BS2 + ib) * BOX_PITCH;
-                            float s3 = w3[0] * q[0];
-                            s3 = fmaf(w3[1], q[1], s3);
-                            s3 = fmaf(w3[2], q[2], s3);
-                            s3 = fmaf(w3[3], q[3], s3);
-                            sa = fmaf(w2[ib], s3, sa);
-                        }
-                        acc = fmaf(w1[ia], sa, acc);
-                    }
+                        float w1[4], w2[4], w3[4];
+                        lagrange4(cd[t][0] - fl0, w1);
+                        lagrange4(cd[t][1] - fl1, w2);
+                        lagrange4(cd[t][2] - fl2, w3);
+                        acc = box_cubic(p, w1, w2, w3);
                     }
                     sl_epilogue<MODE>(a, id0 + t * plane, acc, ce[t]);
                 }
@@ -456,20 +516,47 @@ __global__ void k_range_init(int *range) {
 
 __global__ void __launch_bounds__(256) k_floor_range(const float *__restrict__ disp, long long N,
                                                      int *__restrict__ range) {
+    // all three components in one sweep (float4 loads where the rows allow),
+    // then a block reduction and one atomic per bound and block
+    __shared__ int red[8][6];
+    int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, mx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    const long long stride = (long long)gridDim.x * 256;
+    const bool vec = (N & 3) == 0 && (((uintptr_t)disp) & 15) == 0;
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
-        int mn = 0x7fffffff, mx = -0x7fffffff;
         const float *dc = disp + c * N;
-        for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N; i += (long long)gridDim.x * 256) {
-            const int f = floor_int(dc[i]);
-            mn = min(mn, f);
-            mx = max(mx, f);
+        if (vec) {
+            const float4 *d4 = reinterpret_cast<const float4 *>(dc);
+            for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N / 4; i += stride) {
+                const float4 q = d4[i];
+                const int f0 = floor_int(q.x), f1 = floor_int(q.y), f2 = floor_int(q.z), f3 = floor_int(q.w);
+                mn[c] = min(mn[c], min(min(f0, f1), min(f2, f3)));
+                mx[c] = max(mx[c], max(max(f0, f1), max(f2, f3)));
+            }
+        } else {
+            for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N; i += stride) {
+                const int f = floor_int(dc[i]);
+                mn[c] = min(mn[c], f);
+                mx[c] = max(mx[c], f);
+            }
         }
-        mn = __reduce_min_sync(0xffffffffu, mn);
-        mx = __reduce_max_sync(0xffffffffu, mx);
+    }
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a = __reduce_min_sync(0xffffffffu, mn[c]), b = __reduce_max_sync(0xffffffffu, mx[c]);
         if ((threadIdx.x & 31) == 0) {
-            atomicMin(&range[2 * c], mn);
-            atomicMax(&range[2 * c + 1], mx);
+            red[w][2 * c] = a;
+            red[w][2 * c + 1] = b;
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        int r = red[0][k];
+        for (int y = 1; y < 8; ++y) r = (k & 1) ? max(r, red[y][k]) : min(r, red[y][k]);
+        if (k & 1) atomicMax(&range[k], r);
+        else atomicMin(&range[k], r);
     }
 }
 
@@ -483,15 +570,24 @@ int num_sms() {
     return n;
 }
 
-template <int MODE, int ORDER>
-void launch_pipe_o(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
+// 16-byte box rows need rows of a multiple of 4 floats and an aligned field
+inline int chunk_ok(const Dims &d, const float *f) {
+    return (d.n3 % 4 == 0 && ((uintptr_t)f & 15) == 0) ? 1 : 0;
+}
+
+inline int pipe_blocks(const Dims &d, int per_sm) {
     const long long ntiles = (long long)((d.n3 + PT3 - 1) / PT3) * ((d.n2 + PT2 - 1) / PT2) *
                              ((d.n1 + PT1 - 1) / PT1);
-    const long long want = 2LL * num_sms();
-    const int blocks = (int)(ntiles < want ? ntiles : want);
+    const long long want = (long long)per_sm * num_sms();
+    return (int)(ntiles < want ? ntiles : want);
+}
+
+template <int MODE, int ORDER>
+void launch_pipe_o(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
     cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_sl_pipe<MODE, ORDER><<<blocks, dim3(PT3, PT2), smem, st>>>(a, d, range);
+    k_sl_pipe<MODE, ORDER><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(a, d, range,
+                                                                                        chunk_ok(d, a.src));
 }
 
 template <int MODE>
@@ -578,9 +674,6 @@ __global__ void k_adjoint_final(float *__restrict__ l, const float *__restrict__
     }
 }
 
-inline dim3 grid3(const Dims &d) {
-    return dim3((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
-}
 
 inline int grid1(long long N) {
     long long b = (N + PT - 1) / PT;
@@ -593,22 +686,24 @@ void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream
                         Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 12.0 * d.N, 2);
     k_range_init<<<1, 32, 0, st>>>(range);
-    k_floor_range<<<grid1(d.N), 256, 0, st>>>(disp, d.N, range);
+    k_floor_range<<<4 * num_sms(), 256, 0, st>>>(disp, d.N, range);
 }
 
 void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
                        int *range_m, int *range_p, cudaStream_t st, Profiler *prof) {
+    if (!dispm && !dispp) return;
     const float dt = 1.f / nt;
     const double two_pi = 6.283185307179586476925286766559;
     {
-        ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (dispp ? 36 : 24));
+        ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)));
         const float i1 = (float)(d.n1 / two_pi), i2 = (float)(d.n2 / two_pi), i3 = (float)(d.n3 / two_pi);
+        const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
         if (d.iorder == 1)
-            k_footpoints<1><<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
+            k_footpoints<1><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
         else
-            k_footpoints<3><<<grid3(d), dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
+            k_footpoints<3><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
     }
-    launch_floor_range(d, dispm, range_m, st, prof);
+    if (dispm) launch_floor_range(d, dispm, range_m, st, prof);
     if (dispp) launch_floor_range(d, dispp, range_p, st, prof);
 }
 
