@@ -66,6 +66,24 @@ typedef enum {
  * current device.  *out receives the context or NULL on error. */
 int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, claire_ctx **out);
 
+/* Precision of the stored trajectories.  CLAIRE_PREC_FP32: everything FP32
+ * (the paper's setting).  CLAIRE_PREC_FP16_STORAGE: the state trajectory m^j,
+ * its gradient grad m^j and the gradient's adjoint lambda^j (j = 0..nt) are
+ * stored in FP16 (IEEE binary16, round to nearest even on store) and widened
+ * to FP32 on load; interpolation, spectral operators and body-force
+ * accumulation run in FP32, reductions in FP64 as in the FP32 form.  The
+ * incremental state and adjoint of the Hessian matvec stay FP32 (their scale
+ * follows the PCG direction, which FP16's range does not cover).  The paper
+ * has no FP16 form; results differ from the FP32 form by the FP16 rounding
+ * of the stored fields (about 5e-4 relative per stored value). */
+enum { CLAIRE_PREC_FP32 = 0, CLAIRE_PREC_FP16_STORAGE = 1 };
+
+/* claire_create with a precision mode (CLAIRE_PREC_*); claire_create is
+ * claire_create_ex(..., CLAIRE_PREC_FP32, out).  An unknown mode is
+ * CLAIRE_ERR_ARG. */
+int claire_create_ex(int nx, int ny, int nz, int nt, double beta, double gamma, int precision,
+                     claire_ctx **out);
+
 /* Release the context and its device memory (NULL is a no-op). */
 int claire_destroy(claire_ctx *ctx);
 

@@ -30,7 +30,7 @@ KERNEL = dict(footpoint=0, state=1, adjoint=2, incstate=3, incadj=4, bodyforce=5
               fft_c2c=7, fft_mul=8, fft_c2r=9, reduce=10, vector=11, interp=12, fd=13)
 
 EXPORTED = [
-    "claire_create", "claire_destroy", "claire_set_stream", "claire_set_params",
+    "claire_create", "claire_create_ex", "claire_destroy", "claire_set_stream", "claire_set_params",
     "claire_set_images", "claire_forward", "claire_objective", "claire_linearize",
     "claire_gradient", "claire_hess_matvec", "claire_precond", "claire_grad", "claire_div",
     "claire_apply_A", "claire_interp", "claire_get_field", "claire_solve_opts_default",
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
     pd = ctypes.POINTER(ctypes.c_double)
     sig = {
         "claire_create": [I, I, I, I, D, D, ctypes.POINTER(P)],
+        "claire_create_ex": [I, I, I, I, D, D, I, ctypes.POINTER(P)],
         "claire_destroy": [P], "claire_set_stream": [P, V], "claire_set_params": [P, D, D],
         "claire_set_images": [P, V, V], "claire_forward": [P, V, V, pd],
         "claire_objective": [P, V, pd, pd], "claire_linearize": [P, V],
@@ -174,16 +175,22 @@ class Registration:
     All field arguments are torch CUDA tensors on the current device; the
     context runs on torch's current stream unless ``stream`` is given."""
 
-    def __init__(self, shape, nt, beta, gamma, stream=None):
+    PRECISION = {"fp32": 0, "fp16": 1}
+
+    def __init__(self, shape, nt, beta, gamma, stream=None, precision="fp32"):
+        """precision: "fp32" (the paper's setting) or "fp16" (stored state,
+        state gradient and adjoint trajectories in FP16, FP32 arithmetic)."""
         L = load()
         h = ctypes.c_void_p()
         nx, ny, nz = (int(s) for s in shape)
-        rc = L.claire_create(nx, ny, nz, int(nt), float(beta), float(gamma), ctypes.byref(h))
+        prec = self.PRECISION[precision] if isinstance(precision, str) else int(precision)
+        rc = L.claire_create_ex(nx, ny, nz, int(nt), float(beta), float(gamma), prec, ctypes.byref(h))
         if rc != CLAIRE_OK:
             raise ClaireError(rc, L.claire_last_error(None).decode())
         self._h = h
         self.shape = (nx, ny, nz)
         self.nt, self.beta, self.gamma = nt, beta, gamma
+        self.precision = precision
         st = stream if stream is not None else torch.cuda.current_stream()
         _check(h, L.claire_set_stream(h, ctypes.c_void_p(st.cuda_stream)))
 

@@ -114,6 +114,13 @@ struct claire_ctx {
     float *vlin = nullptr, *dispm = nullptr, *dispp = nullptr;
     float *mhist = nullptr, *gmhist = nullptr, *divv = nullptr, *cfac = nullptr;
     float *lhist = nullptr, *mt = nullptr;
+    // FP16-storage form: the state trajectory m^j, its gradient grad m^j and
+    // the gradient's adjoint lambda^j are stored in FP16 (the incremental
+    // fields of the matvec stay FP32, their scale follows the PCG direction);
+    // gm1f holds grad m(1) in FP32 for the H0 preconditioners, m0h = m0 in FP16
+    bool h16 = false;
+    __half *mhist_h = nullptr, *gmhist_h = nullptr, *lhist_h = nullptr, *mhist_t_h = nullptr, *m0h = nullptr;
+    float *gm1f = nullptr;
     float *s3a = nullptr, *s1a = nullptr, *s1b = nullptr, *fdisp = nullptr;
     float2 *spec = nullptr;
     double *partial = nullptr, *dres = nullptr;
@@ -140,6 +147,7 @@ struct claire_ctx {
     double last_vAv = 0;  // <v, beta A v> (grid sum) of the last gradient with J
 
     float *alloc_f(size_t n) { return (float *)alloc_bytes(n * sizeof(float)); }
+    __half *alloc_h(size_t n) { return (__half *)alloc_bytes(n * sizeof(__half)); }
     void *alloc_bytes(size_t b) {
         void *p = nullptr;
         CK(cudaMalloc(&p, b));
@@ -154,6 +162,9 @@ struct claire_ctx {
 
     long long N() const { return d.N; }
     float *hist(float *base, int j, int comps = 1) const { return base + (size_t)j * comps * d.N; }
+    __half *hist(__half *base, int j, int comps = 1) const { return base + (size_t)j * comps * d.N; }
+    // grad m(1) of the linearization in FP32
+    const float *gm_final() { return h16 ? gm1f : hist(gmhist, nt, 3); }
     double h3() const {
         const double tp = 6.283185307179586476925286766559;
         return (tp / d.n1) * (tp / d.n2) * (tp / d.n3);
@@ -277,7 +288,7 @@ struct claire_ctx {
     int invh0(const float *r, float *s, double tol, int maxit, bool fixed) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
         if (!ih) ih = alloc_f((size_t)15 * d.N);
-        return invh0_on(fine(), hist(gmhist, nt, 3), r, s, tol, maxit, fixed, ih);
+        return invh0_on(fine(), gm_final(), r, s, tol, maxit, fixed, ih);
     }
 
     // two-level InvH0 (Algorithm 2): restrict r and grad m(1) spectrally to the
@@ -289,7 +300,7 @@ struct claire_ctx {
         const Grid cg{co.d, co.ax, co.spec};
         const float c2f = (float)((double)d.N / (double)co.d.N), f2c = 1.f / c2f;
         if (!co.gm_valid) {
-            spectral_forward3(d, ax, hist(gmhist, nt, 3), spec, st, &prof);
+            spectral_forward3(d, ax, gm_final(), spec, st, &prof);
             launch_spec_restrict(d, spec, co.d, co.spec, f2c, st, &prof);
             spectral_inverse3(co.d, co.ax, co.spec, co.gm, (float)(1.0 / (double)co.d.N), st, &prof);
             co.gm_valid = true;
@@ -310,6 +321,10 @@ struct claire_ctx {
         if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
         else spectral(OP_GRAD, f, g, nullptr);
     }
+    void grad_h(const __half *f, __half *g) {
+        if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
+        else spectral_grad_h(d, ax, f, g, spec, st, &prof);
+    }
     void div(const float *v, float *out) {
         if (deriv_fd8) launch_div_fd8(d, v, out, st, &prof);
         else spectral(OP_DIV, v, out, nullptr);
@@ -325,12 +340,22 @@ struct claire_ctx {
             launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), st, &prof);
         } else {
             launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
-            CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-            for (int j = 0; j < nt; ++j)
-                launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
+            if (h16) {
+                CK(cudaMemcpyAsync(mhist_h, m0h, N * sizeof(__half), cudaMemcpyDeviceToDevice, st));
+                for (int j = 0; j < nt; ++j)
+                    launch_state_step(d, hist(mhist_h, j), dispm, rng_m(), hist(mhist_h, j + 1), st, &prof);
+            } else {
+                CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                for (int j = 0; j < nt; ++j)
+                    launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
+            }
         }
-        for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
+        for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) {
+            if (h16) grad_h(hist(mhist_h, j), hist(gmhist_h, j, 3));
+            else grad(hist(mhist, j), hist(gmhist, j, 3));
+        }
         gm0_valid = true;
+        if (h16) launch_h2f(hist(gmhist_h, nt, 3), gm1f, 3 * (long long)N, st, &prof);
         div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
@@ -345,19 +370,27 @@ struct claire_ctx {
                   bool state_ready = false) {
         linearize(v, state_ready);
         const size_t N = d.N;
-        launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
-        for (int j = nt; j >= 1; --j)
-            launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
-                                CLAIRE_K_ADJOINT);
+        if (h16) {
+            launch_sub(d, m1, hist(mhist_h, nt), hist(lhist_h, nt), st, &prof);
+            for (int j = nt; j >= 1; --j)
+                launch_adjoint_step(d, hist(lhist_h, j), dispp, rng_p(), cfac, hist(lhist_h, j - 1), st, &prof,
+                                    CLAIRE_K_ADJOINT);
+        } else {
+            launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
+            for (int j = nt; j >= 1; --j)
+                launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
+                                    CLAIRE_K_ADJOINT);
+        }
         if (!Av) {
             spectral(OP_A, vlin, s3a, nullptr);
             Av = s3a;
         }
-        launch_bodyforce(d, nt, lhist, gmhist, Av, g, st, &prof);
+        if (h16) launch_bodyforce(d, nt, lhist_h, gmhist_h, Av, g, st, &prof);
+        else launch_bodyforce(d, nt, lhist, gmhist, Av, g, st, &prof);
         check_launch("gradient");
         if (J || mis_out) {
             const double H3 = h3();
-            const double mis = 0.5 * H3 * dot(hist(lhist, nt), hist(lhist, nt), (long long)N);
+            const double mis = h16 ? final_mismatch() : 0.5 * H3 * dot(hist(lhist, nt), hist(lhist, nt), (long long)N);
             last_vAv = dot(vlin, Av, 3 * (long long)N);
             const double reg = 0.5 * H3 * last_vAv;
             if (J) *J = mis + reg;
@@ -372,22 +405,25 @@ struct claire_ctx {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
         const float dt = 1.f / nt;
         float *u = s1a, *un = s1b;
-        launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
+        if (h16) launch_incstate_init(d, dt, vt, hist(gmhist_h, 0, 3), u, st, &prof);
+        else launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
         for (int j = 0; j < nt; ++j) {
-            launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist, j + 1, 3), un, st, &prof);
+            if (h16) launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist_h, j + 1, 3), un, st, &prof);
+            else launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist, j + 1, 3), un, st, &prof);
             float *t = u; u = un; un = t;
         }
-        launch_incadj_init(d, dt, u, vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
+        if (h16) launch_incadj_init(d, dt, u, vt, hist(gmhist_h, nt, 3), hist(lhist, nt), mt, st, &prof);
+        else launch_incadj_init(d, dt, u, vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
         for (int j = nt; j >= 1; --j)
             launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
                                 CLAIRE_K_INCADJ);
         if (Avt && want_dot) {
-            launch_bodyforce_dot(d.N, nt, lhist, gmhist, Avt, vt, Hvt, partial, dres, st, &prof);
-        } else if (Avt) {
-            launch_bodyforce(d, nt, lhist, gmhist, Avt, Hvt, st, &prof);
+            if (h16) launch_bodyforce_dot(d.N, nt, lhist, gmhist_h, Avt, vt, Hvt, partial, dres, st, &prof);
+            else launch_bodyforce_dot(d.N, nt, lhist, gmhist, Avt, vt, Hvt, partial, dres, st, &prof);
         } else {
-            launch_bodyforce(d, nt, lhist, gmhist, nullptr, Hvt, st, &prof);
-            spectral(OP_A, vt, Hvt, Hvt);
+            if (h16) launch_bodyforce(d, nt, lhist, gmhist_h, Avt, Hvt, st, &prof);
+            else launch_bodyforce(d, nt, lhist, gmhist, Avt, Hvt, st, &prof);
+            if (!Avt) spectral(OP_A, vt, Hvt, Hvt);
         }
         check_launch("hess_matvec");
     }
@@ -491,24 +527,44 @@ struct claire_ctx {
     }
 
     // the forward solve of the line search: m^j for v into mhist_t (j >= 1)
-    // with the X- foot points in fdisp; returns m(1)
-    const float *forward_trial(const float *v) {
-        if (!mhist_t) mhist_t = alloc_f((size_t)(nt + 1) * d.N);
+    // with the X- foot points in fdisp; returns the mismatch 1/2 ||m(1) - m1||^2
+    double trial_mismatch(const float *v) {
         launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
+        if (h16) {
+            if (!mhist_t_h) mhist_t_h = alloc_h((size_t)(nt + 1) * d.N);
+            for (int j = 0; j < nt; ++j)
+                launch_state_step(d, j == 0 ? m0h : hist(mhist_t_h, j), fdisp, rng_f(), hist(mhist_t_h, j + 1),
+                                  st, &prof);
+            check_launch("forward_trial");
+            launch_sqdiff(hist(mhist_t_h, nt), m1, d.N, partial, dres, st, &prof);
+            return 0.5 * h3() * fetch();
+        }
+        if (!mhist_t) mhist_t = alloc_f((size_t)(nt + 1) * d.N);
         const float *src = m0;
         for (int j = 0; j < nt; ++j) {
             launch_state_step(d, src, fdisp, rng_f(), hist(mhist_t, j + 1), st, &prof);
             src = hist(mhist_t, j + 1);
         }
         check_launch("forward_trial");
-        return src;
+        return mismatch_of(src);
     }
     // the last trial's state and foot points become those of the linearization
     void adopt_trial() {
-        std::swap(mhist, mhist_t);
         std::swap(dispm, fdisp);
         std::swap(off_m, off_f);
-        CK(cudaMemcpyAsync(mhist, m0, d.N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        if (h16) {
+            std::swap(mhist_h, mhist_t_h);
+            CK(cudaMemcpyAsync(mhist_h, m0h, d.N * sizeof(__half), cudaMemcpyDeviceToDevice, st));
+        } else {
+            std::swap(mhist, mhist_t);
+            CK(cudaMemcpyAsync(mhist, m0, d.N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    // 1/2 h^3 ||m(1) - m1||^2 of the linearization's state
+    double final_mismatch() {
+        if (h16) launch_sqdiff(hist(mhist_h, nt), m1, d.N, partial, dres, st, &prof);
+        else launch_sqdiff(hist(mhist, nt), m1, d.N, partial, dres, st, &prof);
+        return 0.5 * h3() * fetch();
     }
 
     double mismatch_of(const float *mfinal) {
@@ -559,6 +615,11 @@ static void check_params(double beta, double gamma) {
 extern "C" {
 
 int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, claire_ctx **out) {
+    return claire_create_ex(nx, ny, nz, nt, beta, gamma, CLAIRE_PREC_FP32, out);
+}
+
+int claire_create_ex(int nx, int ny, int nz, int nt, double beta, double gamma, int precision,
+                     claire_ctx **out) {
     if (!out) {
         g_create_error = "out is NULL";
         return CLAIRE_ERR_ARG;
@@ -572,10 +633,15 @@ int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, cla
         g_create_error = "nt must be in [1, 256]";
         return CLAIRE_ERR_ARG;
     }
+    if (precision != CLAIRE_PREC_FP32 && precision != CLAIRE_PREC_FP16_STORAGE) {
+        g_create_error = "unknown precision mode";
+        return CLAIRE_ERR_ARG;
+    }
     claire_ctx *c = nullptr;
     try {
         check_params(beta, gamma);
         c = new claire_ctx();
+        c->h16 = precision == CLAIRE_PREC_FP16_STORAGE;
         c->d.n1 = nx;
         c->d.n2 = ny;
         c->d.n3 = nz;
@@ -604,8 +670,16 @@ int claire_create(int nx, int ny, int nz, int nt, double beta, double gamma, cla
         c->vlin = c->alloc_f(3 * N);
         c->dispm = c->alloc_f(3 * N);
         c->dispp = c->alloc_f(3 * N);
-        c->mhist = c->alloc_f((size_t)(nt + 1) * N);
-        c->gmhist = c->alloc_f((size_t)(nt + 1) * 3 * N);
+        if (c->h16) {
+            c->mhist_h = c->alloc_h((size_t)(nt + 1) * N);
+            c->gmhist_h = c->alloc_h((size_t)(nt + 1) * 3 * N);
+            c->lhist_h = c->alloc_h((size_t)(nt + 1) * N);
+            c->m0h = c->alloc_h(N);
+            c->gm1f = c->alloc_f(3 * N);
+        } else {
+            c->mhist = c->alloc_f((size_t)(nt + 1) * N);
+            c->gmhist = c->alloc_f((size_t)(nt + 1) * 3 * N);
+        }
         c->divv = c->alloc_f(N);
         c->cfac = c->alloc_f(N);
         c->lhist = c->alloc_f((size_t)(nt + 1) * N);
@@ -660,6 +734,7 @@ int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1) {
     const size_t b = ctx->d.N * sizeof(float);
     CK(cudaMemcpyAsync(ctx->m0, m0, b, cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->m1, m1, b, cudaMemcpyDeviceToDevice, ctx->st));
+    if (ctx->h16) launch_f2h(ctx->m0, ctx->m0h, ctx->d.N, ctx->st, nullptr);
     ctx->have_images = true;
     ctx->have_lin = false;
     ctx->gm0_valid = false;
@@ -822,6 +897,14 @@ int claire_get_field(claire_ctx *ctx, int which, int j, float *out) {
     if (which != CLAIRE_FIELD_ADJ && which != CLAIRE_FIELD_INCADJ && which != CLAIRE_FIELD_INCST &&
         !ctx->have_lin)
         throw Error(CLAIRE_ERR_STATE, "no linearization");
+    if (ctx->h16 && (which == CLAIRE_FIELD_STATE || which == CLAIRE_FIELD_GRADM || which == CLAIRE_FIELD_ADJ)) {
+        const __half *h = which == CLAIRE_FIELD_STATE ? ctx->hist(ctx->mhist_h, j)
+                        : which == CLAIRE_FIELD_GRADM ? ctx->hist(ctx->gmhist_h, j, 3)
+                                                      : ctx->hist(ctx->lhist_h, j);
+        launch_h2f(h, out, which == CLAIRE_FIELD_GRADM ? 3 * (long long)N : (long long)N, ctx->st, nullptr);
+        check_launch("get_field");
+        return CLAIRE_OK;
+    }
     switch (which) {
         case CLAIRE_FIELD_DISPM: src = ctx->dispm; n = 3 * N; break;
         case CLAIRE_FIELD_DISPP: src = ctx->dispp; n = 3 * N; break;
@@ -992,7 +1075,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             EvTimer t(st, &rep.t_obj_ms);
             for (int ls = 0; ls <= o.max_ls; ++ls) {
                 launch_axpby(vn, 1.f, v, (float)alpha, x, n3, st, &ctx->prof);
-                const double mis = ctx->mismatch_of(ctx->forward_trial(vn));
+                const double mis = ctx->trial_mismatch(vn);
                 const double reg = 0.5 * H3 * (vAv + alpha * (xAv + vAx) + alpha * alpha * xAx);
                 const double Jt = mis + reg;
                 rep.n_ls++;
@@ -1028,8 +1111,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
     rep.grel = g0 > 0 ? gn / g0 : 0.0;
     {
         // relative mismatch at the final v: the cached state is at v
-        launch_sqdiff(ctx->hist(ctx->mhist, ctx->nt), ctx->m1, ctx->d.N, ctx->partial, ctx->dres, st, &ctx->prof);
-        const double a = ctx->fetch();
+        const double a = ctx->final_mismatch() / (0.5 * ctx->h3());
         launch_sqdiff(ctx->m0, ctx->m1, ctx->d.N, ctx->partial, ctx->dres, st, &ctx->prof);
         const double b = ctx->fetch();
         rep.mismatch_rel = b > 0 ? std::sqrt(a / b) : 0.0;

@@ -9,6 +9,7 @@
 // First derivatives use 0 at the Nyquist index of an even axis.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,6 +116,39 @@ void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float 
                           Profiler *prof);
 void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,
                       const float *add, float *out, cudaStream_t st, Profiler *prof);
+
+// FP16-storage form: the stored trajectories (m^j, grad m^j, lambda^j) are
+// FP16; these overloads take them as such and compute in FP32
+void launch_state_step(const Dims &d, const __half *src, const float *dispm, const int *range_m,
+                       __half *dst, cudaStream_t st, Profiler *prof);
+void launch_adjoint_step(const Dims &d, const __half *src, const float *dispp, const int *range_p,
+                         const float *cfac, __half *dst, cudaStream_t st, Profiler *prof, int kclass);
+void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half *gm0, float *u0,
+                          cudaStream_t st, Profiler *prof);
+void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
+                          const int *range_m, const float *vt, const __half *gm_next, float *dst,
+                          cudaStream_t st, Profiler *prof);
+void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
+                        const __half *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
+                        Profiler *prof);
+void launch_sub(const Dims &d, const float *a, const __half *b, __half *out, cudaStream_t st,
+                Profiler *prof);
+void launch_bodyforce(const Dims &d, int nt, const float *lhist, const __half *gmhist,
+                      const float *add, float *out, cudaStream_t st, Profiler *prof);
+void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *gmhist,
+                      const float *add, float *out, cudaStream_t st, Profiler *prof);
+void launch_bodyforce_dot(long long N, int nt, const float *lhist, const __half *gmhist,
+                          const float *Ap, const float *p, float *q, double *partial,
+                          double *dev_out, cudaStream_t st, Profiler *prof);
+void launch_sqdiff(const __half *a, const float *b, long long n, double *partial,
+                   double *dev_out, cudaStream_t st, Profiler *prof);
+// FP16 <-> FP32 copies of n values
+void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof);
+void launch_h2f(const __half *in, float *out, long long n, cudaStream_t st, Profiler *prof);
+// first derivatives of an FP16 scalar field into an FP16 vector field
+void spectral_grad_h(const Dims &d, const FftPlan *ax, const __half *in, __half *out, float2 *spec,
+                     cudaStream_t st, Profiler *prof);
+void launch_grad_fd8(const Dims &d, const __half *f, __half *g, cudaStream_t st, Profiler *prof);
 
 // ------------------------------------------------------------- vectors ----
 // FP64 reductions; results land in dev_out[0..k) (device doubles)

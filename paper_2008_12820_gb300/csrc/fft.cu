@@ -18,6 +18,7 @@
 // reversal, twiddles from a table computed in double on the host.
 // Strided passes (x2, x1) load tiles of TK consecutive k3 columns so that
 // every row access is a contiguous 8*TK-byte segment.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "claire_internal.cuh"
@@ -25,6 +26,12 @@
 namespace claire {
 
 namespace {
+
+// real fields are FP32, or FP16 in the FP16-storage form (FP32 arithmetic)
+__device__ __forceinline__ float ldr(const float *p) { return *p; }
+__device__ __forceinline__ float ldr(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void str(float *p, float v) { *p = v; }
+__device__ __forceinline__ void str(__half *p, float v) { *p = __float2half_rn(v); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -270,9 +277,9 @@ struct Fft {
 
 // ---------------------------------------------------------------- pass 1 ---
 // x3 forward real -> half spectrum.  Block: L complex lines = 2L real lines.
-template <int N, int L>
+template <int N, int L, typename TI = float>
 __global__ void __launch_bounds__(kThreads)
-k_r2c_x3(const float *__restrict__ in, float2 *__restrict__ out, long long nlines, FftPlan p,
+k_r2c_x3(const TI *__restrict__ in, float2 *__restrict__ out, long long nlines, FftPlan p,
          int h3, int p3) {
     extern __shared__ float2 sm[];
     const int n = Fft<N>::size(p), ls = L + 1;
@@ -282,8 +289,8 @@ k_r2c_x3(const float *__restrict__ in, float2 *__restrict__ out, long long nline
     for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
         const int l = t / n, e = t - l * n;
         const long long la = line0 + 2 * l;
-        const float re = la < nlines ? in[la * n + e] : 0.f;
-        const float im = la + 1 < nlines ? in[(la + 1) * n + e] : 0.f;
+        const float re = la < nlines ? ldr(in + la * n + e) : 0.f;
+        const float im = la + 1 < nlines ? ldr(in + (la + 1) * n + e) : 0.f;
         A[e * ls + l] = make_float2(re, im);
     }
     __syncthreads();
@@ -441,9 +448,9 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
 
 // ---------------------------------------------------------------- pass 5 ---
 // x3 inverse half spectrum -> real, two real lines per complex transform.
-template <int N, int L, int EPI>
+template <int N, int L, int EPI, typename TO = float>
 __global__ void __launch_bounds__(kThreads)
-k_c2r_x3(const float2 *__restrict__ in, float *__restrict__ out, const float *__restrict__ add,
+k_c2r_x3(const float2 *__restrict__ in, TO *__restrict__ out, const float *__restrict__ add,
          long long nlines, FftPlan p, int h3, int p3) {
     extern __shared__ float2 sm[];
     const int n = Fft<N>::size(p), ls = L + 1;
@@ -477,12 +484,12 @@ k_c2r_x3(const float2 *__restrict__ in, float *__restrict__ out, const float *__
         if (la < nlines) {
             float val = z.x;
             if (EPI == EPI_ADD) val += add[la * n + e];
-            out[la * n + e] = val;
+            str(out + la * n + e, val);
         }
         if (la + 1 < nlines) {
             float val = z.y;
             if (EPI == EPI_ADD) val += add[(la + 1) * n + e];
-            out[(la + 1) * n + e] = val;
+            str(out + (la + 1) * n + e, val);
         }
     }
 }
@@ -508,17 +515,17 @@ constexpr int tile_cols(int n, int nbuf) {
 // runtime plan (N = 0)
 #define CLAIRE_CT_SIZES(X) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(384) X(512) X(768)
 
-template <int N, int L>
-void r2c_l(const Dims &d, const FftPlan &p, const float *in, float2 *out, long long nlines,
+template <int N, int L, typename TI>
+void r2c_l(const Dims &d, const FftPlan &p, const TI *in, float2 *out, long long nlines,
            cudaStream_t st) {
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const long long blocks = (nlines + 2 * L - 1) / (2 * L);
-    set_smem(k_r2c_x3<N, L>, smem);
-    k_r2c_x3<N, L><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3);
+    set_smem(k_r2c_x3<N, L, TI>, smem);
+    k_r2c_x3<N, L, TI><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3);
 }
 
-template <int N>
-void r2c_n(const Dims &d, const FftPlan &p, const float *in, float2 *out, int ncomp,
+template <int N, typename TI>
+void r2c_n(const Dims &d, const FftPlan &p, const TI *in, float2 *out, int ncomp,
            cudaStream_t st) {
     const long long nlines = (long long)ncomp * d.n1 * d.n2;
     if constexpr (N > 0) {
@@ -532,7 +539,8 @@ void r2c_n(const Dims &d, const FftPlan &p, const float *in, float2 *out, int nc
     }
 }
 
-void r2c_x3(const Dims &d, const FftPlan &p, const float *in, float2 *out, int ncomp,
+template <typename TI>
+void r2c_x3(const Dims &d, const FftPlan &p, const TI *in, float2 *out, int ncomp,
             cudaStream_t st) {
     switch (d.n3) {
 #define CASE_N(NN) case NN: r2c_n<NN>(d, p, in, out, ncomp, st); return;
@@ -609,24 +617,24 @@ void mul_x1_op(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &
     }
 }
 
-template <int N, int L>
-void c2r_l(const Dims &d, const FftPlan &p, const float2 *in, float *out, const float *add,
+template <int N, int L, typename TO>
+void c2r_l(const Dims &d, const FftPlan &p, const float2 *in, TO *out, const float *add,
            long long nlines, cudaStream_t st) {
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const long long blocks = (nlines + 2 * L - 1) / (2 * L);
     if (add) {
-        set_smem(k_c2r_x3<N, L, EPI_ADD>, smem);
-        k_c2r_x3<N, L, EPI_ADD><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines, p,
-                                                                          d.h3, d.p3);
+        set_smem(k_c2r_x3<N, L, EPI_ADD, TO>, smem);
+        k_c2r_x3<N, L, EPI_ADD, TO><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines, p,
+                                                                              d.h3, d.p3);
     } else {
-        set_smem(k_c2r_x3<N, L, EPI_STORE>, smem);
-        k_c2r_x3<N, L, EPI_STORE><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines,
-                                                                            p, d.h3, d.p3);
+        set_smem(k_c2r_x3<N, L, EPI_STORE, TO>, smem);
+        k_c2r_x3<N, L, EPI_STORE, TO><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines,
+                                                                                p, d.h3, d.p3);
     }
 }
 
-template <int N>
-void c2r_n(const Dims &d, const FftPlan &p, const float2 *in, float *out, const float *add,
+template <int N, typename TO>
+void c2r_n(const Dims &d, const FftPlan &p, const float2 *in, TO *out, const float *add,
            int ncomp, cudaStream_t st) {
     const long long nlines = (long long)ncomp * d.n1 * d.n2;
     if constexpr (N > 0) {
@@ -640,7 +648,8 @@ void c2r_n(const Dims &d, const FftPlan &p, const float2 *in, float *out, const 
     }
 }
 
-void c2r_x3(const Dims &d, const FftPlan &p, const float2 *in, float *out, const float *add,
+template <typename TO>
+void c2r_x3(const Dims &d, const FftPlan &p, const float2 *in, TO *out, const float *add,
             int ncomp, cudaStream_t st) {
     switch (d.n3) {
 #define CASE_N(NN) case NN: c2r_n<NN>(d, p, in, out, add, ncomp, st); return;
@@ -745,6 +754,32 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
     {
         ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, nout * (R + C + (add ? R : 0.0)));
         c2r_x3(d, ax[2], spec, out, add, nout, st);
+    }
+}
+
+void spectral_grad_h(const Dims &d, const FftPlan *ax, const __half *in, __half *out, float2 *spec,
+                     cudaStream_t st, Profiler *prof) {
+    const double R = 2.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
+    const SpecParams sp{0.f, 0.f, (float)(1.0 / (double)d.N)};
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_R2C, st, R + C);
+        r2c_x3(d, ax[2], in, spec, 1, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_C2C, st, 2 * C);
+        c2c_x2(d, ax[1], spec, 1, -1.f, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, 4 * C);
+        mul_x1_op<OP_GRAD>(d, ax[0], spec, sp, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_C2C, st, 3 * 2 * C);
+        c2c_x2(d, ax[1], spec, 3, +1.f, st);
+    }
+    {
+        ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, 3 * (R + C));
+        c2r_x3(d, ax[2], spec, out, nullptr, 3, st);
     }
 }
 

@@ -20,7 +20,10 @@
 // (A shared-memory box version of the foot points measured no faster: its
 // three 64-tap sums per voxel load the shared-memory pipe as much as the L1
 // gathers do, and the box copies come on top.)
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "claire_internal.cuh"
 
@@ -29,6 +32,14 @@ namespace claire {
 namespace {
 
 constexpr int BX = 32, BY = 8;
+
+// Stored fields are FP32 or, in the FP16-storage form, FP16; arithmetic is
+// FP32 either way (FP16 values widen on load, results round to nearest even
+// on store).
+__device__ __forceinline__ float ldf(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void stf(float *p, float v) { *p = v; }
+__device__ __forceinline__ void stf(__half *p, float v) { *p = __float2half_rn(v); }
 
 // cubic Lagrange basis on the nodes -1, 0, 1, 2 evaluated at t in [0, 1)
 __device__ __forceinline__ void lagrange4(float t, float w[4]) {
@@ -71,7 +82,8 @@ __device__ __forceinline__ void axis_stencil(int i, float disp, int n, int strid
     }
 }
 
-__device__ __forceinline__ float gather64(const float *__restrict__ f, const Axis4 &a1,
+template <typename T>
+__device__ __forceinline__ float gather64(const T *__restrict__ f, const Axis4 &a1,
                                           const Axis4 &a2, const Axis4 &a3) {
     float acc = 0.f;
 #pragma unroll
@@ -79,11 +91,11 @@ __device__ __forceinline__ float gather64(const float *__restrict__ f, const Axi
         float s2 = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float *row = f + a1.o[i] + a2.o[j];
-            float s3 = a3.w[0] * __ldg(row + a3.o[0]);
-            s3 = fmaf(a3.w[1], __ldg(row + a3.o[1]), s3);
-            s3 = fmaf(a3.w[2], __ldg(row + a3.o[2]), s3);
-            s3 = fmaf(a3.w[3], __ldg(row + a3.o[3]), s3);
+            const T *row = f + a1.o[i] + a2.o[j];
+            float s3 = a3.w[0] * ldf(row + a3.o[0]);
+            s3 = fmaf(a3.w[1], ldf(row + a3.o[1]), s3);
+            s3 = fmaf(a3.w[2], ldf(row + a3.o[2]), s3);
+            s3 = fmaf(a3.w[3], ldf(row + a3.o[3]), s3);
             s2 = fmaf(a2.w[j], s3, s2);
         }
         acc = fmaf(a1.w[i], s2, acc);
@@ -92,7 +104,8 @@ __device__ __forceinline__ float gather64(const float *__restrict__ f, const Axi
 }
 
 // trilinear (first-order Lagrange) periodic interpolation at i + disp
-__device__ __forceinline__ float gather8(const float *__restrict__ f, const Dims &d, int i1, int i2,
+template <typename T>
+__device__ __forceinline__ float gather8(const T *__restrict__ f, const Dims &d, int i1, int i2,
                                          int i3, float d1, float d2, float d3) {
     const float fl1 = floorf(d1), fl2 = floorf(d2), fl3 = floorf(d3);
     const float t1 = d1 - fl1, t2 = d2 - fl2, t3 = d3 - fl3;
@@ -102,12 +115,12 @@ __device__ __forceinline__ float gather8(const float *__restrict__ f, const Dims
     const int a1 = a0 + 1 == d.n1 ? 0 : a0 + 1, b1 = b0 + 1 == d.n2 ? 0 : b0 + 1;
     const int c1 = c0 + 1 == d.n3 ? 0 : c0 + 1;
     const long long s1 = (long long)d.n2 * d.n3, s2 = d.n3;
-    const float *r00 = f + a0 * s1 + b0 * s2, *r01 = f + a0 * s1 + b1 * s2;
-    const float *r10 = f + a1 * s1 + b0 * s2, *r11 = f + a1 * s1 + b1 * s2;
-    const float x00 = fmaf(t3, __ldg(r00 + c1) - __ldg(r00 + c0), __ldg(r00 + c0));
-    const float x01 = fmaf(t3, __ldg(r01 + c1) - __ldg(r01 + c0), __ldg(r01 + c0));
-    const float x10 = fmaf(t3, __ldg(r10 + c1) - __ldg(r10 + c0), __ldg(r10 + c0));
-    const float x11 = fmaf(t3, __ldg(r11 + c1) - __ldg(r11 + c0), __ldg(r11 + c0));
+    const T *r00 = f + a0 * s1 + b0 * s2, *r01 = f + a0 * s1 + b1 * s2;
+    const T *r10 = f + a1 * s1 + b0 * s2, *r11 = f + a1 * s1 + b1 * s2;
+    const float x00 = fmaf(t3, ldf(r00 + c1) - ldf(r00 + c0), ldf(r00 + c0));
+    const float x01 = fmaf(t3, ldf(r01 + c1) - ldf(r01 + c0), ldf(r01 + c0));
+    const float x10 = fmaf(t3, ldf(r10 + c1) - ldf(r10 + c0), ldf(r10 + c0));
+    const float x11 = fmaf(t3, ldf(r11 + c1) - ldf(r11 + c0), ldf(r11 + c0));
     const float y0 = fmaf(t2, x01 - x00, x00), y1 = fmaf(t2, x11 - x10, x10);
     return fmaf(t1, y1 - y0, y0);
 }
@@ -172,15 +185,18 @@ k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__re
 // ---------------------------------------------------------------------------
 enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3 };
 
-struct SlArgs {
-    const float *src;   // field gathered at the foot points
+// TS: storage type of the gathered and written field; TG: of grad m
+template <typename TS = float, typename TG = float>
+struct SlArgsT {
+    const TS *src;      // field gathered at the foot points
     const float *disp;  // foot point minus grid point, index units, [3][N]
-    float *dst;
+    TS *dst;
     const float *aux;   // SL_ADJ: c;  SL_ADJFAC: div v on the grid
     const float *vt;    // SL_INCSTATE: vt [3][N]
-    const float *gm;    // SL_INCSTATE: grad m^{j+1} [3][N]
+    const TG *gm;       // SL_INCSTATE: grad m^{j+1} [3][N]
     float dt;
 };
+using SlArgs = SlArgsT<float, float>;
 
 __device__ __forceinline__ int floor_int(float x) {
     return (int)fminf(fmaxf(floorf(x), -1.0e6f), 1.0e6f);
@@ -192,7 +208,8 @@ __device__ __forceinline__ int floor_int(float x) {
 // base pointer and reads the 64 taps with row offsets plus immediate column
 // offsets; the few stencils that wrap take the per-axis wrapped path.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float gather_lean(const float *__restrict__ f, const Dims &d, int i1,
+template <typename T>
+__device__ __forceinline__ float gather_lean(const T *__restrict__ f, const Dims &d, int i1,
                                              int i2, int i3, float d1, float d2, float d3) {
     const float fl1 = floorf(d1), fl2 = floorf(d2), fl3 = floorf(d3);
     float w1[4], w2[4], w3[4];
@@ -203,18 +220,18 @@ __device__ __forceinline__ float gather_lean(const float *__restrict__ f, const 
     const int s2 = d.n3, s1 = d.n2 * d.n3;
     if ((unsigned)b1 <= (unsigned)(d.n1 - 4) && (unsigned)b2 <= (unsigned)(d.n2 - 4) &&
         (unsigned)b3 <= (unsigned)(d.n3 - 4)) {
-        const float *p = f + ((long long)b1 * d.n2 + b2) * d.n3 + b3;
+        const T *p = f + ((long long)b1 * d.n2 + b2) * d.n3 + b3;
         float acc = 0.f;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             float sa = 0.f;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const float *q = p + a * s1 + b * s2;
-                float s3 = w3[0] * __ldg(q);
-                s3 = fmaf(w3[1], __ldg(q + 1), s3);
-                s3 = fmaf(w3[2], __ldg(q + 2), s3);
-                s3 = fmaf(w3[3], __ldg(q + 3), s3);
+                const T *q = p + a * s1 + b * s2;
+                float s3 = w3[0] * ldf(q);
+                s3 = fmaf(w3[1], ldf(q + 1), s3);
+                s3 = fmaf(w3[2], ldf(q + 2), s3);
+                s3 = fmaf(w3[3], ldf(q + 3), s3);
                 sa = fmaf(w2[b], s3, sa);
             }
             acc = fmaf(w1[a], sa, acc);
@@ -263,28 +280,28 @@ __device__ __forceinline__ void cp_async_wait() {
 
 template <int MODE> struct EpiCount { static constexpr int v = MODE == SL_INCSTATE ? 6 : (MODE == SL_PLAIN ? 0 : 1); };
 
-template <int MODE>
-__device__ __forceinline__ void sl_epilogue(const SlArgs &a, long long id, float val, const float *e) {
+template <int MODE, typename A>
+__device__ __forceinline__ void sl_epilogue(const A &a, long long id, float val, const float *e) {
     if (MODE == SL_PLAIN) {
-        a.dst[id] = val;
+        stf(a.dst + id, val);
     } else if (MODE == SL_ADJ) {
-        a.dst[id] = e[0] * val;
+        stf(a.dst + id, e[0] * val);
     } else if (MODE == SL_ADJFAC) {
         const float dx = e[0];
-        a.dst[id] = 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val;
+        stf(a.dst + id, 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val);
     } else {
         const float f = -(e[0] * e[3] + e[1] * e[4] + e[2] * e[5]);
-        a.dst[id] = fmaf(a.dt, f, val);
+        stf(a.dst + id, fmaf(a.dt, f, val));
     }
 }
 
-template <int MODE>
-__device__ __forceinline__ void sl_load_epi(const SlArgs &a, long long id, long long N, float *e) {
+template <int MODE, typename A>
+__device__ __forceinline__ void sl_load_epi(const A &a, long long id, long long N, float *e) {
     if (MODE == SL_ADJ || MODE == SL_ADJFAC) {
         e[0] = a.aux[id];
     } else if (MODE == SL_INCSTATE) {
         e[0] = a.vt[id]; e[1] = a.vt[N + id]; e[2] = a.vt[2 * N + id];
-        e[3] = a.gm[id]; e[4] = a.gm[N + id]; e[5] = a.gm[2 * N + id];
+        e[3] = ldf(a.gm + id); e[4] = ldf(a.gm + N + id); e[5] = ldf(a.gm + 2 * N + id);
     }
 }
 
@@ -343,6 +360,67 @@ __device__ __forceinline__ void box_copy(const float *__restrict__ src, const Di
     cp_async_commit();
 }
 
+// FP16 source fields: the box is widened to FP32 in shared memory, so the
+// interpolation below is the same.  Chunked (n3 a multiple of 8 and a 16-byte
+// aligned field): each thread loads up to HB_PER 16-byte chunks of 8 halves
+// into registers (issued before the current tile is computed) and widens and
+// stores them after it; rows start at lo3 rounded down to a multiple of 8.
+// Otherwise the box is copied element by element, synchronously.
+constexpr int HBOX_CH = 6;  // 16-byte chunks (8 halves) per box row
+static_assert(8 * HBOX_CH >= BS3 + 7 && 8 * HBOX_CH <= BOX_PITCH, "FP16 box row must cover the shifted row");
+constexpr int HB_PER = (BOX_ROWS * HBOX_CH + PT3 * PT2 - 1) / (PT3 * PT2);
+
+__device__ __forceinline__ int hbox_shift(int lo3, bool chunked) { return chunked ? lo3 - (lo3 & ~7) : 0; }
+
+struct HStage {
+    uint4 q[HB_PER];
+};
+
+__device__ __forceinline__ void hbox_load(const __half *__restrict__ src, const Dims &d, long long plane, int lo1,
+                                          int lo2, int lo3, HStage &hs) {
+    const int tid = threadIdx.y * PT3 + threadIdx.x;
+    const int x0 = lo3 & ~7;
+#pragma unroll
+    for (int i = 0; i < HB_PER; ++i) {
+        const int e = tid + i * PT3 * PT2;
+        if (e < BOX_ROWS * HBOX_CH) {
+            const int row = e / HBOX_CH, ch = e - row * HBOX_CH;
+            const int z = row / BS2, y = row - z * BS2;
+            const __half *g = src + wrap_index(lo1 + z, d.n1) * plane + (long long)wrap_index(lo2 + y, d.n2) * d.n3 +
+                              wrap_index(x0 + 8 * ch, d.n3);
+            hs.q[i] = __ldg(reinterpret_cast<const uint4 *>(g));
+        }
+    }
+}
+
+__device__ __forceinline__ void hbox_store(const HStage &hs, float *buf) {
+    const int tid = threadIdx.y * PT3 + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < HB_PER; ++i) {
+        const int e = tid + i * PT3 * PT2;
+        if (e < BOX_ROWS * HBOX_CH) {
+            const int row = e / HBOX_CH, ch = e - row * HBOX_CH;
+            const __half2 *h = reinterpret_cast<const __half2 *>(&hs.q[i]);
+            const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
+            const float2 c = __half22float2(h[2]), e2 = __half22float2(h[3]);
+            float4 *dst = reinterpret_cast<float4 *>(buf + row * BOX_PITCH + 8 * ch);
+            dst[0] = make_float4(a.x, a.y, b.x, b.y);
+            dst[1] = make_float4(c.x, c.y, e2.x, e2.y);
+        }
+    }
+}
+
+__device__ __forceinline__ void hbox_copy_sync(const __half *__restrict__ src, const Dims &d, long long plane,
+                                               int lo1, int lo2, int lo3, float *buf) {
+    const int tid = threadIdx.y * PT3 + threadIdx.x;
+    for (int e = tid; e < BOX_ROWS * BS3; e += PT3 * PT2) {
+        const int row = e / BS3, x = e - row * BS3;
+        const int z = row / BS2, y = row - z * BS2;
+        buf[row * BOX_PITCH + x] = ldf(src + wrap_index(lo1 + z, d.n1) * plane +
+                                       (long long)wrap_index(lo2 + y, d.n2) * d.n3 + wrap_index(lo3 + x, d.n3));
+    }
+}
+
 // 64-tap tricubic sum from a box position; pairs of rows go through the
 // paired FP32 instructions (FMUL2/FFMA2), the x2 and x1 contractions too
 __device__ __forceinline__ float box_cubic(const float *p, const float w1[4], const float w2[4], const float w3[4]) {
@@ -383,7 +461,9 @@ __device__ __forceinline__ float box_linear(const float *p, float u1, float u2, 
 
 // resident blocks per SM: the incremental-state step carries six epilogue
 // inputs per voxel and keeps two; the others fit three
-template <int MODE> struct SlOcc { static constexpr int v = MODE == SL_INCSTATE ? 2 : 3; };
+template <int MODE, typename TS = float> struct SlOcc {
+    static constexpr int v = (MODE == SL_INCSTATE || !std::is_same<TS, float>::value) ? 2 : 3;
+};
 
 // tiles of block b: a contiguous range, so neighbouring tiles (which share
 // halo rows in L2) run on the same block one after the other
@@ -392,10 +472,11 @@ __device__ __forceinline__ void tile_range(int ntiles, int &tbeg, int &tend) {
     tend = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
 }
 
-template <int MODE, int ORDER>
-__global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE>::v)
-k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
+template <int MODE, int ORDER, typename TS = float, typename TG = float>
+__global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE, TS>::v)
+k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_in) {
     constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
+    constexpr bool HALF = !std::is_same<TS, float>::value;
     extern __shared__ float smem[];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool chunked = chunked_in != 0;
@@ -430,7 +511,8 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
     }
 
     auto issue_box = [&](int t1, int t2, int t3, float *buf) {
-        box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
+        if constexpr (!HALF)
+            box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
     };
     auto load_regs = [&](int t1, int t2, int t3, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
         const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
@@ -450,7 +532,18 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
     // tile counters of the next tile to fetch (x3 fastest)
     int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
     float nd[PT1][3], ne[PT1][NE];
-    issue_box(c1, c2, c3, smem);
+    HStage hs;  // FP16 staging (unused for FP32 sources)
+    if constexpr (HALF) {
+        const int lo1 = c1 * PT1 + fmn0 - 1, lo2 = c2 * PT2 + fmn1 - 1, lo3 = c3 * PT3 + fmn2 - 1;
+        if (chunked) {
+            hbox_load(a.src, d, plane, lo1, lo2, lo3, hs);
+            hbox_store(hs, smem);
+        } else {
+            hbox_copy_sync(a.src, d, plane, lo1, lo2, lo3, smem);
+        }
+    } else {
+        issue_box(c1, c2, c3, smem);
+    }
     load_regs(c1, c2, c3, nd, ne);
     int cur = 0;
     for (int tile = tbeg; tile < tend; ++tile) {
@@ -467,7 +560,13 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
 #pragma unroll
             for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
         }
-        if (tile + 1 < tend) {
+        const bool more = tile + 1 < tend;
+        if constexpr (HALF) {
+            if (more) {
+                if (chunked) hbox_load(a.src, d, plane, c1 * PT1 + fmn0 - 1, c2 * PT2 + fmn1 - 1, c3 * PT3 + fmn2 - 1, hs);
+                load_regs(c1, c2, c3, nd, ne);
+            }
+        } else if (more) {
             issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
             load_regs(c1, c2, c3, nd, ne);
             cp_async_wait<1>();
@@ -478,7 +577,7 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
         const float *bx = smem + cur * BOX_FLOATS;
         const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
         const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
-        const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
+        const int sh = HALF ? hbox_shift(t3 * PT3 + fmn2 - 1, chunked) : box_shift(t3 * PT3 + fmn2 - 1, chunked);
         if (i3 < d.n3 && i2 < d.n2) {
 #pragma unroll
             for (int t = 0; t < PT1; ++t) {
@@ -499,6 +598,13 @@ k_sl_pipe(SlArgs a, Dims d, const int *__restrict__ range, int chunked_in) {
                     }
                     sl_epilogue<MODE>(a, id0 + t * plane, acc, ce[t]);
                 }
+            }
+        }
+        if constexpr (HALF) {
+            if (more) {
+                float *nbuf = smem + (cur ^ 1) * BOX_FLOATS;
+                if (chunked) hbox_store(hs, nbuf);
+                else hbox_copy_sync(a.src, d, plane, c1 * PT1 + fmn0 - 1, c2 * PT2 + fmn1 - 1, c3 * PT3 + fmn2 - 1, nbuf);
             }
         }
         __syncthreads();
@@ -570,9 +676,12 @@ int num_sms() {
     return n;
 }
 
-// 16-byte box rows need rows of a multiple of 4 floats and an aligned field
-inline int chunk_ok(const Dims &d, const float *f) {
-    return (d.n3 % 4 == 0 && ((uintptr_t)f & 15) == 0) ? 1 : 0;
+// 16-byte box rows need rows of a whole number of chunks (4 floats or 8
+// halves) and a 16-byte aligned field
+template <typename T>
+inline int chunk_ok(const Dims &d, const T *f) {
+    const int per = 16 / (int)sizeof(T);
+    return (d.n3 % per == 0 && ((uintptr_t)f & 15) == 0) ? 1 : 0;
 }
 
 inline int pipe_blocks(const Dims &d, int per_sm) {
@@ -582,16 +691,16 @@ inline int pipe_blocks(const Dims &d, int per_sm) {
     return (int)(ntiles < want ? ntiles : want);
 }
 
-template <int MODE, int ORDER>
-void launch_pipe_o(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
+template <int MODE, int ORDER, typename TS, typename TG>
+void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
-    cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_sl_pipe<MODE, ORDER><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(a, d, range,
-                                                                                        chunk_ok(d, a.src));
+    cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER, TS, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_sl_pipe<MODE, ORDER, TS, TG><<<pipe_blocks(d, SlOcc<MODE, TS>::v), dim3(PT3, PT2), smem, st>>>(
+        a, d, range, chunk_ok(d, a.src));
 }
 
-template <int MODE>
-void launch_pipe(const Dims &d, const SlArgs &a, const int *range, cudaStream_t st) {
+template <int MODE, typename TS, typename TG>
+void launch_pipe(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
     if (d.iorder == 1) launch_pipe_o<MODE, 1>(d, a, range, st);
     else launch_pipe_o<MODE, 3>(d, a, range, st);
 }
@@ -599,45 +708,49 @@ void launch_pipe(const Dims &d, const SlArgs &a, const int *range, cudaStream_t 
 // ----------------------------------------------------------- pointwise ----
 constexpr int PT = 256;
 
-__global__ void k_incstate_init(const float *__restrict__ vt, const float *__restrict__ gm,
+template <typename TG>
+__global__ void k_incstate_init(const float *__restrict__ vt, const TG *__restrict__ gm,
                                 float *__restrict__ u0, long long N, float hdt) {
     for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
-        const float f = -(vt[i] * gm[i] + vt[N + i] * gm[N + i] + vt[2 * N + i] * gm[2 * N + i]);
+        const float f = -(vt[i] * ldf(gm + i) + vt[N + i] * ldf(gm + N + i) + vt[2 * N + i] * ldf(gm + 2 * N + i));
         u0[i] = hdt * f;
     }
 }
 
 // lt(1) = -mt(1) = -(u^nt - dt/2 f^nt);  also returns mt(1)
+template <typename TG>
 __global__ void k_incadj_init(const float *__restrict__ u, const float *__restrict__ vt,
-                              const float *__restrict__ gm, float *__restrict__ lt,
+                              const TG *__restrict__ gm, float *__restrict__ lt,
                               float *__restrict__ mt, long long N, float hdt) {
     for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
-        const float f = -(vt[i] * gm[i] + vt[N + i] * gm[N + i] + vt[2 * N + i] * gm[2 * N + i]);
+        const float f = -(vt[i] * ldf(gm + i) + vt[N + i] * ldf(gm + N + i) + vt[2 * N + i] * ldf(gm + 2 * N + i));
         const float m = u[i] - hdt * f;
         lt[i] = -m;
         if (mt) mt[i] = m;
     }
 }
 
-__global__ void k_sub(const float *__restrict__ a, const float *__restrict__ b,
-                      float *__restrict__ out, long long N) {
+template <typename TB, typename TO>
+__global__ void k_sub(const float *__restrict__ a, const TB *__restrict__ b,
+                      TO *__restrict__ out, long long N) {
     for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT)
-        out[i] = a[i] - b[i];
+        stf(out + i, a[i] - ldf(b + i));
 }
 
 // body force by the trapezoidal rule: out_d = add_d + dt sum_j w_j l^j dm^j/dx_d
-__global__ void k_bodyforce(const float *__restrict__ lh, const float *__restrict__ gmh,
+template <typename TL, typename TG>
+__global__ void k_bodyforce(const TL *__restrict__ lh, const TG *__restrict__ gmh,
                             const float *__restrict__ add, float *__restrict__ out, long long N,
                             int nt, float dt) {
     for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
         float b1 = 0.f, b2 = 0.f, b3 = 0.f;
         for (int j = 0; j <= nt; ++j) {
             const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
-            const float l = w * lh[(long long)j * N + i];
-            const float *g = gmh + (long long)j * 3 * N;
-            b1 = fmaf(l, g[i], b1);
-            b2 = fmaf(l, g[N + i], b2);
-            b3 = fmaf(l, g[2 * N + i], b3);
+            const float l = w * ldf(lh + (long long)j * N + i);
+            const TG *g = gmh + (long long)j * 3 * N;
+            b1 = fmaf(l, ldf(g + i), b1);
+            b2 = fmaf(l, ldf(g + N + i), b2);
+            b3 = fmaf(l, ldf(g + 2 * N + i), b3);
         }
         if (add) {
             b1 += add[i];
@@ -722,18 +835,46 @@ void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float
     launch_pipe<SL_ADJFAC>(d, a, range_p, st);
 }
 
+namespace {
+template <typename TS>
+void state_step(const Dims &d, const TS *src, const float *dispm, const int *range_m, TS *dst, cudaStream_t st,
+                Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_STATE, st, (12.0 + 2 * sizeof(TS)) * d.N);
+    SlArgsT<TS, float> a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f};
+    launch_pipe<SL_PLAIN>(d, a, range_m, st);
+}
+template <typename TS>
+void adjoint_step(const Dims &d, const TS *src, const float *dispp, const int *range_p, const float *cfac,
+                  TS *dst, cudaStream_t st, Profiler *prof, int kclass) {
+    ProfScope ps(prof, kclass, st, (16.0 + 2 * sizeof(TS)) * d.N);
+    SlArgsT<TS, float> a{src, dispp, dst, cfac, nullptr, nullptr, 0.f};
+    launch_pipe<SL_ADJ>(d, a, range_p, st);
+}
+template <typename TG>
+void incstate_step(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+                   const float *vt, const TG *gm_next, float *dst, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_INCSTATE, st, (32.0 + 3 * sizeof(TG)) * d.N);
+    SlArgsT<float, TG> a{src, dispm, dst, nullptr, vt, gm_next, dt};
+    launch_pipe<SL_INCSTATE>(d, a, range_m, st);
+}
+}  // namespace
+
 void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
                        float *dst, cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_STATE, st, 20.0 * d.N);
-    SlArgs a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f};
-    launch_pipe<SL_PLAIN>(d, a, range_m, st);
+    state_step(d, src, dispm, range_m, dst, st, prof);
+}
+void launch_state_step(const Dims &d, const __half *src, const float *dispm, const int *range_m,
+                       __half *dst, cudaStream_t st, Profiler *prof) {
+    state_step(d, src, dispm, range_m, dst, st, prof);
 }
 
 void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
                          const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass) {
-    ProfScope ps(prof, kclass, st, 24.0 * d.N);
-    SlArgs a{src, dispp, dst, cfac, nullptr, nullptr, 0.f};
-    launch_pipe<SL_ADJ>(d, a, range_p, st);
+    adjoint_step(d, src, dispp, range_p, cfac, dst, st, prof, kclass);
+}
+void launch_adjoint_step(const Dims &d, const __half *src, const float *dispp, const int *range_p,
+                         const float *cfac, __half *dst, cudaStream_t st, Profiler *prof, int kclass) {
+    adjoint_step(d, src, dispp, range_p, cfac, dst, st, prof, kclass);
 }
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
@@ -741,13 +882,21 @@ void launch_incstate_init(const Dims &d, float dt, const float *vt, const float 
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 28.0 * d.N);
     k_incstate_init<<<grid1(d.N), PT, 0, st>>>(vt, gm0, u0, d.N, 0.5f * dt);
 }
+void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half *gm0, float *u0,
+                          cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 22.0 * d.N);
+    k_incstate_init<<<grid1(d.N), PT, 0, st>>>(vt, gm0, u0, d.N, 0.5f * dt);
+}
 
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
                           const int *range_m, const float *vt, const float *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_INCSTATE, st, 44.0 * d.N);
-    SlArgs a{src, dispm, dst, nullptr, vt, gm_next, dt};
-    launch_pipe<SL_INCSTATE>(d, a, range_m, st);
+    incstate_step(d, dt, src, dispm, range_m, vt, gm_next, dst, st, prof);
+}
+void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
+                          const int *range_m, const float *vt, const __half *gm_next, float *dst,
+                          cudaStream_t st, Profiler *prof) {
+    incstate_step(d, dt, src, dispm, range_m, vt, gm_next, dst, st, prof);
 }
 
 void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
@@ -756,10 +905,21 @@ void launch_incadj_init(const Dims &d, float dt, const float *u_last, const floa
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)d.N * (mt_out ? 36 : 32));
     k_incadj_init<<<grid1(d.N), PT, 0, st>>>(u_last, vt, gm_last, lt_last, mt_out, d.N, 0.5f * dt);
 }
+void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
+                        const __half *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
+                        Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)d.N * (mt_out ? 30 : 26));
+    k_incadj_init<<<grid1(d.N), PT, 0, st>>>(u_last, vt, gm_last, lt_last, mt_out, d.N, 0.5f * dt);
+}
 
 void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
                 Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 12.0 * d.N);
+    k_sub<<<grid1(d.N), PT, 0, st>>>(a, b, out, d.N);
+}
+void launch_sub(const Dims &d, const float *a, const __half *b, __half *out, cudaStream_t st,
+                Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 8.0 * d.N);
     k_sub<<<grid1(d.N), PT, 0, st>>>(a, b, out, d.N);
 }
 
@@ -776,10 +936,27 @@ void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float 
     k_adjoint_final<<<grid1(d.N), PT, 0, st>>>(l, m1, m, gm_final, gmis, inv_h3, d.N);
 }
 
+namespace {
+template <typename TL, typename TG>
+void bodyforce(const Dims &d, int nt, const TL *lhist, const TG *gmhist, const float *add, float *out,
+               cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st,
+                 (double)d.N * ((sizeof(TL) + 3.0 * sizeof(TG)) * (nt + 1) + 12 + (add ? 12 : 0)));
+    k_bodyforce<<<grid1(d.N), PT, 0, st>>>(lhist, gmhist, add, out, d.N, nt, 1.f / nt);
+}
+}  // namespace
+
 void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,
                       const float *add, float *out, cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, (double)d.N * (16.0 * (nt + 1) + 12 + (add ? 12 : 0)));
-    k_bodyforce<<<grid1(d.N), PT, 0, st>>>(lhist, gmhist, add, out, d.N, nt, 1.f / nt);
+    bodyforce(d, nt, lhist, gmhist, add, out, st, prof);
+}
+void launch_bodyforce(const Dims &d, int nt, const float *lhist, const __half *gmhist,
+                      const float *add, float *out, cudaStream_t st, Profiler *prof) {
+    bodyforce(d, nt, lhist, gmhist, add, out, st, prof);
+}
+void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *gmhist,
+                      const float *add, float *out, cudaStream_t st, Profiler *prof) {
+    bodyforce(d, nt, lhist, gmhist, add, out, st, prof);
 }
 
 }  // namespace claire

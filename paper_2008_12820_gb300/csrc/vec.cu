@@ -10,6 +10,7 @@
 // block reduces in FP64 by warp shuffles, block partials go to a fixed-size
 // array, and one block sums them in a fixed order: deterministic for a given
 // grid.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "claire_internal.cuh"
@@ -17,6 +18,9 @@
 namespace claire {
 
 namespace {
+
+__device__ __forceinline__ float ldv(const float *p) { return *p; }
+__device__ __forceinline__ float ldv(const __half *p) { return __half2float(*p); }
 
 constexpr int RT = 256;
 
@@ -64,13 +68,13 @@ struct Acc2 {
 };
 
 // MODE 0: sum a*b;  MODE 1: sum (a-b)^2
-template <int MODE>
-__global__ void __launch_bounds__(RT) k_reduce2(const float *__restrict__ a, const float *__restrict__ b,
+template <int MODE, typename TA = float>
+__global__ void __launch_bounds__(RT) k_reduce2(const TA *__restrict__ a, const float *__restrict__ b,
                                                 long long n, double *__restrict__ partial) {
     Acc2 acc;
     const long long stride = (long long)gridDim.x * RT;
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride) {
-        const float x = a[i], y = b[i];
+        const float x = ldv(a + i), y = b[i];
         if (MODE == 0) {
             acc.add_prod(x, y);
         } else {
@@ -253,8 +257,9 @@ __global__ void __launch_bounds__(RT) k_h0_apply(float *__restrict__ q, const fl
 // Body force of the Hessian matvec plus the carried beta*A p, and p . q:
 //   q_d = Ap_d + dt sum_j w_j l^j d_d m^j,   partial sums of sum_d p_d q_d
 // (fuses the PCG curvature product into the pass that writes q)
+template <typename TG>
 __global__ void __launch_bounds__(RT) k_bodyforce_dot(const float *__restrict__ lh,
-                                                      const float *__restrict__ gmh,
+                                                      const TG *__restrict__ gmh,
                                                       const float *__restrict__ Ap,
                                                       const float *__restrict__ p,
                                                       float *__restrict__ q, long long N, int nt,
@@ -266,10 +271,10 @@ __global__ void __launch_bounds__(RT) k_bodyforce_dot(const float *__restrict__ 
         for (int j = 0; j <= nt; ++j) {
             const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
             const float l = w * lh[(long long)j * N + i];
-            const float *g = gmh + (long long)j * 3 * N;
-            b1 = fmaf(l, g[i], b1);
-            b2 = fmaf(l, g[N + i], b2);
-            b3 = fmaf(l, g[2 * N + i], b3);
+            const TG *g = gmh + (long long)j * 3 * N;
+            b1 = fmaf(l, ldv(g + i), b1);
+            b2 = fmaf(l, ldv(g + N + i), b2);
+            b3 = fmaf(l, ldv(g + 2 * N + i), b3);
         }
         b1 += Ap[i];
         b2 += Ap[N + i];
@@ -283,6 +288,15 @@ __global__ void __launch_bounds__(RT) k_bodyforce_dot(const float *__restrict__ 
     }
     const double s = block_sum(acc.value());
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_f2h(const float *__restrict__ in, __half *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        out[i] = __float2half_rn(in[i]);
+}
+__global__ void k_h2f(const __half *__restrict__ in, float *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
+        out[i] = __half2float(in[i]);
 }
 
 inline int blocks_for(long long n) {
@@ -306,6 +320,24 @@ void launch_sqdiff(const float *a, const float *b, long long n, double *partial,
     const int nb = blocks_for(n);
     k_reduce2<1><<<nb, RT, 0, st>>>(a, b, n, partial);
     k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_sqdiff(const __half *a, const float *b, long long n, double *partial, double *dev_out,
+                   cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st, 6.0 * n, 2);
+    const int nb = blocks_for(n);
+    k_reduce2<1><<<nb, RT, 0, st>>>(a, b, n, partial);
+    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 6.0 * n);
+    k_f2h<<<blocks_for(n), RT, 0, st>>>(in, out, n);
+}
+
+void launch_h2f(const __half *in, float *out, long long n, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 6.0 * n);
+    k_h2f<<<blocks_for(n), RT, 0, st>>>(in, out, n);
 }
 
 void launch_pcg_xr(float *x, float *r, const float *p, const float *q, float alpha, long long n,
@@ -359,13 +391,25 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
     k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0);
 }
 
-void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
-                          const float *Ap, const float *p, float *q, double *partial,
-                          double *dev_out, cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, (double)N * (16.0 * (nt + 1) + 36), 2);
+template <typename TG>
+static void bodyforce_dot(long long N, int nt, const float *lhist, const TG *gmhist, const float *Ap,
+                          const float *p, float *q, double *partial, double *dev_out, cudaStream_t st,
+                          Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, (double)N * ((4.0 + 3 * sizeof(TG)) * (nt + 1) + 36), 2);
     const int nb = blocks_for(N);
     k_bodyforce_dot<<<nb, RT, 0, st>>>(lhist, gmhist, Ap, p, q, N, nt, 1.f / nt, partial);
     k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+}
+
+void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
+                          const float *Ap, const float *p, float *q, double *partial,
+                          double *dev_out, cudaStream_t st, Profiler *prof) {
+    bodyforce_dot(N, nt, lhist, gmhist, Ap, p, q, partial, dev_out, st, prof);
+}
+void launch_bodyforce_dot(long long N, int nt, const float *lhist, const __half *gmhist,
+                          const float *Ap, const float *p, float *q, double *partial,
+                          double *dev_out, cudaStream_t st, Profiler *prof) {
+    bodyforce_dot(N, nt, lhist, gmhist, Ap, p, q, partial, dev_out, st, prof);
 }
 
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
