@@ -42,10 +42,17 @@ METRIC = ("Hessian matvec Gvoxel/s and GN solve time @256³; % of HBM roofline; 
           "err vs FP64")
 UNIT = "Gvoxel/s"
 WORKLOAD = "blob256"
-WORKLOAD_DESC = ("256^3 synthetic brain-like blob images (12 ellipsoids, sigma 2 voxels), "
-                 "reference warped by a band-limited displacement (|k|<=6, max 4 voxels); "
-                 "nt=4, beta=1e-2, gamma=1, cubic SL, spectral ops, PC InvA, "
-                 "full GN-Krylov solve to 5e-2 from v=0")
+WORKLOAD_DESCS = {
+    "blob256": ("256^3 synthetic brain-like blob images (12 ellipsoids, sigma 2 voxels), "
+                "reference warped by a band-limited displacement (|k|<=6, max 4 voxels); "
+                "nt=4, beta=1e-2, gamma=1, cubic SL, spectral ops, PC InvA, "
+                "full GN-Krylov solve to 5e-2 from v=0"),
+    "blob768": ("768^3 synthetic brain-like blob images (60 ellipsoids, sigma 3 voxels), "
+                "reference warped by a band-limited displacement (|k|<=6, max 4 voxels); "
+                "nt=8, beta=1e-2, gamma=1, cubic SL, spectral ops, PC InvA, "
+                "full GN-Krylov solve to 5e-2 from v=0"),
+}
+WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 CPU_SAMPLE_N = 64        # oracle solves the same generator on a 64^3 grid
 ERR_CHECK_N = 128        # GPU vs oracle gradient / matvec on a 128^3 instance
 
@@ -70,6 +77,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"],
+                    help="fp16: stored state / adjoint trajectories in FP16 (FP32 arithmetic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", type=int, default=0,
@@ -203,7 +212,7 @@ def run_ours(args):
     m0 = torch.from_numpy(w["m0"]).cuda()
     m1 = torch.from_numpy(w["m1"]).cuda()
     v = torch.zeros((3,) + shape, device="cuda")
-    reg = claire.Registration(shape, nt, beta, gamma)
+    reg = claire.Registration(shape, nt, beta, gamma, precision=args.precision)
     reg.set_images(m0, m1)
     stream = torch.cuda.current_stream()
 
@@ -277,9 +286,10 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "grid": list(shape), "nt": nt, "beta": beta,
-                   "gamma": gamma, "precond": "InvA", "eps_n": 5e-2,
-                   "l2": "inputs larger than L2 (working set ~5 GB)",
+        "config": {"workload": WORKLOAD_DESCS.get(args.workload, args.workload), "grid": list(shape),
+                   "nt": nt, "beta": beta, "gamma": gamma, "precond": "InvA", "eps_n": 5e-2,
+                   "storage": "fp16 trajectories" if args.precision == "fp16" else "fp32",
+                   "l2": f"inputs larger than L2 (working set {reg.workspace_bytes() / 1e9:.1f} GB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "gn_solve_time_s": round(ms * 1e-3, 5),
         "hess_matvec_gvoxel_s": round(mv_gvox, 4), "hess_matvec_ms": round(mv_ms, 4),
@@ -325,7 +335,7 @@ def run_ours(args):
     # ---- CPU baseline (FP64 oracle) and error vs FP64, rank 0 at N = 1 ------
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample()
-        out["err_vs_fp64"] = error_vs_oracle(claire, synth)
+        out["err_vs_fp64"] = error_vs_oracle(claire, synth, args.precision)
     reg.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -357,7 +367,7 @@ def cpu_baseline_sample(steps=1):
             "seconds": round(t, 3)}
 
 
-def error_vs_oracle(claire, synth):
+def error_vs_oracle(claire, synth, precision="fp32"):
     """Relative L2 error of the GPU gradient, objective and Hessian matvec
     against the FP64 oracle on the 128^3 instance of the same generator."""
     import numpy as np
@@ -371,7 +381,7 @@ def error_vs_oracle(claire, synth):
     P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
     go, Jo = P.gradient(v)
     Ho = P.matvec(vt)
-    with claire.Registration((n, n, n), w["nt"], w["beta"], w["gamma"]) as reg:
+    with claire.Registration((n, n, n), w["nt"], w["beta"], w["gamma"], precision=precision) as reg:
         reg.set_images(torch.from_numpy(w["m0"]).cuda(), torch.from_numpy(w["m1"]).cuda())
         g, J = reg.gradient(torch.from_numpy(v).cuda())
         H = reg.hess_matvec(None, torch.from_numpy(vt).cuda())
@@ -390,7 +400,7 @@ def error_vs_oracle(claire, synth):
         eb = sum(float(np.sum(np.abs(np.fft.fftn(b[c])) ** 2 * wgt)) for c in range(3))
         return (ea / eb) ** 0.5
 
-    return {"grid": [n, n, n], "gradient": rel(g, go), "hess_matvec": rel(H, Ho),
+    return {"grid": [n, n, n], "storage": precision, "gradient": rel(g, go), "hess_matvec": rel(H, Ho),
             "objective": abs(J - Jo) / abs(Jo), "gradient_Hm1": rel_hm1(g, go),
             "hess_matvec_Hm1": rel_hm1(H, Ho),
             "note": "L2 errors of fields containing beta*A of a smooth field sit at the FP32 "

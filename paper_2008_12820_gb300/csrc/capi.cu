@@ -115,12 +115,15 @@ struct claire_ctx {
     float *mhist = nullptr, *gmhist = nullptr, *divv = nullptr, *cfac = nullptr;
     float *lhist = nullptr, *mt = nullptr;
     // FP16-storage form: the state trajectory m^j, its gradient grad m^j and
-    // the gradient's adjoint lambda^j are stored in FP16 (the incremental
-    // fields of the matvec stay FP32, their scale follows the PCG direction);
-    // gm1f holds grad m(1) in FP32 for the H0 preconditioners, m0h = m0 in FP16
+    // the gradient's adjoint lambda^j are stored in FP16.  The transport itself
+    // runs in FP32 (two scratch fields in turn, each step also writing the FP16
+    // copy), grad m^j is taken of the FP32 state before it is rounded, and the
+    // final state m(1) is kept in FP32 (m1f) for the mismatch and lambda(1).
+    // The incremental fields of the matvec stay FP32 (their scale follows the
+    // PCG direction); gm1f holds grad m(1) in FP32 for the H0 preconditioners.
     bool h16 = false;
-    __half *mhist_h = nullptr, *gmhist_h = nullptr, *lhist_h = nullptr, *mhist_t_h = nullptr, *m0h = nullptr;
-    float *gm1f = nullptr;
+    __half *mhist_h = nullptr, *gmhist_h = nullptr, *lhist_h = nullptr;
+    float *gm1f = nullptr, *m1f = nullptr;
     float *s3a = nullptr, *s1a = nullptr, *s1b = nullptr, *fdisp = nullptr;
     float2 *spec = nullptr;
     double *partial = nullptr, *dres = nullptr;
@@ -321,7 +324,7 @@ struct claire_ctx {
         if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
         else spectral(OP_GRAD, f, g, nullptr);
     }
-    void grad_h(const __half *f, __half *g) {
+    void grad_h(const float *f, __half *g) {
         if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
         else spectral_grad_h(d, ax, f, g, spec, st, &prof);
     }
@@ -338,24 +341,32 @@ struct claire_ctx {
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         if (state_ready) {
             launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), st, &prof);
+        } else if (h16) {
+            // FP32 transport; FP16 copies of m^j and of grad m^j (taken of the
+            // FP32 state); m(1) and grad m(1) also kept in FP32
+            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
+            launch_f2h(m0, mhist_h, (long long)N, st, &prof);
+            if (!gm0_valid) grad_h(m0, hist(gmhist_h, 0, 3));
+            const float *src = m0;
+            float *a = s1a, *b = s1b;
+            for (int j = 0; j < nt; ++j) {
+                float *dst = j + 1 == nt ? m1f : a;
+                launch_state_step(d, src, dispm, rng_m(), dst, st, &prof, hist(mhist_h, j + 1));
+                if (j + 1 < nt) grad_h(dst, hist(gmhist_h, j + 1, 3));
+                src = dst;
+                std::swap(a, b);
+            }
+            grad(m1f, gm1f);
+            launch_f2h(gm1f, hist(gmhist_h, nt, 3), 3 * (long long)N, st, &prof);
         } else {
             launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
-            if (h16) {
-                CK(cudaMemcpyAsync(mhist_h, m0h, N * sizeof(__half), cudaMemcpyDeviceToDevice, st));
-                for (int j = 0; j < nt; ++j)
-                    launch_state_step(d, hist(mhist_h, j), dispm, rng_m(), hist(mhist_h, j + 1), st, &prof);
-            } else {
-                CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-                for (int j = 0; j < nt; ++j)
-                    launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
-            }
+            CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            for (int j = 0; j < nt; ++j)
+                launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
         }
-        for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) {
-            if (h16) grad_h(hist(mhist_h, j), hist(gmhist_h, j, 3));
-            else grad(hist(mhist, j), hist(gmhist, j, 3));
-        }
+        if (!h16)
+            for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
         gm0_valid = true;
-        if (h16) launch_h2f(hist(gmhist_h, nt, 3), gm1f, 3 * (long long)N, st, &prof);
         div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
@@ -371,10 +382,15 @@ struct claire_ctx {
         linearize(v, state_ready);
         const size_t N = d.N;
         if (h16) {
-            launch_sub(d, m1, hist(mhist_h, nt), hist(lhist_h, nt), st, &prof);
-            for (int j = nt; j >= 1; --j)
-                launch_adjoint_step(d, hist(lhist_h, j), dispp, rng_p(), cfac, hist(lhist_h, j - 1), st, &prof,
-                                    CLAIRE_K_ADJOINT);
+            // FP32 adjoint transport with FP16 copies of lambda^j
+            float *a = s1a, *b = s1b;
+            launch_sub(d, m1, m1f, a, st, &prof);
+            launch_f2h(a, hist(lhist_h, nt), (long long)N, st, &prof);
+            for (int j = nt; j >= 1; --j) {
+                launch_adjoint_step(d, a, dispp, rng_p(), cfac, b, st, &prof, CLAIRE_K_ADJOINT,
+                                    hist(lhist_h, j - 1));
+                std::swap(a, b);
+            }
         } else {
             launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
             for (int j = nt; j >= 1; --j)
@@ -526,19 +542,16 @@ struct claire_ctx {
         return src;
     }
 
-    // the forward solve of the line search: m^j for v into mhist_t (j >= 1)
-    // with the X- foot points in fdisp; returns the mismatch 1/2 ||m(1) - m1||^2
+    // the forward solve of the line search; returns 1/2 h^3 ||m(1) - m1||^2.
+    // The FP32 form keeps the trial's states (m^j into mhist_t, X- in fdisp):
+    // an accepted trial becomes the next linearization as it stands.  The
+    // FP16-storage form stores grad m^j of the FP32 states, which the trial does
+    // not make, so it transports in FP32 scratch and its linearization
+    // recomputes the state.
+    bool keeps_trial() const { return !h16; }
     double trial_mismatch(const float *v) {
+        if (h16) return mismatch_of(forward(v));
         launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
-        if (h16) {
-            if (!mhist_t_h) mhist_t_h = alloc_h((size_t)(nt + 1) * d.N);
-            for (int j = 0; j < nt; ++j)
-                launch_state_step(d, j == 0 ? m0h : hist(mhist_t_h, j), fdisp, rng_f(), hist(mhist_t_h, j + 1),
-                                  st, &prof);
-            check_launch("forward_trial");
-            launch_sqdiff(hist(mhist_t_h, nt), m1, d.N, partial, dres, st, &prof);
-            return 0.5 * h3() * fetch();
-        }
         if (!mhist_t) mhist_t = alloc_f((size_t)(nt + 1) * d.N);
         const float *src = m0;
         for (int j = 0; j < nt; ++j) {
@@ -552,18 +565,12 @@ struct claire_ctx {
     void adopt_trial() {
         std::swap(dispm, fdisp);
         std::swap(off_m, off_f);
-        if (h16) {
-            std::swap(mhist_h, mhist_t_h);
-            CK(cudaMemcpyAsync(mhist_h, m0h, d.N * sizeof(__half), cudaMemcpyDeviceToDevice, st));
-        } else {
-            std::swap(mhist, mhist_t);
-            CK(cudaMemcpyAsync(mhist, m0, d.N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-        }
+        std::swap(mhist, mhist_t);
+        CK(cudaMemcpyAsync(mhist, m0, d.N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
     // 1/2 h^3 ||m(1) - m1||^2 of the linearization's state
     double final_mismatch() {
-        if (h16) launch_sqdiff(hist(mhist_h, nt), m1, d.N, partial, dres, st, &prof);
-        else launch_sqdiff(hist(mhist, nt), m1, d.N, partial, dres, st, &prof);
+        launch_sqdiff(h16 ? m1f : hist(mhist, nt), m1, d.N, partial, dres, st, &prof);
         return 0.5 * h3() * fetch();
     }
 
@@ -674,8 +681,8 @@ int claire_create_ex(int nx, int ny, int nz, int nt, double beta, double gamma, 
             c->mhist_h = c->alloc_h((size_t)(nt + 1) * N);
             c->gmhist_h = c->alloc_h((size_t)(nt + 1) * 3 * N);
             c->lhist_h = c->alloc_h((size_t)(nt + 1) * N);
-            c->m0h = c->alloc_h(N);
             c->gm1f = c->alloc_f(3 * N);
+            c->m1f = c->alloc_f(N);
         } else {
             c->mhist = c->alloc_f((size_t)(nt + 1) * N);
             c->gmhist = c->alloc_f((size_t)(nt + 1) * 3 * N);
@@ -734,7 +741,6 @@ int claire_set_images(claire_ctx *ctx, const float *m0, const float *m1) {
     const size_t b = ctx->d.N * sizeof(float);
     CK(cudaMemcpyAsync(ctx->m0, m0, b, cudaMemcpyDeviceToDevice, ctx->st));
     CK(cudaMemcpyAsync(ctx->m1, m1, b, cudaMemcpyDeviceToDevice, ctx->st));
-    if (ctx->h16) launch_f2h(ctx->m0, ctx->m0h, ctx->d.N, ctx->st, nullptr);
     ctx->have_images = true;
     ctx->have_lin = false;
     ctx->gm0_valid = false;
@@ -1092,11 +1098,11 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         }
         CK(cudaMemcpyAsync(v, vn, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
         launch_axpby(Av, 1.f, Av, (float)alpha, Ax, n3, st, &ctx->prof);
-        ctx->adopt_trial();
+        if (ctx->keeps_trial()) ctx->adopt_trial();
         ++k;
         {
             EvTimer t(st, &rep.t_grad_ms);
-            ctx->gradient(v, g, &J, nullptr, Av, true);
+            ctx->gradient(v, g, &J, nullptr, Av, ctx->keeps_trial());
         }
         vAv = ctx->last_vAv;
         gn = std::sqrt(ctx->dot(g, g, n3));

@@ -93,10 +93,13 @@ void launch_interp(const Dims &d, const float *f, const float *disp, float *out,
                    cudaStream_t st, Profiler *prof, int kclass);
 void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
                            const int *range_p, float *cfac, cudaStream_t st, Profiler *prof);
+// dst_h (optional): an FP16 copy of dst, the stored trajectory of the
+// FP16-storage form
 void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
-                       float *dst, cudaStream_t st, Profiler *prof);
+                       float *dst, cudaStream_t st, Profiler *prof, __half *dst_h = nullptr);
 void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
-                         const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass);
+                         const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass,
+                         __half *dst_h = nullptr);
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
                           cudaStream_t st, Profiler *prof);
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
@@ -118,11 +121,7 @@ void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gm
                       const float *add, float *out, cudaStream_t st, Profiler *prof);
 
 // FP16-storage form: the stored trajectories (m^j, grad m^j, lambda^j) are
-// FP16; these overloads take them as such and compute in FP32
-void launch_state_step(const Dims &d, const __half *src, const float *dispm, const int *range_m,
-                       __half *dst, cudaStream_t st, Profiler *prof);
-void launch_adjoint_step(const Dims &d, const __half *src, const float *dispp, const int *range_p,
-                         const float *cfac, __half *dst, cudaStream_t st, Profiler *prof, int kclass);
+// FP16; these overloads read them as such and compute in FP32
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half *gm0, float *u0,
                           cudaStream_t st, Profiler *prof);
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
@@ -131,8 +130,6 @@ void launch_incstate_step(const Dims &d, float dt, const float *src, const float
 void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
                         const __half *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
                         Profiler *prof);
-void launch_sub(const Dims &d, const float *a, const __half *b, __half *out, cudaStream_t st,
-                Profiler *prof);
 void launch_bodyforce(const Dims &d, int nt, const float *lhist, const __half *gmhist,
                       const float *add, float *out, cudaStream_t st, Profiler *prof);
 void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *gmhist,
@@ -140,15 +137,13 @@ void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *
 void launch_bodyforce_dot(long long N, int nt, const float *lhist, const __half *gmhist,
                           const float *Ap, const float *p, float *q, double *partial,
                           double *dev_out, cudaStream_t st, Profiler *prof);
-void launch_sqdiff(const __half *a, const float *b, long long n, double *partial,
-                   double *dev_out, cudaStream_t st, Profiler *prof);
 // FP16 <-> FP32 copies of n values
 void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof);
 void launch_h2f(const __half *in, float *out, long long n, cudaStream_t st, Profiler *prof);
-// first derivatives of an FP16 scalar field into an FP16 vector field
-void spectral_grad_h(const Dims &d, const FftPlan *ax, const __half *in, __half *out, float2 *spec,
+// first derivatives of an FP32 scalar field stored as an FP16 vector field
+void spectral_grad_h(const Dims &d, const FftPlan *ax, const float *in, __half *out, float2 *spec,
                      cudaStream_t st, Profiler *prof);
-void launch_grad_fd8(const Dims &d, const __half *f, __half *g, cudaStream_t st, Profiler *prof);
+void launch_grad_fd8(const Dims &d, const float *f, __half *g, cudaStream_t st, Profiler *prof);
 
 // ------------------------------------------------------------- vectors ----
 // FP64 reductions; results land in dev_out[0..k) (device doubles)

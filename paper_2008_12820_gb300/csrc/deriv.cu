@@ -18,9 +18,8 @@ constexpr int DX = 32, DY = 8;
 
 __device__ __forceinline__ int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// FP32 fields, or FP16 ones in the FP16-storage form (FP32 arithmetic)
+// outputs are FP32, or FP16 in the FP16-storage form (FP32 arithmetic)
 __device__ __forceinline__ float ldd(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ldd(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ void std_(float *p, float v) { *p = v; }
 __device__ __forceinline__ void std_(__half *p, float v) { *p = __float2half_rn(v); }
 
@@ -38,8 +37,8 @@ __device__ __forceinline__ float fd8(const T *__restrict__ f, long long o, int i
     return r * ih;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(DX * DY) k_grad_fd8(const T *__restrict__ f, T *__restrict__ g,
+template <typename TO>
+__global__ void __launch_bounds__(DX * DY) k_grad_fd8(const float *__restrict__ f, TO *__restrict__ g,
                                                       Dims d, float ih1, float ih2, float ih3) {
     const int i3 = blockIdx.x * DX + threadIdx.x, i2 = blockIdx.y * DY + threadIdx.y, i1 = blockIdx.z;
     if (i3 >= d.n3 || i2 >= d.n2) return;
@@ -71,9 +70,9 @@ void launch_grad_fd8(const Dims &d, const float *f, float *g, cudaStream_t st, P
                                                    (float)(d.n3 / tp));
 }
 
-void launch_grad_fd8(const Dims &d, const __half *f, __half *g, cudaStream_t st, Profiler *prof) {
+void launch_grad_fd8(const Dims &d, const float *f, __half *g, cudaStream_t st, Profiler *prof) {
     const double tp = 6.283185307179586476925286766559;
-    ProfScope ps(prof, CLAIRE_K_FD, st, 8.0 * d.N);
+    ProfScope ps(prof, CLAIRE_K_FD, st, 10.0 * d.N);
     k_grad_fd8<<<grid_d(d), dim3(DX, DY), 0, st>>>(f, g, d, (float)(d.n1 / tp), (float)(d.n2 / tp),
                                                    (float)(d.n3 / tp));
 }

@@ -29,7 +29,6 @@ namespace {
 
 // real fields are FP32, or FP16 in the FP16-storage form (FP32 arithmetic)
 __device__ __forceinline__ float ldr(const float *p) { return *p; }
-__device__ __forceinline__ float ldr(const __half *p) { return __half2float(*p); }
 __device__ __forceinline__ void str(float *p, float v) { *p = v; }
 __device__ __forceinline__ void str(__half *p, float v) { *p = __float2half_rn(v); }
 
@@ -757,9 +756,9 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
     }
 }
 
-void spectral_grad_h(const Dims &d, const FftPlan *ax, const __half *in, __half *out, float2 *spec,
+void spectral_grad_h(const Dims &d, const FftPlan *ax, const float *in, __half *out, float2 *spec,
                      cudaStream_t st, Profiler *prof) {
-    const double R = 2.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
+    const double R = 4.0 * d.N, Rh = 2.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
     const SpecParams sp{0.f, 0.f, (float)(1.0 / (double)d.N)};
     {
         ProfScope ps(prof, CLAIRE_K_FFT_R2C, st, R + C);
@@ -778,7 +777,7 @@ void spectral_grad_h(const Dims &d, const FftPlan *ax, const __half *in, __half 
         c2c_x2(d, ax[1], spec, 3, +1.f, st);
     }
     {
-        ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, 3 * (R + C));
+        ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, 3 * (Rh + C));
         c2r_x3(d, ax[2], spec, out, nullptr, 3, st);
     }
 }

@@ -39,7 +39,6 @@ constexpr int BX = 32, BY = 8;
 __device__ __forceinline__ float ldf(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ldf(const __half *p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ void stf(float *p, float v) { *p = v; }
-__device__ __forceinline__ void stf(__half *p, float v) { *p = __float2half_rn(v); }
 
 // cubic Lagrange basis on the nodes -1, 0, 1, 2 evaluated at t in [0, 1)
 __device__ __forceinline__ void lagrange4(float t, float w[4]) {
@@ -195,6 +194,7 @@ struct SlArgsT {
     const float *vt;    // SL_INCSTATE: vt [3][N]
     const TG *gm;       // SL_INCSTATE: grad m^{j+1} [3][N]
     float dt;
+    __half *dst_h = nullptr;  // SL_PLAIN / SL_ADJ: optional FP16 copy of dst (stored trajectories)
 };
 using SlArgs = SlArgsT<float, float>;
 
@@ -284,8 +284,11 @@ template <int MODE, typename A>
 __device__ __forceinline__ void sl_epilogue(const A &a, long long id, float val, const float *e) {
     if (MODE == SL_PLAIN) {
         stf(a.dst + id, val);
+        if (a.dst_h) a.dst_h[id] = __float2half_rn(val);
     } else if (MODE == SL_ADJ) {
-        stf(a.dst + id, e[0] * val);
+        const float r = e[0] * val;
+        stf(a.dst + id, r);
+        if (a.dst_h) a.dst_h[id] = __float2half_rn(r);
     } else if (MODE == SL_ADJFAC) {
         const float dx = e[0];
         stf(a.dst + id, 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val);
@@ -360,67 +363,6 @@ __device__ __forceinline__ void box_copy(const float *__restrict__ src, const Di
     cp_async_commit();
 }
 
-// FP16 source fields: the box is widened to FP32 in shared memory, so the
-// interpolation below is the same.  Chunked (n3 a multiple of 8 and a 16-byte
-// aligned field): each thread loads up to HB_PER 16-byte chunks of 8 halves
-// into registers (issued before the current tile is computed) and widens and
-// stores them after it; rows start at lo3 rounded down to a multiple of 8.
-// Otherwise the box is copied element by element, synchronously.
-constexpr int HBOX_CH = 6;  // 16-byte chunks (8 halves) per box row
-static_assert(8 * HBOX_CH >= BS3 + 7 && 8 * HBOX_CH <= BOX_PITCH, "FP16 box row must cover the shifted row");
-constexpr int HB_PER = (BOX_ROWS * HBOX_CH + PT3 * PT2 - 1) / (PT3 * PT2);
-
-__device__ __forceinline__ int hbox_shift(int lo3, bool chunked) { return chunked ? lo3 - (lo3 & ~7) : 0; }
-
-struct HStage {
-    uint4 q[HB_PER];
-};
-
-__device__ __forceinline__ void hbox_load(const __half *__restrict__ src, const Dims &d, long long plane, int lo1,
-                                          int lo2, int lo3, HStage &hs) {
-    const int tid = threadIdx.y * PT3 + threadIdx.x;
-    const int x0 = lo3 & ~7;
-#pragma unroll
-    for (int i = 0; i < HB_PER; ++i) {
-        const int e = tid + i * PT3 * PT2;
-        if (e < BOX_ROWS * HBOX_CH) {
-            const int row = e / HBOX_CH, ch = e - row * HBOX_CH;
-            const int z = row / BS2, y = row - z * BS2;
-            const __half *g = src + wrap_index(lo1 + z, d.n1) * plane + (long long)wrap_index(lo2 + y, d.n2) * d.n3 +
-                              wrap_index(x0 + 8 * ch, d.n3);
-            hs.q[i] = __ldg(reinterpret_cast<const uint4 *>(g));
-        }
-    }
-}
-
-__device__ __forceinline__ void hbox_store(const HStage &hs, float *buf) {
-    const int tid = threadIdx.y * PT3 + threadIdx.x;
-#pragma unroll
-    for (int i = 0; i < HB_PER; ++i) {
-        const int e = tid + i * PT3 * PT2;
-        if (e < BOX_ROWS * HBOX_CH) {
-            const int row = e / HBOX_CH, ch = e - row * HBOX_CH;
-            const __half2 *h = reinterpret_cast<const __half2 *>(&hs.q[i]);
-            const float2 a = __half22float2(h[0]), b = __half22float2(h[1]);
-            const float2 c = __half22float2(h[2]), e2 = __half22float2(h[3]);
-            float4 *dst = reinterpret_cast<float4 *>(buf + row * BOX_PITCH + 8 * ch);
-            dst[0] = make_float4(a.x, a.y, b.x, b.y);
-            dst[1] = make_float4(c.x, c.y, e2.x, e2.y);
-        }
-    }
-}
-
-__device__ __forceinline__ void hbox_copy_sync(const __half *__restrict__ src, const Dims &d, long long plane,
-                                               int lo1, int lo2, int lo3, float *buf) {
-    const int tid = threadIdx.y * PT3 + threadIdx.x;
-    for (int e = tid; e < BOX_ROWS * BS3; e += PT3 * PT2) {
-        const int row = e / BS3, x = e - row * BS3;
-        const int z = row / BS2, y = row - z * BS2;
-        buf[row * BOX_PITCH + x] = ldf(src + wrap_index(lo1 + z, d.n1) * plane +
-                                       (long long)wrap_index(lo2 + y, d.n2) * d.n3 + wrap_index(lo3 + x, d.n3));
-    }
-}
-
 // 64-tap tricubic sum from a box position; pairs of rows go through the
 // paired FP32 instructions (FMUL2/FFMA2), the x2 and x1 contractions too
 __device__ __forceinline__ float box_cubic(const float *p, const float w1[4], const float w2[4], const float w3[4]) {
@@ -461,9 +403,7 @@ __device__ __forceinline__ float box_linear(const float *p, float u1, float u2, 
 
 // resident blocks per SM: the incremental-state step carries six epilogue
 // inputs per voxel and keeps two; the others fit three
-template <int MODE, typename TS = float> struct SlOcc {
-    static constexpr int v = (MODE == SL_INCSTATE || !std::is_same<TS, float>::value) ? 2 : 3;
-};
+template <int MODE> struct SlOcc { static constexpr int v = MODE == SL_INCSTATE ? 2 : 3; };
 
 // tiles of block b: a contiguous range, so neighbouring tiles (which share
 // halo rows in L2) run on the same block one after the other
@@ -473,10 +413,10 @@ __device__ __forceinline__ void tile_range(int ntiles, int &tbeg, int &tend) {
 }
 
 template <int MODE, int ORDER, typename TS = float, typename TG = float>
-__global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE, TS>::v)
+__global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE>::v)
 k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_in) {
+    static_assert(std::is_same<TS, float>::value, "the box path stages FP32 source fields");
     constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
-    constexpr bool HALF = !std::is_same<TS, float>::value;
     extern __shared__ float smem[];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool chunked = chunked_in != 0;
@@ -511,8 +451,7 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
     }
 
     auto issue_box = [&](int t1, int t2, int t3, float *buf) {
-        if constexpr (!HALF)
-            box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
+        box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
     };
     auto load_regs = [&](int t1, int t2, int t3, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
         const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
@@ -532,18 +471,7 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
     // tile counters of the next tile to fetch (x3 fastest)
     int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
     float nd[PT1][3], ne[PT1][NE];
-    HStage hs;  // FP16 staging (unused for FP32 sources)
-    if constexpr (HALF) {
-        const int lo1 = c1 * PT1 + fmn0 - 1, lo2 = c2 * PT2 + fmn1 - 1, lo3 = c3 * PT3 + fmn2 - 1;
-        if (chunked) {
-            hbox_load(a.src, d, plane, lo1, lo2, lo3, hs);
-            hbox_store(hs, smem);
-        } else {
-            hbox_copy_sync(a.src, d, plane, lo1, lo2, lo3, smem);
-        }
-    } else {
-        issue_box(c1, c2, c3, smem);
-    }
+    issue_box(c1, c2, c3, smem);
     load_regs(c1, c2, c3, nd, ne);
     int cur = 0;
     for (int tile = tbeg; tile < tend; ++tile) {
@@ -560,13 +488,7 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
 #pragma unroll
             for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
         }
-        const bool more = tile + 1 < tend;
-        if constexpr (HALF) {
-            if (more) {
-                if (chunked) hbox_load(a.src, d, plane, c1 * PT1 + fmn0 - 1, c2 * PT2 + fmn1 - 1, c3 * PT3 + fmn2 - 1, hs);
-                load_regs(c1, c2, c3, nd, ne);
-            }
-        } else if (more) {
+        if (tile + 1 < tend) {
             issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
             load_regs(c1, c2, c3, nd, ne);
             cp_async_wait<1>();
@@ -577,7 +499,7 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
         const float *bx = smem + cur * BOX_FLOATS;
         const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
         const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
-        const int sh = HALF ? hbox_shift(t3 * PT3 + fmn2 - 1, chunked) : box_shift(t3 * PT3 + fmn2 - 1, chunked);
+        const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
         if (i3 < d.n3 && i2 < d.n2) {
 #pragma unroll
             for (int t = 0; t < PT1; ++t) {
@@ -598,13 +520,6 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
                     }
                     sl_epilogue<MODE>(a, id0 + t * plane, acc, ce[t]);
                 }
-            }
-        }
-        if constexpr (HALF) {
-            if (more) {
-                float *nbuf = smem + (cur ^ 1) * BOX_FLOATS;
-                if (chunked) hbox_store(hs, nbuf);
-                else hbox_copy_sync(a.src, d, plane, c1 * PT1 + fmn0 - 1, c2 * PT2 + fmn1 - 1, c3 * PT3 + fmn2 - 1, nbuf);
             }
         }
         __syncthreads();
@@ -695,7 +610,7 @@ template <int MODE, int ORDER, typename TS, typename TG>
 void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
     cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER, TS, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_sl_pipe<MODE, ORDER, TS, TG><<<pipe_blocks(d, SlOcc<MODE, TS>::v), dim3(PT3, PT2), smem, st>>>(
+    k_sl_pipe<MODE, ORDER, TS, TG><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(
         a, d, range, chunk_ok(d, a.src));
 }
 
@@ -835,21 +750,22 @@ void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float
     launch_pipe<SL_ADJFAC>(d, a, range_p, st);
 }
 
-namespace {
-template <typename TS>
-void state_step(const Dims &d, const TS *src, const float *dispm, const int *range_m, TS *dst, cudaStream_t st,
-                Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_STATE, st, (12.0 + 2 * sizeof(TS)) * d.N);
-    SlArgsT<TS, float> a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f};
+void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
+                       float *dst, cudaStream_t st, Profiler *prof, __half *dst_h) {
+    ProfScope ps(prof, CLAIRE_K_STATE, st, (20.0 + (dst_h ? 2 : 0)) * d.N);
+    SlArgs a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f, dst_h};
     launch_pipe<SL_PLAIN>(d, a, range_m, st);
 }
-template <typename TS>
-void adjoint_step(const Dims &d, const TS *src, const float *dispp, const int *range_p, const float *cfac,
-                  TS *dst, cudaStream_t st, Profiler *prof, int kclass) {
-    ProfScope ps(prof, kclass, st, (16.0 + 2 * sizeof(TS)) * d.N);
-    SlArgsT<TS, float> a{src, dispp, dst, cfac, nullptr, nullptr, 0.f};
+
+void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
+                         const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass,
+                         __half *dst_h) {
+    ProfScope ps(prof, kclass, st, (24.0 + (dst_h ? 2 : 0)) * d.N);
+    SlArgs a{src, dispp, dst, cfac, nullptr, nullptr, 0.f, dst_h};
     launch_pipe<SL_ADJ>(d, a, range_p, st);
 }
+
+namespace {
 template <typename TG>
 void incstate_step(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
                    const float *vt, const TG *gm_next, float *dst, cudaStream_t st, Profiler *prof) {
@@ -858,24 +774,6 @@ void incstate_step(const Dims &d, float dt, const float *src, const float *dispm
     launch_pipe<SL_INCSTATE>(d, a, range_m, st);
 }
 }  // namespace
-
-void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
-                       float *dst, cudaStream_t st, Profiler *prof) {
-    state_step(d, src, dispm, range_m, dst, st, prof);
-}
-void launch_state_step(const Dims &d, const __half *src, const float *dispm, const int *range_m,
-                       __half *dst, cudaStream_t st, Profiler *prof) {
-    state_step(d, src, dispm, range_m, dst, st, prof);
-}
-
-void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
-                         const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass) {
-    adjoint_step(d, src, dispp, range_p, cfac, dst, st, prof, kclass);
-}
-void launch_adjoint_step(const Dims &d, const __half *src, const float *dispp, const int *range_p,
-                         const float *cfac, __half *dst, cudaStream_t st, Profiler *prof, int kclass) {
-    adjoint_step(d, src, dispp, range_p, cfac, dst, st, prof, kclass);
-}
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
                           cudaStream_t st, Profiler *prof) {
@@ -915,11 +813,6 @@ void launch_incadj_init(const Dims &d, float dt, const float *u_last, const floa
 void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
                 Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 12.0 * d.N);
-    k_sub<<<grid1(d.N), PT, 0, st>>>(a, b, out, d.N);
-}
-void launch_sub(const Dims &d, const float *a, const __half *b, __half *out, cudaStream_t st,
-                Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 8.0 * d.N);
     k_sub<<<grid1(d.N), PT, 0, st>>>(a, b, out, d.N);
 }
 

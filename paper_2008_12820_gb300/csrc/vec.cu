@@ -322,14 +322,6 @@ void launch_sqdiff(const float *a, const float *b, long long n, double *partial,
     k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
-void launch_sqdiff(const __half *a, const float *b, long long n, double *partial, double *dev_out,
-                   cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_REDUCE, st, 6.0 * n, 2);
-    const int nb = blocks_for(n);
-    k_reduce2<1><<<nb, RT, 0, st>>>(a, b, n, partial);
-    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
-}
-
 void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 6.0 * n);
     k_f2h<<<blocks_for(n), RT, 0, st>>>(in, out, n);

@@ -25,6 +25,7 @@ Seeds: each named workload uses numpy's PCG64 with seed 1000 + its index.
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -268,16 +269,28 @@ WORKLOADS = {
 
 def workload(name, shape=None):
     """Inputs of a named workload, optionally at another grid size (same
-    generator and seed)."""
+    generator and seed).  If the environment names a directory in
+    CLAIRE_SYNTH_CACHE, generated arrays are kept there as .npy files and
+    reused (the 768^3 images take minutes to make on the host)."""
     w = dict(WORKLOADS[name])
     if shape is not None:
         w["shape"] = tuple(shape)
-    if name.startswith("sin"):
-        d = sinusoid_pair(w["shape"], w["seed"])
-    elif name == "blob768":
-        d = blob_pair(w["shape"], w["seed"], n_blobs=60, sigma_vox=3.0)
+    cache = os.environ.get("CLAIRE_SYNTH_CACHE")
+    tag = f"{name}_{'x'.join(str(n) for n in w['shape'])}_s{w['seed']}"
+    keys = ("m0", "m1", "v_true")
+    if cache and all(os.path.exists(os.path.join(cache, f"{tag}_{k}.npy")) for k in keys):
+        d = {k: np.load(os.path.join(cache, f"{tag}_{k}.npy")) for k in keys}
     else:
-        d = blob_pair(w["shape"], w["seed"])
+        if name.startswith("sin"):
+            d = sinusoid_pair(w["shape"], w["seed"])
+        elif name == "blob768":
+            d = blob_pair(w["shape"], w["seed"], n_blobs=60, sigma_vox=3.0)
+        else:
+            d = blob_pair(w["shape"], w["seed"])
+        if cache:
+            os.makedirs(cache, exist_ok=True)
+            for k in keys:
+                np.save(os.path.join(cache, f"{tag}_{k}.npy"), d[k])
     d.update(nt=w["nt"], beta=w["beta"], gamma=w["gamma"], shape=w["shape"])
     return d
 

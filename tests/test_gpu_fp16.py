@@ -1,24 +1,20 @@
-"""The FP16-storage form (stored m^j, grad m^j and lambda^j in FP16, FP32
-arithmetic) against the FP64 oracle and against the FP32 form on the GPU.
+"""The FP16-storage form against the FP64 oracle and against the FP32 form on
+the GPU.  In that form the stored trajectories (m^j, grad m^j and the
+gradient's adjoint lambda^j) are FP16 copies of FP32 values: the transport
+runs in FP32, grad m^j is taken of the FP32 state, m(1) stays FP32.
 
-Tolerances follow from the FP16 unit roundoff u = 2^-11 (round to nearest
-even on store).  Each stored value carries a relative error of at most u and
-these errors are independent between time steps, so after j steps a field
-transported by interpolation (weights summing to one) is off by about
-u*sqrt(j+1) in relative L2; the tests allow 4x that.  Two quantities magnify
-the stored-state rounding and get their own bound:
-  * grad m^j: the rounding noise of m^j is white, and spectral differentiation
-    scales white noise by the rms wavenumber (about n/2 on n points), against
-    the |k| ~ 4 of the signal: rel error ~ u*sqrt(j+1)*n/8, allowed 4x;
-  * lambda^j: lambda^nt = m1 - m^nt is a small difference of O(1) fields, so
-    the absolute rounding of m^nt is relative to ||m(1)|| / ||lambda^nt||.
-The gradient, the objective and the Hessian matvec integrate these fields and
-come out far more accurate than the worst of them (measured 2e-4, 6e-6 and
-1.5e-4 at 32^3); they are held to the transport bound.  A full solve in FP16
-storage must take the same Gauss-Newton path as the FP32 form and land on the
-same objective within the same bound."""
-import math
-
+Tolerances from the FP16 unit roundoff u = 2^-11 (round to nearest even):
+  * a stored field is its FP32 value rounded once: relative L2 error <= u
+    (plus the FP32 form's own 1e-5);
+  * the body force b = dt sum_j w_j lambda^j grad m^j of the gradient, and
+    b~ of the matvec (whose incremental state reads grad m^j), multiply two
+    rounded factors per term: relative error <= 2u of b, so the gradient
+    g = beta A v + b (beta A v carries no FP16 error) is off by at most
+    2u ||b|| / ||g|| relative, and Hv likewise with b~;
+  * the objective uses m(1) in FP32: the FP32 tolerance.
+Converged solves use the FP32 form's 1e-4 after a solve: the FP16-storage
+form must reach the stated accuracy of the plain form.  The fixed-work step
+(10 unconverged PCG steps) gets its own bound."""
 import numpy as np
 import pytest
 
@@ -30,6 +26,8 @@ from paper_2008_12820_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 U16 = 2.0 ** -11
+TOL = 1e-5
+TOL_SOLVE = 1e-4
 
 
 def rel(a, b):
@@ -57,42 +55,50 @@ def host(t):
     return t.cpu().numpy().astype(np.float64)
 
 
+def body_force_bound(total, reg_part):
+    """2u ||b|| / ||total|| with b = total - reg_part, plus the FP32 tolerance"""
+    return TOL + 2 * U16 * np.linalg.norm(total - reg_part) / np.linalg.norm(total)
+
+
 @pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((64, 64, 64), 8)])
 def test_fp16_storage_operators_vs_oracle(claire, shape, nt):
     """state, grad m, adjoint, gradient, objective and matvec of one
     linearization (rows a3, a4, a6, a7-a9) in the FP16-storage form"""
+    beta, gamma = 1e-2, 1.0
     d = synth.sinusoid_pair(shape, 1000)
     m0, m1, v = d["m0"], d["m1"], (0.8 * d["v_true"]).astype(np.float32)
     vt = synth.smooth_direction(shape, 7).astype(np.float32)
-    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    P = O.Problem(m0, m1, nt, beta, gamma)
     P.linearize(v)
     mh, gmh = P.state_history(), P.grad_state_history()
     go, Jo, lh = P.gradient(v, want_adjoint=True)
     Ho = P.matvec(vt)
-    tol = 4 * U16 * math.sqrt(nt + 1)
-    tol_gm = tol * max(shape) / 8
-    tol_adj = tol * np.linalg.norm(mh[nt]) / np.linalg.norm(lh[nt])
-    with claire.Registration(shape, nt, 1e-2, 1.0, precision="fp16") as reg:
+    tol_g = body_force_bound(go, O.apply_A(v, beta, gamma))
+    tol_h = body_force_bound(Ho, O.apply_A(vt, beta, gamma))
+    with claire.Registration(shape, nt, beta, gamma, precision="fp16") as reg:
         reg.set_images(dev(m0), dev(m1))
         g, J = reg.gradient(dev(v))
         for j in range(nt + 1):
-            assert rel(host(reg.field("state", j)), mh[j]) < tol, j
-            assert rel(host(reg.field("gradm", j)), gmh[j]) < tol_gm, j
-            assert rel(host(reg.field("adj", j)), lh[j]) < tol_adj, j
-        assert rel(host(g), go) < tol
-        assert abs(J - Jo) / abs(Jo) < tol
+            assert rel(host(reg.field("state", j)), mh[j]) < U16 + TOL, j
+            assert rel(host(reg.field("gradm", j)), gmh[j]) < U16 + TOL, j
+            assert rel(host(reg.field("adj", j)), lh[j]) < U16 + TOL, j
+        assert rel(host(g), go) < tol_g
+        assert abs(J - Jo) / abs(Jo) < TOL
         H = reg.hess_matvec(dev(v), dev(vt))
-        assert rel(host(H), Ho) < tol
+        assert rel(host(H), Ho) < tol_h
 
 
 def test_fp16_storage_fixed_work_step_vs_oracle(claire):
     """sinusoid workload, 32^3: 1 GN iteration with exactly 10 PCG steps in
-    the FP16-storage form against the oracle's FP64 solve"""
+    the FP16-storage form against the oracle's FP64 solve.  Ten unconverged
+    Krylov steps carry the matvec's FP16 perturbation (<= 2u of the body
+    force each time H is applied) into the iterate instead of damping it as a
+    converged solve does; allowed: 4u (measured 0.84u)."""
     w = synth.workload("sin32")
     shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
     P = O.Problem(w["m0"], w["m1"], nt, beta, gamma)
     vo, ro = P.solve(np.zeros((3,) + shape), max_gn=1, fixed_pcg=10)
-    tol = 4 * U16 * math.sqrt(nt + 1)
+    tol = 4 * U16
     with claire.Registration(shape, nt, beta, gamma, precision="fp16") as reg:
         reg.set_images(dev(w["m0"]), dev(w["m1"]))
         v = torch.zeros((3,) + shape, device="cuda")
@@ -105,11 +111,10 @@ def test_fp16_storage_fixed_work_step_vs_oracle(claire):
 
 @pytest.mark.parametrize("precond", ["invA", "2LinvH0"])
 def test_fp16_storage_solve_matches_fp32_form(claire, precond):
-    """blob workload at 96^3 (cfg1 generator): the FP16-storage form takes the
-    FP32 form's Gauss-Newton path to the same accuracy"""
+    """blob workload at 96^3 (the 128^3 / 256^3 generator): the FP16-storage
+    form takes the FP32 form's Gauss-Newton path to the same accuracy"""
     w = synth.workload("blob256", shape=(96, 96, 96))
     shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
-    tol = 4 * U16 * math.sqrt(nt + 1)
     out = {}
     for prec in ("fp32", "fp16"):
         with claire.Registration(shape, nt, beta, gamma, precision=prec) as reg:
@@ -121,51 +126,50 @@ def test_fp16_storage_solve_matches_fp32_form(claire, precond):
     r32, v32 = out["fp32"]
     r16, v16 = out["fp16"]
     assert r16.n_gn == r32.n_gn and abs(r16.n_pcg - r32.n_pcg) <= 1
-    assert abs(r16.J - r32.J) / abs(r32.J) < tol
-    assert abs(r16.mismatch_rel - r32.mismatch_rel) / r32.mismatch_rel < tol
-    assert rel(v16, v32) < tol
+    assert abs(r16.J - r32.J) / abs(r32.J) < TOL_SOLVE
+    assert abs(r16.mismatch_rel - r32.mismatch_rel) / r32.mismatch_rel < TOL_SOLVE
+    assert rel(v16, v32) < TOL_SOLVE
 
 
 def test_fp16_storage_paper_gpu_discretization(claire):
     """FD8 derivatives and trilinear interpolation with FP16 storage against
     the oracle in the same discretization"""
-    shape, nt = (32, 32, 32), 4
+    shape, nt, beta, gamma = (32, 32, 32), 4, 1e-2, 1.0
     d = synth.sinusoid_pair(shape, 1000)
     m0, m1, v = d["m0"], d["m1"], (0.8 * d["v_true"]).astype(np.float32)
     vt = synth.smooth_direction(shape, 7).astype(np.float32)
-    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    P = O.Problem(m0, m1, nt, beta, gamma)
     P.set_discretization(interp="linear", deriv="fd8")
     go, Jo = P.gradient(v)
     Ho = P.matvec(vt)
-    tol = 4 * U16 * math.sqrt(nt + 1)
-    with claire.Registration(shape, nt, 1e-2, 1.0, precision="fp16") as reg:
+    with claire.Registration(shape, nt, beta, gamma, precision="fp16") as reg:
         reg.set_discretization(interp="linear", deriv="fd8")
         reg.set_images(dev(m0), dev(m1))
         g, J = reg.gradient(dev(v))
-        assert rel(host(g), go) < tol
-        assert abs(J - Jo) / abs(Jo) < tol
-        assert rel(host(reg.hess_matvec(dev(v), dev(vt))), Ho) < tol
+        assert rel(host(g), go) < body_force_bound(go, O.apply_A(v, beta, gamma))
+        assert abs(J - Jo) / abs(Jo) < TOL
+        H = reg.hess_matvec(dev(v), dev(vt))
+        assert rel(host(H), Ho) < body_force_bound(Ho, O.apply_A(vt, beta, gamma))
 
 
 def test_fp16_storage_odd_sizes_and_wide_displacement(claire):
-    """n3 not a multiple of 8 (element-wise FP16 box copy) and displacements
-    wider than the shared-memory box (global gather of FP16 fields)"""
+    """an odd grid (FP32 box copied float by float) and displacements wider
+    than the shared-memory box (global gather)"""
     for shape, scale in [((20, 27, 45), 0.8), ((32, 32, 32), 6.0)]:
-        nt = 2
+        nt, beta, gamma = 2, 1e-2, 1.0
         d = synth.sinusoid_pair(shape, 1001)
         m0, m1, v = d["m0"], d["m1"], (scale * d["v_true"]).astype(np.float32)
-        P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+        P = O.Problem(m0, m1, nt, beta, gamma)
         P.linearize(v)
         mh = P.state_history()
         go, Jo = P.gradient(v)
-        tol = 4 * U16 * math.sqrt(nt + 1)
-        with claire.Registration(shape, nt, 1e-2, 1.0, precision="fp16") as reg:
+        with claire.Registration(shape, nt, beta, gamma, precision="fp16") as reg:
             reg.set_images(dev(m0), dev(m1))
             g, J = reg.gradient(dev(v))
             for j in range(nt + 1):
-                assert rel(host(reg.field("state", j)), mh[j]) < tol, (shape, j)
-            assert rel(host(g), go) < tol, shape
-            assert abs(J - Jo) / abs(Jo) < tol, shape
+                assert rel(host(reg.field("state", j)), mh[j]) < U16 + TOL, (shape, j)
+            assert rel(host(g), go) < body_force_bound(go, O.apply_A(v, beta, gamma)), shape
+            assert abs(J - Jo) / abs(Jo) < TOL, shape
 
 
 def test_fp16_storage_invalid_precision(claire):
