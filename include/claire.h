@@ -257,6 +257,21 @@ void claire_solve_opts_default(claire_solve_opts *opts);
 int claire_solve(claire_ctx *ctx, float *v_inout, const claire_solve_opts *opts,
                  claire_solve_report *report);
 
+/* Batched form (no counterpart in the paper, which registers one pair at a
+ * time): solve n independent registrations together, one per context, each
+ * exactly as claire_solve would (same options for all; contexts may differ
+ * in grid size, nt, beta, gamma and precision).  Each context runs on a CUDA
+ * stream created for the call and is driven by a host thread of its own, so
+ * the kernels of different pairs overlap on the GPU; the results are bitwise
+ * those of n claire_solve calls.  ctxs[i] (distinct, on the current device)
+ * with velocity v[i] (float[3][N_i], device, in/out); reports may be NULL,
+ * else n entries.  The call first synchronizes each context's stream and
+ * restores it on return.  Returns CLAIRE_OK or the first failing status
+ * (each report then holds its own; claire_last_error(ctxs[i]) the message);
+ * n in [1, 1024] and NULL or repeated contexts are CLAIRE_ERR_ARG. */
+int claire_solve_batch(claire_ctx *const *ctxs, float *const *v, int n,
+                       const claire_solve_opts *opts, claire_solve_report *reports);
+
 /* Parameter continuation in beta (Section 3 "Preconditioning", last
  * paragraph): Gauss-Newton solves for beta_k = max(beta_target,
  * beta_start * factor^k), k = 0, 1, ..., each started from the previous

@@ -36,7 +36,7 @@ EXPORTED = [
     "claire_apply_A", "claire_interp", "claire_get_field", "claire_solve_opts_default",
     "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
-    "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization",
+    "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization", "claire_solve_batch",
     "claire_mismatch_forward", "claire_mismatch_backward",
 ]
 
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         "claire_apply_A": [P, V, V], "claire_interp": [P, V, V, V],
         "claire_get_field": [P, I, I, V],
         "claire_solve": [P, V, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
+        "claire_solve_batch": [ctypes.POINTER(P), ctypes.POINTER(V), I, ctypes.POINTER(SolveOpts),
+                               ctypes.POINTER(SolveReport)],
         "claire_profile_enable": [P, I],
         "claire_profile_read": [P, I, ctypes.POINTER(ctypes.c_long), pd, pd],
         "claire_launch_count": [P, ctypes.POINTER(ctypes.c_long)],
@@ -169,6 +171,29 @@ def precond_noalloc(r, s, beta, gamma, stream=None):
     return s
 
 
+def solve_batch(regs, vs, check=True, **opts):
+    """Solve the registrations ``regs`` (Registration objects, distinct) with
+    velocities ``vs`` (float32 CUDA tensors, in/out) together through
+    claire_solve_batch: one CUDA stream and host thread per pair, results
+    bitwise those of ``reg.solve(v)`` one by one.  Returns the reports."""
+    n = len(regs)
+    if n != len(vs) or n == 0:
+        raise ValueError("need as many velocities as registrations (>= 1)")
+    if isinstance(opts.get("precond"), str):
+        opts["precond"] = Registration.PRECOND[opts["precond"]]
+    o = Registration.default_opts(**opts)
+    hs = (ctypes.c_void_p * n)(*[r.handle for r in regs])
+    ps = (ctypes.c_void_p * n)(*[ctypes.c_void_p(v.data_ptr()) for v in vs])
+    reps = (SolveReport * n)()
+    rc = load().claire_solve_batch(hs, ps, n, ctypes.byref(o), reps)
+    if check and rc != CLAIRE_OK:
+        bad = [i for i in range(n) if reps[i].status != CLAIRE_OK]
+        if bad:
+            _check(regs[bad[0]].handle, rc)
+        raise ClaireError(rc, load().claire_last_error(None).decode())
+    return [Report(**reps[i].as_dict()) for i in range(n)]
+
+
 class Registration:
     """One registration problem on an nx*ny*nz grid (a claire_ctx).
 
@@ -192,6 +217,7 @@ class Registration:
         self.nt, self.beta, self.gamma = nt, beta, gamma
         self.precision = precision
         st = stream if stream is not None else torch.cuda.current_stream()
+        self._stream = st
         _check(h, L.claire_set_stream(h, ctypes.c_void_p(st.cuda_stream)))
 
     # ---- lifetime ----

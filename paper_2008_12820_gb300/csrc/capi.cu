@@ -14,6 +14,7 @@
 #include <exception>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -1144,6 +1145,82 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
     const int status = do_solve(ctx, v, o, rep_out);
     if (status != CLAIRE_OK) return status;
     API_END(ctx)
+}
+
+int claire_solve_batch(claire_ctx *const *ctxs, float *const *v, int n, const claire_solve_opts *opts,
+                       claire_solve_report *reports) {
+    if (!ctxs || !v || n < 1 || n > 1024) {
+        set_thread_error("claire_solve_batch: need n in [1, 1024] and non-NULL arrays");
+        return CLAIRE_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !v[i]) {
+            set_thread_error("claire_solve_batch: NULL context or velocity");
+            return CLAIRE_ERR_ARG;
+        }
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == ctxs[i]) {
+                set_thread_error("claire_solve_batch: a context appears twice");
+                return CLAIRE_ERR_ARG;
+            }
+    }
+    claire_solve_opts o;
+    if (opts) o = *opts; else claire_solve_opts_default(&o);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_thread_error("claire_solve_batch: no current device");
+        return CLAIRE_ERR_CUDA;
+    }
+    // each registration runs on a stream of its own, driven by a host thread
+    // of its own (its PCG and line search branch on its own FP64 scalars);
+    // the hardware interleaves the kernels of the streams
+    std::vector<cudaStream_t> own(n, nullptr), prev(n, nullptr);
+    std::vector<int> status(n, CLAIRE_OK);
+    int rc = CLAIRE_OK;
+    for (int i = 0; i < n && rc == CLAIRE_OK; ++i) {
+        prev[i] = ctxs[i]->st;
+        if (cudaStreamSynchronize(prev[i]) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess) {
+            ctxs[i]->err = "claire_solve_batch: stream setup failed";
+            rc = CLAIRE_ERR_CUDA;
+        }
+    }
+    if (reports) std::memset(reports, 0, (size_t)n * sizeof(claire_solve_report));
+    if (rc == CLAIRE_OK) {
+        std::vector<std::thread> th;
+        th.reserve(n);
+        for (int i = 0; i < n; ++i) {
+            ctxs[i]->st = own[i];
+            th.emplace_back([&, i] {
+                claire_ctx *c = ctxs[i];
+                cudaSetDevice(dev);
+                try {
+                    status[i] = do_solve(c, v[i], o, reports ? &reports[i] : nullptr);
+                } catch (const Error &e) {
+                    c->err = e.msg;
+                    status[i] = e.code;
+                } catch (const std::bad_alloc &) {
+                    c->err = "host allocation failed";
+                    status[i] = CLAIRE_ERR_OOM;
+                } catch (const std::exception &e) {
+                    c->err = e.what();
+                    status[i] = CLAIRE_ERR_CUDA;
+                }
+                if (reports && status[i] != CLAIRE_OK) reports[i].status = status[i];
+            });
+        }
+        for (auto &t : th) t.join();
+        for (int i = 0; i < n; ++i)
+            if (status[i] != CLAIRE_OK && rc == CLAIRE_OK) rc = status[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        if (own[i]) {
+            cudaStreamSynchronize(own[i]);
+            cudaStreamDestroy(own[i]);
+        }
+        ctxs[i]->st = prev[i];
+    }
+    return rc;
 }
 
 int claire_solve_continuation(claire_ctx *ctx, float *v, double beta_target, double beta_start,

@@ -581,13 +581,14 @@ __global__ void __launch_bounds__(256) k_floor_range(const float *__restrict__ d
     }
 }
 
+// SM count of the device current at the first call (thread-safe initialisation)
 int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, c = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    }
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) c = 152;
+        return c;
+    }();
     return n;
 }
 

@@ -295,6 +295,22 @@ def workload(name, shape=None):
     return d
 
 
+def batch_workload(seed=1003, n_pairs=16, sizes=(64, 96, 128, 160)):
+    """The batched form's inputs: n_pairs blob pairs (the 128^3 / 256^3
+    generator: 12 ellipsoids, sigma 2 voxels, max displacement 4 voxels) on
+    cubic grids drawn uniformly from ``sizes``; pair i uses seed 1000*seed + i.
+    N_t = 4, beta = 1e-2, gamma = 1.  Returns a list of workload dicts."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.choice(np.asarray(sizes), size=n_pairs)
+    out = []
+    for i, n in enumerate(ns):
+        shape = (int(n),) * 3
+        d = blob_pair(shape, 1000 * seed + i)
+        d.update(nt=4, beta=1e-2, gamma=1.0, shape=shape)
+        out.append(d)
+    return out
+
+
 def smooth_direction(shape, seed, kmax=6):
     """A random smooth vector field with unit max norm (test directions)."""
     rng = np.random.Generator(np.random.PCG64(seed))
