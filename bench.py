@@ -62,11 +62,11 @@ KCLASS = ["footpoint", "state", "adjoint", "incstate", "incadj", "bodyforce", "f
 # argument of k_sl_pipe is the step kind: 0 plain, 1 adjoint, 2 incremental
 # state, 3 adjoint factor
 KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3, *>",
-          "state": "k_sl_pipe<0, *>", "adjoint": "k_sl_pipe<1, *>", "incstate": "k_sl_pipe<2, *>",
+          "state": "k_sl_pipe<0, *>", "adjoint": "k_sl_pipe<1, *>", "incstate": "k_sl_pipe<2, *>, k_sl_pipe<4, *>",
           "incadj": "k_sl_pipe<1, *>", "bodyforce": "k_bodyforce", "fft_r2c": "k_r2c_x3",
           "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1", "fft_c2r": "k_c2r_x3",
           "reduce": "k_reduce2, k_stats, k_finalize, k_finalize4",
-          "vector": "k_pcg_update, k_pcg_dir, k_axpby, k_sub, k_incstate_init, k_incadj_init",
+          "vector": "k_pcg_update, k_pcg_dir_u0, k_axpby, k_sub, k_incstate_init, k_f2h, k_h2f",
           "interp": "k_sl_pipe<0, *>", "fd": "k_grad_fd8, k_div_fd8"}
 
 

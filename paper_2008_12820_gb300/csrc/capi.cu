@@ -418,19 +418,25 @@ struct claire_ctx {
     // Hvt = beta A vt + int lt grad m dt.  Avt, if given, is beta*A vt already
     // at hand (PCG carries it along); otherwise it is applied spectrally.
     // With Avt and want_dot, dres[0] receives vt . Hvt from the same pass.
-    void matvec(const float *vt, float *Hvt, const float *Avt = nullptr, bool want_dot = false) {
+    // u0_ready: s1a already holds u0 = dt/2 f^0 (written by the PCG direction
+    // update, launch_pcg_dir_u0).
+    void matvec(const float *vt, float *Hvt, const float *Avt = nullptr, bool want_dot = false,
+                bool u0_ready = false) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
         const float dt = 1.f / nt;
         float *u = s1a, *un = s1b;
-        if (h16) launch_incstate_init(d, dt, vt, hist(gmhist_h, 0, 3), u, st, &prof);
-        else launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
-        for (int j = 0; j < nt; ++j) {
+        if (!u0_ready) {
+            if (h16) launch_incstate_init(d, dt, vt, hist(gmhist_h, 0, 3), u, st, &prof);
+            else launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
+        }
+        for (int j = 0; j + 1 < nt; ++j) {
             if (h16) launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist_h, j + 1, 3), un, st, &prof);
             else launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist, j + 1, 3), un, st, &prof);
             float *t = u; u = un; un = t;
         }
-        if (h16) launch_incadj_init(d, dt, u, vt, hist(gmhist_h, nt, 3), hist(lhist, nt), mt, st, &prof);
-        else launch_incadj_init(d, dt, u, vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
+        // the last step writes the incremental adjoint's final condition
+        if (h16) launch_incstate_last(d, dt, u, dispm, rng_m(), vt, hist(gmhist_h, nt, 3), hist(lhist, nt), mt, st, &prof);
+        else launch_incstate_last(d, dt, u, dispm, rng_m(), vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
         for (int j = nt; j >= 1; --j)
             launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
                                 CLAIRE_K_INCADJ);
@@ -1034,14 +1040,24 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                 ctx->spectral(OP_A, z, q, nullptr);
                 return q;
             };
+            // the direction update also writes u0 of the next matvec into s1a
+            auto pcg_dir = [&](const float *Az, float b, bool init) {
+                const float hdt = 0.5f / ctx->nt;
+                if (ctx->h16)
+                    launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, b, N, init, ctx->hist(ctx->gmhist_h, 0, 3),
+                                      ctx->s1a, hdt, st, &ctx->prof);
+                else
+                    launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, b, N, init, ctx->hist(ctx->gmhist, 0, 3),
+                                      ctx->s1a, hdt, st, &ctx->prof);
+            };
             if (r0 > 0) {
                 const float *Az = apply_pc();
-                launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, Az, 0.f, N, true, st, &ctx->prof);
+                pcg_dir(Az, 0.f, true);
                 double rz = ctx->dot(r, z, n3);
                 while (it < maxit) {
                     {
                         EvTimer t(st, &rep.t_hess_ms);
-                        ctx->matvec(p, q, Ap, true);
+                        ctx->matvec(p, q, Ap, true, true);
                     }
                     rep.n_matvec++;
                     const double pq = ctx->fetch(0);
@@ -1066,7 +1082,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                     const double rz_new = ctx->dot(r, z, n3);
                     const double beta = rz_new / rz;
                     rz = rz_new;
-                    launch_pcg_dir(p, Ap, z, r, ctx->dres + 1, Az, (float)beta, N, false, st, &ctx->prof);
+                    pcg_dir(Az, (float)beta, false);
                 }
             }
             rep.n_pcg += it;

@@ -105,9 +105,14 @@ void launch_incstate_init(const Dims &d, float dt, const float *vt, const float 
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
                           const int *range_m, const float *vt, const float *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof);
-void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
-                        const float *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
-                        Profiler *prof);
+// the last incremental-state step fused with the incremental adjoint's final
+// condition: lt_last = -mt(1), mt_out (nullable) = mt(1)
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+                          const float *vt, const float *gm_last, float *lt_last, float *mt_out,
+                          cudaStream_t st, Profiler *prof);
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+                          const float *vt, const __half *gm_last, float *lt_last, float *mt_out,
+                          cudaStream_t st, Profiler *prof);
 void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
                 Profiler *prof);  // out = a - b
 // b += w * l * gm
@@ -127,9 +132,6 @@ void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
                           const int *range_m, const float *vt, const __half *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof);
-void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
-                        const __half *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
-                        Profiler *prof);
 void launch_bodyforce(const Dims &d, int nt, const float *lhist, const __half *gmhist,
                       const float *add, float *out, cudaStream_t st, Profiler *prof);
 void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *gmhist,
@@ -172,6 +174,14 @@ void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const floa
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
                     const float *Az, float b, long long N, bool init, cudaStream_t st,
                     Profiler *prof);
+// launch_pcg_dir that also writes u0 = dt/2 * (-p . gm0) (N floats), the
+// first incremental-state field of the next matvec (hdt = dt/2)
+void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const float *gm0, float *u0, float hdt, cudaStream_t st,
+                       Profiler *prof);
+void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const __half *gm0, float *u0, float hdt, cudaStream_t st,
+                       Profiler *prof);
 // q = Ap + body force of (lhist, gmhist); dev_out[0] = p . q (fused curvature)
 void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
                           const float *Ap, const float *p, float *q, double *partial,

@@ -182,7 +182,9 @@ k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__re
 // ---------------------------------------------------------------------------
 // Arguments shared by the semi-Lagrangian step kernels.
 // ---------------------------------------------------------------------------
-enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3 };
+// SL_INCLAST: the last incremental-state step, whose epilogue writes the
+// incremental adjoint's final condition lt(1) = -mt(1) (and mt(1)) directly
+enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3, SL_INCLAST = 4 };
 
 // TS: storage type of the gathered and written field; TG: of grad m
 template <typename TS = float, typename TG = float>
@@ -195,6 +197,7 @@ struct SlArgsT {
     const TG *gm;       // SL_INCSTATE: grad m^{j+1} [3][N]
     float dt;
     __half *dst_h = nullptr;  // SL_PLAIN / SL_ADJ: optional FP16 copy of dst (stored trajectories)
+    float *dst2 = nullptr;    // SL_INCLAST: mt(1) (optional)
 };
 using SlArgs = SlArgsT<float, float>;
 
@@ -278,7 +281,9 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
-template <int MODE> struct EpiCount { static constexpr int v = MODE == SL_INCSTATE ? 6 : (MODE == SL_PLAIN ? 0 : 1); };
+template <int MODE> struct EpiCount {
+    static constexpr int v = (MODE == SL_INCSTATE || MODE == SL_INCLAST) ? 6 : (MODE == SL_PLAIN ? 0 : 1);
+};
 
 template <int MODE, typename A>
 __device__ __forceinline__ void sl_epilogue(const A &a, long long id, float val, const float *e) {
@@ -292,9 +297,15 @@ __device__ __forceinline__ void sl_epilogue(const A &a, long long id, float val,
     } else if (MODE == SL_ADJFAC) {
         const float dx = e[0];
         stf(a.dst + id, 1.f + 0.5f * a.dt * (val + dx) + 0.5f * a.dt * a.dt * dx * val);
-    } else {
+    } else if (MODE == SL_INCSTATE) {
         const float f = -(e[0] * e[3] + e[1] * e[4] + e[2] * e[5]);
         stf(a.dst + id, fmaf(a.dt, f, val));
+    } else {
+        // u(1) = u^{nt-1}(X-) + dt f(1); mt(1) = u(1) - dt/2 f(1); lt(1) = -mt(1)
+        const float f = -(e[0] * e[3] + e[1] * e[4] + e[2] * e[5]);
+        const float m = fmaf(a.dt, f, val) - 0.5f * a.dt * f;
+        stf(a.dst + id, -m);
+        if (a.dst2) a.dst2[id] = m;
     }
 }
 
@@ -302,7 +313,7 @@ template <int MODE, typename A>
 __device__ __forceinline__ void sl_load_epi(const A &a, long long id, long long N, float *e) {
     if (MODE == SL_ADJ || MODE == SL_ADJFAC) {
         e[0] = a.aux[id];
-    } else if (MODE == SL_INCSTATE) {
+    } else if (MODE == SL_INCSTATE || MODE == SL_INCLAST) {
         e[0] = a.vt[id]; e[1] = a.vt[N + id]; e[2] = a.vt[2 * N + id];
         e[3] = ldf(a.gm + id); e[4] = ldf(a.gm + N + id); e[5] = ldf(a.gm + 2 * N + id);
     }
@@ -403,7 +414,7 @@ __device__ __forceinline__ float box_linear(const float *p, float u1, float u2, 
 
 // resident blocks per SM: the incremental-state step carries six epilogue
 // inputs per voxel and keeps two; the others fit three
-template <int MODE> struct SlOcc { static constexpr int v = MODE == SL_INCSTATE ? 2 : 3; };
+template <int MODE> struct SlOcc { static constexpr int v = (MODE == SL_INCSTATE || MODE == SL_INCLAST) ? 2 : 3; };
 
 // tiles of block b: a contiguous range, so neighbouring tiles (which share
 // halo rows in L2) run on the same block one after the other
@@ -633,19 +644,6 @@ __global__ void k_incstate_init(const float *__restrict__ vt, const TG *__restri
     }
 }
 
-// lt(1) = -mt(1) = -(u^nt - dt/2 f^nt);  also returns mt(1)
-template <typename TG>
-__global__ void k_incadj_init(const float *__restrict__ u, const float *__restrict__ vt,
-                              const TG *__restrict__ gm, float *__restrict__ lt,
-                              float *__restrict__ mt, long long N, float hdt) {
-    for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
-        const float f = -(vt[i] * ldf(gm + i) + vt[N + i] * ldf(gm + N + i) + vt[2 * N + i] * ldf(gm + 2 * N + i));
-        const float m = u[i] - hdt * f;
-        lt[i] = -m;
-        if (mt) mt[i] = m;
-    }
-}
-
 template <typename TB, typename TO>
 __global__ void k_sub(const float *__restrict__ a, const TB *__restrict__ b,
                       TO *__restrict__ out, long long N) {
@@ -774,7 +772,27 @@ void incstate_step(const Dims &d, float dt, const float *src, const float *dispm
     SlArgsT<float, TG> a{src, dispm, dst, nullptr, vt, gm_next, dt};
     launch_pipe<SL_INCSTATE>(d, a, range_m, st);
 }
+template <typename TG>
+void incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+                   const float *vt, const TG *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
+                   Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_INCSTATE, st, (32.0 + 3 * sizeof(TG) + (mt_out ? 4 : 0)) * d.N);
+    SlArgsT<float, TG> a{src, dispm, lt_last, nullptr, vt, gm_last, dt};
+    a.dst2 = mt_out;
+    launch_pipe<SL_INCLAST>(d, a, range_m, st);
+}
 }  // namespace
+
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+                          const float *vt, const float *gm_last, float *lt_last, float *mt_out,
+                          cudaStream_t st, Profiler *prof) {
+    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, st, prof);
+}
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+                          const float *vt, const __half *gm_last, float *lt_last, float *mt_out,
+                          cudaStream_t st, Profiler *prof) {
+    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, st, prof);
+}
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
                           cudaStream_t st, Profiler *prof) {
@@ -796,19 +814,6 @@ void launch_incstate_step(const Dims &d, float dt, const float *src, const float
                           const int *range_m, const float *vt, const __half *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof) {
     incstate_step(d, dt, src, dispm, range_m, vt, gm_next, dst, st, prof);
-}
-
-void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
-                        const float *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
-                        Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)d.N * (mt_out ? 36 : 32));
-    k_incadj_init<<<grid1(d.N), PT, 0, st>>>(u_last, vt, gm_last, lt_last, mt_out, d.N, 0.5f * dt);
-}
-void launch_incadj_init(const Dims &d, float dt, const float *u_last, const float *vt,
-                        const __half *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
-                        Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)d.N * (mt_out ? 30 : 26));
-    k_incadj_init<<<grid1(d.N), PT, 0, st>>>(u_last, vt, gm_last, lt_last, mt_out, d.N, 0.5f * dt);
 }
 
 void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,

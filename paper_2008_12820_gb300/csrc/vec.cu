@@ -240,6 +240,38 @@ __global__ void __launch_bounds__(RT) k_pcg_dir(float *__restrict__ p, float *__
     }
 }
 
+// k_pcg_dir per voxel, also writing the first incremental-state field of the
+// next matvec, u0 = dt/2 f^0 with f^0 = -p . grad m^0 (saves that pass)
+template <typename TG>
+__global__ void __launch_bounds__(RT) k_pcg_dir_u0(float *__restrict__ p, float *__restrict__ Ap,
+                                                   const float *__restrict__ z, const float *__restrict__ r,
+                                                   const double *__restrict__ rsum, const float *__restrict__ Az,
+                                                   float b, long long N, int init, const TG *__restrict__ gm0,
+                                                   float *__restrict__ u0, float hdt) {
+    const long long stride = (long long)gridDim.x * RT;
+    float mean[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mean[c] = Az ? 0.f : (float)(rsum[c] / (double)N);
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
+        float pc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long k = c * N + i;
+            const float ar = Az ? Az[k] : r[k] - mean[c];
+            if (init) {
+                pc[c] = z[k];
+                Ap[k] = ar;
+            } else {
+                pc[c] = fmaf(b, p[k], z[k]);
+                Ap[k] = fmaf(b, Ap[k], ar);
+            }
+            p[k] = pc[c];
+        }
+        const float f = -(pc[0] * ldv(gm0 + i) + pc[1] * ldv(gm0 + N + i) + pc[2] * ldv(gm0 + 2 * N + i));
+        u0[i] = hdt * f;
+    }
+}
+
 // zero-velocity Hessian applied to p given beta0*A p:  q = Ap + gm (gm . p)
 __global__ void __launch_bounds__(RT) k_h0_apply(float *__restrict__ q, const float *__restrict__ Ap,
                                                  const float *__restrict__ gm, const float *__restrict__ p,
@@ -381,6 +413,25 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
                     Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (init ? 16 : 24));
     k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0);
+}
+
+template <typename TG>
+static void pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const TG *gm0, float *u0, float hdt, cudaStream_t st,
+                       Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)N * (3.0 * (init ? 16 : 24) + 3 * sizeof(TG) + 4));
+    k_pcg_dir_u0<<<blocks_for(N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt);
+}
+
+void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const float *gm0, float *u0, float hdt, cudaStream_t st,
+                       Profiler *prof) {
+    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, st, prof);
+}
+void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const __half *gm0, float *u0, float hdt, cudaStream_t st,
+                       Profiler *prof) {
+    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, st, prof);
 }
 
 template <typename TG>
