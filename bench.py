@@ -209,12 +209,15 @@ def run_ours(args):
     w = synth.workload(args.workload, shape=(args.grid,) * 3 if args.grid else None)
     shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
     N = int(np.prod(shape))
+    # a stream of its own (not the legacy default stream), so that the library
+    # can capture the PCG matvec into a CUDA graph
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     m0 = torch.from_numpy(w["m0"]).cuda()
     m1 = torch.from_numpy(w["m1"]).cuda()
     v = torch.zeros((3,) + shape, device="cuda")
     reg = claire.Registration(shape, nt, beta, gamma, precision=args.precision)
     reg.set_images(m0, m1)
-    stream = torch.cuda.current_stream()
 
     def step():
         v.zero_()
@@ -231,7 +234,6 @@ def run_ours(args):
     # ---- timed region ----------------------------------------------------
     clocks = ClockSampler(local)
     clocks.start()
-    reg.profile_enable(True)
     launches0 = reg.launch_count()
     barrier()
     torch.cuda.synchronize()
@@ -246,10 +248,16 @@ def run_ours(args):
     launches = reg.launch_count() - launches0
     ms = e0.elapsed_time(e1) / args.steps
     clk = clocks.stop()
-    prof = {k: reg.profile_read(i) for i, k in enumerate(KCLASS)}
-    reg.profile_enable(False)
     ms, value = aggregate_ranks(ms, N, ws, device="cuda")
     rep = reports[-1]
+
+    # ---- per-class kernel times: one more solve with the profiler on (its
+    # per-launch events keep the matvec out of the CUDA graph) -------------
+    reg.profile_enable(True)
+    step()
+    torch.cuda.synchronize()
+    prof = {k: reg.profile_read(i) for i, k in enumerate(KCLASS)}
+    reg.profile_enable(False)
 
     # ---- Hessian matvec throughput at the solution (own events loop) -------
     reg.linearize(v)
@@ -272,7 +280,7 @@ def run_ours(args):
     dom = max(prof, key=lambda k: prof[k][1])
     nl, kms, kby = prof[dom]
     achieved = (kby / nl) / ((kms / nl) * 1e-3) / 1e9 if nl else 0.0
-    breakdown = {k: {"launches": n_, "ms_per_step": round(t_ / args.steps, 4),
+    breakdown = {k: {"launches": n_, "ms_per_step": round(t_, 4),
                      "GBps": round(b_ / (t_ * 1e-3) / 1e9, 1) if t_ > 0 else None}
                  for k, (n_, t_, b_) in prof.items() if n_}
     roofline = {"bound": "hbm", "kernel": dom, "kernels": KNAMES[dom],
@@ -459,6 +467,9 @@ def run_batch(args):
     from paper_2008_12820_gb300 import claire, synth
 
     ws = synth.batch_workload()
+    # a stream of its own for the one-by-one solves, so both arms replay the
+    # captured PCG matvec (the batch makes a stream per pair)
+    torch.cuda.set_stream(torch.cuda.Stream())
     regs, vs = [], []
     for w in ws:
         r = claire.Registration(w["shape"], w["nt"], w["beta"], w["gamma"])

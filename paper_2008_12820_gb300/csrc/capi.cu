@@ -160,6 +160,7 @@ struct claire_ctx {
         return p;
     }
     ~claire_ctx() {
+        if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
         for (void *p : allocs) cudaFree(p);
         for (int a = 0; a < 3; ++a) cudaFree((void *)ax[a].tw);
     }
@@ -371,6 +372,7 @@ struct claire_ctx {
         div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         check_launch("linearize");
+        ++lin_epoch;
         have_lin = true;
         co.gm_valid = false;
     }
@@ -415,6 +417,26 @@ struct claire_ctx {
         }
     }
 
+    // CUDA graph of the matvec's launch sequence.  The PCG loop calls the
+    // matvec with the same buffers every iteration of a linearization, so the
+    // second call with a given signature is captured and later ones replay
+    // the graph (one launch instead of ~12).  Off on the legacy stream (no
+    // capture there) and while the profiler records per-launch events.
+    struct MvGraph {
+        cudaGraphExec_t exec = nullptr;
+        const float *vt = nullptr, *Avt = nullptr;
+        float *Hvt = nullptr;
+        bool want_dot = false, u0_ready = false;
+        unsigned long long epoch = ~0ULL;
+        int seen = 0;       // calls with this signature so far
+        long kernels = 0;   // kernel launches one replay stands for
+        bool same(const float *a, float *b, const float *c, bool w, bool u, unsigned long long e) const {
+            return vt == a && Hvt == b && Avt == c && want_dot == w && u0_ready == u && epoch == e;
+        }
+    } mvg;
+    unsigned long long lin_epoch = 0;  // bumped by every linearization
+    bool use_graphs = true;
+
     // Hvt = beta A vt + int lt grad m dt.  Avt, if given, is beta*A vt already
     // at hand (PCG carries it along); otherwise it is applied spectrally.
     // With Avt and want_dot, dres[0] receives vt . Hvt from the same pass.
@@ -423,6 +445,60 @@ struct claire_ctx {
     void matvec(const float *vt, float *Hvt, const float *Avt = nullptr, bool want_dot = false,
                 bool u0_ready = false) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
+        const bool graph = use_graphs && Avt && st != 0 && !prof.on;
+        if (graph) {
+            if (mvg.same(vt, Hvt, Avt, want_dot, u0_ready, lin_epoch)) {
+                if (mvg.exec) {
+                    CK(cudaGraphLaunch(mvg.exec, st));
+                    prof.launches += mvg.kernels;
+                    return;
+                }
+                if (mvg.seen >= 1) {
+                    capture_matvec(vt, Hvt, Avt, want_dot, u0_ready);
+                    return;
+                }
+            } else {
+                drop_graph();
+                mvg.vt = vt; mvg.Hvt = Hvt; mvg.Avt = Avt; mvg.want_dot = want_dot; mvg.u0_ready = u0_ready;
+                mvg.epoch = lin_epoch;
+                mvg.seen = 0;
+            }
+            ++mvg.seen;
+        }
+        matvec_launches(vt, Hvt, Avt, want_dot, u0_ready);
+        check_launch("hess_matvec");
+    }
+
+    void drop_graph() {
+        if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
+        mvg.exec = nullptr;
+    }
+
+    void capture_matvec(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const long before = prof.launches;
+        try {
+            matvec_launches(vt, Hvt, Avt, want_dot, u0_ready);
+            mvg.kernels = prof.launches - before;
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamEndCapture(st, &g));
+        const cudaError_t e = cudaGraphInstantiate(&mvg.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            mvg.exec = nullptr;
+            throw Error(CLAIRE_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+        }
+        CK(cudaGraphLaunch(mvg.exec, st));
+        check_launch("hess_matvec graph");
+    }
+
+    void matvec_launches(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
         const float dt = 1.f / nt;
         float *u = s1a, *un = s1b;
         if (!u0_ready) {
@@ -448,7 +524,6 @@ struct claire_ctx {
             else launch_bodyforce(d, nt, lhist, gmhist, Avt, Hvt, st, &prof);
             if (!Avt) spectral(OP_A, vt, Hvt, Hvt);
         }
-        check_launch("hess_matvec");
     }
 
     // ---- differentiable transport with state checkpointing -----------------

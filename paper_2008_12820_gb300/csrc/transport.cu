@@ -23,6 +23,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "claire_internal.cuh"
@@ -621,7 +622,13 @@ inline int pipe_blocks(const Dims &d, int per_sm) {
 template <int MODE, int ORDER, typename TS, typename TG>
 void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
-    cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER, TS, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the shared-memory limit is set once per instantiation, so that launches
+    // being captured into a CUDA graph make no other runtime call
+    static std::once_flag attr;
+    std::call_once(attr, [] {
+        cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER, TS, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * BOX_FLOATS * sizeof(float)));
+    });
     k_sl_pipe<MODE, ORDER, TS, TG><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(
         a, d, range, chunk_ok(d, a.src));
 }

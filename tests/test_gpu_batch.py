@@ -100,3 +100,26 @@ def test_batch_invalid_arguments(claire):
         claire.solve_batch([reg, reg], [v, v.clone()])
     assert e.value.code == 1
     reg.close()
+
+
+def test_graph_replayed_matvec_equals_direct_launches(claire):
+    """On a stream of its own the solver captures the PCG matvec into a CUDA
+    graph and replays it; on the legacy stream it launches the kernels one by
+    one.  Same kernels, same order: the solves must agree bit for bit (FP32 and
+    FP16-storage forms, InvA and InvH0)."""
+    w = pairs()[4]
+    for prec, pc in [("fp32", "invA"), ("fp16", "invA"), ("fp32", "invH0")]:
+        out = []
+        for st in (None, torch.cuda.Stream()):
+            with torch.cuda.stream(st) if st is not None else torch.cuda.stream(torch.cuda.default_stream()):
+                reg = claire.Registration(w["shape"], w["nt"], w["beta"], w["gamma"], precision=prec)
+                reg.set_images(dev(w["m0"]), dev(w["m1"]))
+                v = torch.zeros((3,) + w["shape"], device="cuda")
+                rep = reg.solve(v, precond=pc)
+                torch.cuda.synchronize()
+                out.append((rep, v.clone(), reg.launch_count()))
+                reg.close()
+        (r1, v1, n1), (r2, v2, n2) = out
+        assert r1.n_pcg == r2.n_pcg and r1.J == r2.J, (prec, pc)
+        assert torch.equal(v1, v2), (prec, pc)
+        assert n1 == n2, (prec, pc)   # replays count the kernels they stand for
