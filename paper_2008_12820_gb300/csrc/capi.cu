@@ -129,6 +129,7 @@ struct claire_ctx {
     float2 *spec = nullptr;
     double *partial = nullptr, *dres = nullptr;
     int *dflag = nullptr;
+    int *fpart = nullptr;  // the foot-point blocks' partial floor ranges
     // floor ranges of the displacement fields: X-, X+, forward-only X-, interp
     // (the X- and forward-only slots swap when a line-search trial is adopted)
     int *rng = nullptr;
@@ -342,11 +343,11 @@ struct claire_ctx {
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         if (state_ready) {
-            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), st, &prof);
+            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), fpart, st, &prof);
         } else if (h16) {
             // FP32 transport; FP16 copies of m^j and of grad m^j (taken of the
             // FP32 state); m(1) and grad m(1) also kept in FP32
-            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
+            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
             launch_f2h(m0, mhist_h, (long long)N, st, &prof);
             if (!gm0_valid) grad_h(m0, hist(gmhist_h, 0, 3));
             const float *src = m0;
@@ -361,7 +362,7 @@ struct claire_ctx {
             grad(m1f, gm1f);
             launch_f2h(gm1f, hist(gmhist_h, nt, 3), 3 * (long long)N, st, &prof);
         } else {
-            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
+            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
             CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
             for (int j = 0; j < nt; ++j)
                 launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
@@ -555,7 +556,7 @@ struct claire_ctx {
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         have_lin = false;  // the full history is not kept on this path
-        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
+        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
         div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         CK(cudaMemcpyAsync(ck, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -612,7 +613,7 @@ struct claire_ctx {
     // m(1) for v into mout (N); uses fdisp, s1a, s1b; leaves the cache alone
     const float *forward(const float *v) {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
-        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
+        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, fpart, st, &prof);
         const float *src = m0;
         float *a = s1a, *b = s1b;
         for (int j = 0; j < nt; ++j) {
@@ -633,7 +634,7 @@ struct claire_ctx {
     bool keeps_trial() const { return !h16; }
     double trial_mismatch(const float *v) {
         if (h16) return mismatch_of(forward(v));
-        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
+        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, fpart, st, &prof);
         if (!mhist_t) mhist_t = alloc_f((size_t)(nt + 1) * d.N);
         const float *src = m0;
         for (int j = 0; j < nt; ++j) {
@@ -782,6 +783,7 @@ int claire_create_ex(int nx, int ny, int nz, int nt, double beta, double gamma, 
         c->dres = (double *)c->alloc_bytes(8 * sizeof(double));
         c->dflag = (int *)c->alloc_bytes(sizeof(int));
         c->rng = (int *)c->alloc_bytes(24 * sizeof(int));
+        c->fpart = (int *)c->alloc_bytes((size_t)footpoint_parts(c->d) * sizeof(int));
     } catch (const Error &e) {
         g_create_error = e.msg;
         delete c;

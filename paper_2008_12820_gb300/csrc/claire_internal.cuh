@@ -85,8 +85,10 @@ void launch_div_fd8(const Dims &d, const float *v, float *out, cudaStream_t st, 
 // Foot points and the per-axis [min, max] floor range of each displacement
 // field (6 ints each), which fixes the shared-memory box of the SL kernels.
 // Either of dispm (X-) and dispp (X+) may be null; that side is skipped.
+// part: scratch of footpoint_parts(d) ints (the blocks' partial ranges).
 void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
-                       int *range_m, int *range_p, cudaStream_t st, Profiler *prof);
+                       int *range_m, int *range_p, int *part, cudaStream_t st, Profiler *prof);
+long long footpoint_parts(const Dims &d);
 void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream_t st,
                         Profiler *prof);
 void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int *range,

@@ -146,37 +146,106 @@ __device__ __forceinline__ Pt this_point(const Dims &d) {
 // foot points: Heun (RK2) backward (sign -1) and forward (sign +1) in one pass
 //   y* = x + s dt v(x);  X = x + s dt/2 (v(x) + v(y*));  disp = (X - x)/h
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int floor_int(float x) {
+    return (int)fminf(fmaxf(floorf(x), -1.0e6f), 1.0e6f);
+}
+
+// The block also reduces the per-axis floor range of what it wrote (the SL
+// steps' box geometry) into part[block][12]: side, axis, {min, max}.
 template <int ORDER>
 __global__ void __launch_bounds__(BX * BY)
 k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__restrict__ dispp,
-             Dims d, float dt, float ih1, float ih2, float ih3) {
-    Pt p = this_point(d);
-    if (!p.ok) return;
+             Dims d, float dt, float ih1, float ih2, float ih3, int *__restrict__ part) {
+    __shared__ int red[BY][12];
+    const Pt p = this_point(d);
     const long long N = d.N;
-    const float v1 = v[p.id], v2 = v[N + p.id], v3 = v[2 * N + p.id];
+    float v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    if (p.ok) {
+        v1 = v[p.id];
+        v2 = v[N + p.id];
+        v3 = v[2 * N + p.id];
+    }
     // X- (side 0) and X+ (side 1); a side whose output is null is skipped
-    for (int s = dispm ? 0 : 1; s < (dispp ? 2 : 1); ++s) {
-        const float sg = s == 0 ? -1.f : 1.f;
-        const float q1 = sg * dt * v1 * ih1, q2 = sg * dt * v2 * ih2, q3 = sg * dt * v3 * ih3;
-        float w1, w2, w3;
-        if (ORDER == 1) {
-            w1 = gather8(v, d, p.i1, p.i2, p.i3, q1, q2, q3);
-            w2 = gather8(v + N, d, p.i1, p.i2, p.i3, q1, q2, q3);
-            w3 = gather8(v + 2 * N, d, p.i1, p.i2, p.i3, q1, q2, q3);
-        } else {
-            Axis4 a1, a2, a3;
-            axis_stencil(p.i1, q1, d.n1, d.n2 * d.n3, a1);
-            axis_stencil(p.i2, q2, d.n2, d.n3, a2);
-            axis_stencil(p.i3, q3, d.n3, 1, a3);
-            w1 = gather64(v, a1, a2, a3);
-            w2 = gather64(v + N, a1, a2, a3);
-            w3 = gather64(v + 2 * N, a1, a2, a3);
-        }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
         float *out = s == 0 ? dispm : dispp;
-        const float hs = 0.5f * sg * dt;
-        out[p.id] = hs * (v1 + w1) * ih1;
-        out[N + p.id] = hs * (v2 + w2) * ih2;
-        out[2 * N + p.id] = hs * (v3 + w3) * ih3;
+        if (!out) continue;
+        int f[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, g[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+        if (p.ok) {
+            const float sg = s == 0 ? -1.f : 1.f;
+            const float q1 = sg * dt * v1 * ih1, q2 = sg * dt * v2 * ih2, q3 = sg * dt * v3 * ih3;
+            float w1, w2, w3;
+            if (ORDER == 1) {
+                w1 = gather8(v, d, p.i1, p.i2, p.i3, q1, q2, q3);
+                w2 = gather8(v + N, d, p.i1, p.i2, p.i3, q1, q2, q3);
+                w3 = gather8(v + 2 * N, d, p.i1, p.i2, p.i3, q1, q2, q3);
+            } else {
+                Axis4 a1, a2, a3;
+                axis_stencil(p.i1, q1, d.n1, d.n2 * d.n3, a1);
+                axis_stencil(p.i2, q2, d.n2, d.n3, a2);
+                axis_stencil(p.i3, q3, d.n3, 1, a3);
+                w1 = gather64(v, a1, a2, a3);
+                w2 = gather64(v + N, a1, a2, a3);
+                w3 = gather64(v + 2 * N, a1, a2, a3);
+            }
+            const float hs = 0.5f * sg * dt;
+            const float o[3] = {hs * (v1 + w1) * ih1, hs * (v2 + w2) * ih2, hs * (v3 + w3) * ih3};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                out[c * N + p.id] = o[c];
+                f[c] = g[c] = floor_int(o[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int lo = __reduce_min_sync(0xffffffffu, f[c]), hi = __reduce_max_sync(0xffffffffu, g[c]);
+            if (threadIdx.x == 0) {
+                red[threadIdx.y][6 * s + 2 * c] = lo;
+                red[threadIdx.y][6 * s + 2 * c + 1] = hi;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x < 12) {
+        const int k = threadIdx.x;
+        const bool on = k < 6 ? dispm != nullptr : dispp != nullptr;
+        int r = (k & 1) ? -0x7fffffff : 0x7fffffff;
+        if (on)
+            for (int y = 0; y < BY; ++y) r = (k & 1) ? max(r, red[y][k]) : min(r, red[y][k]);
+        part[(((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * 12 + k] = r;
+    }
+}
+
+// per-axis floor ranges of the foot points from the blocks' partials
+__global__ void __launch_bounds__(256) k_range_parts(const int *__restrict__ part, long long nblocks,
+                                                     int *__restrict__ range_m, int *__restrict__ range_p) {
+    __shared__ int red[8][12];
+    int rg[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) rg[k] = (k & 1) ? -0x7fffffff : 0x7fffffff;
+    for (long long b = blockIdx.x * 256LL + threadIdx.x; b < nblocks; b += (long long)gridDim.x * 256) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const int x = part[b * 12 + k];
+            rg[k] = (k & 1) ? max(rg[k], x) : min(rg[k], x);
+        }
+    }
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const int r = (k & 1) ? __reduce_max_sync(0xffffffffu, rg[k]) : __reduce_min_sync(0xffffffffu, rg[k]);
+        if ((threadIdx.x & 31) == 0) red[w][k] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        const int k = threadIdx.x;
+        int r = red[0][k];
+        for (int y = 1; y < 8; ++y) r = (k & 1) ? max(r, red[y][k]) : min(r, red[y][k]);
+        int *range = k < 6 ? range_m : range_p;
+        if (range) {
+            if (k & 1) atomicMax(&range[k % 6], r);
+            else atomicMin(&range[k % 6], r);
+        }
     }
 }
 
@@ -202,9 +271,6 @@ struct SlArgsT {
 };
 using SlArgs = SlArgsT<float, float>;
 
-__device__ __forceinline__ int floor_int(float x) {
-    return (int)fminf(fmaxf(floorf(x), -1.0e6f), 1.0e6f);
-}
 
 // ---------------------------------------------------------------------------
 // Lean global-memory gather (one thread per voxel, L1-cached).  A voxel whose
@@ -560,6 +626,7 @@ __global__ void __launch_bounds__(256) k_floor_range(const float *__restrict__ d
         const float *dc = disp + c * N;
         if (vec) {
             const float4 *d4 = reinterpret_cast<const float4 *>(dc);
+#pragma unroll 4
             for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N / 4; i += stride) {
                 const float4 q = d4[i];
                 const int f0 = floor_int(q.x), f1 = floor_int(q.y), f2 = floor_int(q.z), f3 = floor_int(q.w);
@@ -720,25 +787,29 @@ void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream
                         Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 12.0 * d.N, 2);
     k_range_init<<<1, 32, 0, st>>>(range);
-    k_floor_range<<<4 * num_sms(), 256, 0, st>>>(disp, d.N, range);
+    k_floor_range<<<8 * num_sms(), 256, 0, st>>>(disp, d.N, range);
 }
 
 void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
-                       int *range_m, int *range_p, cudaStream_t st, Profiler *prof) {
+                       int *range_m, int *range_p, int *part, cudaStream_t st, Profiler *prof) {
     if (!dispm && !dispp) return;
     const float dt = 1.f / nt;
     const double two_pi = 6.283185307179586476925286766559;
-    {
-        ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)));
-        const float i1 = (float)(d.n1 / two_pi), i2 = (float)(d.n2 / two_pi), i3 = (float)(d.n3 / two_pi);
-        const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
-        if (d.iorder == 1)
-            k_footpoints<1><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
-        else
-            k_footpoints<3><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
-    }
-    if (dispm) launch_floor_range(d, dispm, range_m, st, prof);
-    if (dispp) launch_floor_range(d, dispp, range_p, st, prof);
+    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)), 4);
+    const float i1 = (float)(d.n1 / two_pi), i2 = (float)(d.n2 / two_pi), i3 = (float)(d.n3 / two_pi);
+    const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
+    if (d.iorder == 1)
+        k_footpoints<1><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, part);
+    else
+        k_footpoints<3><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, part);
+    if (dispm) k_range_init<<<1, 32, 0, st>>>(range_m);
+    if (dispp) k_range_init<<<1, 32, 0, st>>>(range_p);
+    const long long nblocks = (long long)grid.x * grid.y * grid.z;
+    k_range_parts<<<num_sms(), 256, 0, st>>>(part, nblocks, dispm ? range_m : nullptr, dispp ? range_p : nullptr);
+}
+
+long long footpoint_parts(const Dims &d) {
+    return (long long)((d.n3 + BX - 1) / BX) * ((d.n2 + BY - 1) / BY) * d.n1 * 12;
 }
 
 void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int *range,
