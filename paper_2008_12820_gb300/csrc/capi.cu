@@ -446,7 +446,7 @@ struct claire_ctx {
     void matvec(const float *vt, float *Hvt, const float *Avt = nullptr, bool want_dot = false,
                 bool u0_ready = false) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
-        const bool graph = use_graphs && Avt && st != 0 && !prof.on;
+        const bool graph = use_graphs && Avt && capturable(st) && !prof.on;
         if (graph) {
             if (mvg.same(vt, Hvt, Avt, want_dot, u0_ready, lin_epoch)) {
                 if (mvg.exec) {
@@ -454,10 +454,7 @@ struct claire_ctx {
                     prof.launches += mvg.kernels;
                     return;
                 }
-                if (mvg.seen >= 1) {
-                    capture_matvec(vt, Hvt, Avt, want_dot, u0_ready);
-                    return;
-                }
+                if (mvg.seen >= 1 && capture_matvec(vt, Hvt, Avt, want_dot, u0_ready)) return;
             } else {
                 drop_graph();
                 mvg.vt = vt; mvg.Hvt = Hvt; mvg.Avt = Avt; mvg.want_dot = want_dot; mvg.u0_ready = u0_ready;
@@ -475,8 +472,20 @@ struct claire_ctx {
         mvg.exec = nullptr;
     }
 
-    void capture_matvec(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    // streams a graph can be captured on (not the legacy or per-thread
+    // default streams)
+    static bool capturable(cudaStream_t s) {
+        return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+    }
+
+    // captures and runs the matvec as a graph; false (and graphs off for this
+    // context, the launches not yet run) if the runtime refuses the capture
+    bool capture_matvec(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            use_graphs = false;
+            return false;
+        }
         const long before = prof.launches;
         try {
             matvec_launches(vt, Hvt, Avt, want_dot, u0_ready);
@@ -488,15 +497,19 @@ struct claire_ctx {
             throw;
         }
         cudaGraph_t g = nullptr;
-        CK(cudaStreamEndCapture(st, &g));
-        const cudaError_t e = cudaGraphInstantiate(&mvg.exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess && g) e = cudaGraphInstantiate(&mvg.exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || !mvg.exec) {
+            cudaGetLastError();
             mvg.exec = nullptr;
-            throw Error(CLAIRE_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+            prof.launches = before;
+            use_graphs = false;
+            return false;
         }
         CK(cudaGraphLaunch(mvg.exec, st));
         check_launch("hess_matvec graph");
+        return true;
     }
 
     void matvec_launches(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
