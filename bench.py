@@ -57,7 +57,7 @@ CPU_SAMPLE_N = 64        # oracle solves the same generator on a 64^3 grid
 ERR_CHECK_N = 128        # GPU vs oracle gradient / matvec on a 128^3 instance
 
 KCLASS = ["footpoint", "state", "adjoint", "incstate", "incadj", "bodyforce", "fft_r2c",
-          "fft_c2c", "fft_mul", "fft_c2r", "reduce", "vector", "interp", "fd"]
+          "fft_c2c", "fft_mul", "fft_c2r", "reduce", "vector", "interp", "fd", "deriv"]
 # kernel function names of each class (for the ncu summaries); the template
 # argument of k_sl_pipe is the step kind: 0 plain, 1 adjoint, 2 incremental
 # state, 3 adjoint factor
@@ -67,7 +67,8 @@ KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3, 
           "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1", "fft_c2r": "k_c2r_x3",
           "reduce": "k_reduce2, k_stats, k_finalize, k_finalize4",
           "vector": "k_pcg_update, k_pcg_dir_u0, k_axpby, k_sub, k_incstate_init, k_f2h, k_h2f",
-          "interp": "k_sl_pipe<0, *>", "fd": "k_grad_fd8, k_div_fd8"}
+          "interp": "k_sl_pipe<0, *>", "fd": "k_grad_fd8, k_div_fd8",
+          "deriv": "k_deriv_x3, k_deriv_strided"}
 
 
 def parse():

@@ -286,13 +286,14 @@ int claire_solve_continuation(claire_ctx *ctx, float *v_inout, double beta_targe
 
 /* ---- instrumentation -------------------------------------------------- */
 
-/* Kernel classes timed by the profiler. */
+/* Kernel classes timed by the profiler (CLAIRE_K_DERIV: spectral first
+ * derivatives by axis transforms, three passes per gradient or divergence). */
 enum {
     CLAIRE_K_FOOTPOINT = 0, CLAIRE_K_STATE = 1, CLAIRE_K_ADJOINT = 2,
     CLAIRE_K_INCSTATE = 3, CLAIRE_K_INCADJ = 4, CLAIRE_K_BODYFORCE = 5,
     CLAIRE_K_FFT_R2C = 6, CLAIRE_K_FFT_C2C = 7, CLAIRE_K_FFT_MUL = 8,
     CLAIRE_K_FFT_C2R = 9, CLAIRE_K_REDUCE = 10, CLAIRE_K_VECTOR = 11,
-    CLAIRE_K_INTERP = 12, CLAIRE_K_FD = 13, CLAIRE_K_COUNT = 14
+    CLAIRE_K_INTERP = 12, CLAIRE_K_FD = 13, CLAIRE_K_DERIV = 14, CLAIRE_K_COUNT = 15
 };
 
 /* Enable (1) or disable (0) per-launch CUDA-event timing of every kernel the

@@ -27,7 +27,7 @@ STATUS = {0: "CLAIRE_OK", 1: "CLAIRE_ERR_ARG", 2: "CLAIRE_ERR_OOM", 3: "CLAIRE_E
 
 FIELD = dict(dispm=0, dispp=1, state=2, gradm=3, divv=4, adjf=5, adj=6, incadj=7, incst=8)
 KERNEL = dict(footpoint=0, state=1, adjoint=2, incstate=3, incadj=4, bodyforce=5, fft_r2c=6,
-              fft_c2c=7, fft_mul=8, fft_c2r=9, reduce=10, vector=11, interp=12, fd=13)
+              fft_c2c=7, fft_mul=8, fft_c2r=9, reduce=10, vector=11, interp=12, fd=13, deriv=14)
 
 EXPORTED = [
     "claire_create", "claire_create_ex", "claire_destroy", "claire_set_stream", "claire_set_params",

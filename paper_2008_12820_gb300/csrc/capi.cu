@@ -325,15 +325,15 @@ struct claire_ctx {
     // first derivatives by the selected discretization
     void grad(const float *f, float *g) {
         if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
-        else spectral(OP_GRAD, f, g, nullptr);
+        else spectral_grad_1d(d, ax, f, g, st, &prof);
     }
     void grad_h(const float *f, __half *g) {
         if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
-        else spectral_grad_h(d, ax, f, g, spec, st, &prof);
+        else spectral_grad_1d(d, ax, f, g, st, &prof);
     }
     void div(const float *v, float *out) {
         if (deriv_fd8) launch_div_fd8(d, v, out, st, &prof);
-        else spectral(OP_DIV, v, out, nullptr);
+        else spectral_div_1d(d, ax, v, out, st, &prof);
     }
 
     // With state_ready, mhist and dispm already hold the state and the X- foot

@@ -144,9 +144,11 @@ void launch_bodyforce_dot(long long N, int nt, const float *lhist, const __half 
 // FP16 <-> FP32 copies of n values
 void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof);
 void launch_h2f(const __half *in, float *out, long long n, cudaStream_t st, Profiler *prof);
-// first derivatives of an FP32 scalar field stored as an FP16 vector field
-void spectral_grad_h(const Dims &d, const FftPlan *ax, const float *in, __half *out, float2 *spec,
-                     cudaStream_t st, Profiler *prof);
+// spectral gradient / divergence by axis transforms: d/dx_a = F_a^-1 i k^_a F_a
+// (the same operator as through the 3D transform, one pass per axis)
+void spectral_grad_1d(const Dims &d, const FftPlan *ax, const float *f, float *g, cudaStream_t st, Profiler *prof);
+void spectral_grad_1d(const Dims &d, const FftPlan *ax, const float *f, __half *g, cudaStream_t st, Profiler *prof);
+void spectral_div_1d(const Dims &d, const FftPlan *ax, const float *v, float *out, cudaStream_t st, Profiler *prof);
 void launch_grad_fd8(const Dims &d, const float *f, __half *g, cudaStream_t st, Profiler *prof);
 
 // ------------------------------------------------------------- vectors ----

@@ -21,259 +21,14 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "claire_internal.cuh"
+#include "fft_core.cuh"
 
 namespace claire {
 
 namespace {
-
-// real fields are FP32, or FP16 in the FP16-storage form (FP32 arithmetic)
-__device__ __forceinline__ float ldr(const float *p) { return *p; }
-__device__ __forceinline__ void str(float *p, float v) { *p = v; }
-__device__ __forceinline__ void str(__half *p, float v) { *p = __float2half_rn(v); }
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// multiply by s*i (s = +-1)
-__device__ __forceinline__ float2 mul_si(float2 a, float s) { return make_float2(-s * a.y, s * a.x); }
-
-// in-register DFT of size R: X_q = sum_r a_r exp(s 2 pi i r q / R)
-template <int R> __device__ __forceinline__ void dft(float2 *a, float s);
-
-template <> __device__ __forceinline__ void dft<2>(float2 *a, float) {
-    float2 t = a[1];
-    a[1] = csub(a[0], t);
-    a[0] = cadd(a[0], t);
-}
-
-template <> __device__ __forceinline__ void dft<3>(float2 *a, float s) {
-    const float c = 0.86602540378443864676f;  // sqrt(3)/2
-    float2 t1 = cadd(a[1], a[2]);
-    float2 t2 = csub(a[1], a[2]);
-    float2 m = make_float2(a[0].x - 0.5f * t1.x, a[0].y - 0.5f * t1.y);
-    float2 r = mul_si(make_float2(c * t2.x, c * t2.y), s);
-    a[0] = cadd(a[0], t1);
-    a[1] = cadd(m, r);
-    a[2] = csub(m, r);
-}
-
-template <> __device__ __forceinline__ void dft<4>(float2 *a, float s) {
-    float2 t0 = cadd(a[0], a[2]);
-    float2 t1 = csub(a[0], a[2]);
-    float2 t2 = cadd(a[1], a[3]);
-    float2 t3 = mul_si(csub(a[1], a[3]), s);
-    a[0] = cadd(t0, t2);
-    a[2] = csub(t0, t2);
-    a[1] = cadd(t1, t3);
-    a[3] = csub(t1, t3);
-}
-
-template <> __device__ __forceinline__ void dft<5>(float2 *a, float s) {
-    const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
-    const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
-    const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
-    const float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
-    float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
-    float2 t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
-    float2 b1 = make_float2(a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y);
-    float2 b2 = make_float2(a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y);
-    float2 e1 = mul_si(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y), s);
-    float2 e2 = mul_si(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y), s);
-    a[0] = make_float2(a[0].x + t1.x + t2.x, a[0].y + t1.y + t2.y);
-    a[1] = cadd(b1, e1);
-    a[4] = csub(b1, e1);
-    a[2] = cadd(b2, e2);
-    a[3] = csub(b2, e2);
-}
-
-template <> __device__ __forceinline__ void dft<8>(float2 *a, float s) {
-    const float h = 0.70710678118654752440f;  // cos(pi/4)
-    float2 e[4] = {a[0], a[2], a[4], a[6]};
-    float2 o[4] = {a[1], a[3], a[5], a[7]};
-    dft<4>(e, s);
-    dft<4>(o, s);
-    // o_q *= exp(s 2 pi i q / 8)
-    o[1] = cmul(o[1], make_float2(h, s * h));
-    o[2] = mul_si(o[2], s);
-    o[3] = cmul(o[3], make_float2(-h, s * h));
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        a[q] = cadd(e[q], o[q]);
-        a[q + 4] = csub(e[q], o[q]);
-    }
-}
-
-// 16 = 4 x 4: DFT-4 over r2 for each r1, twiddle exp(s 2 pi i r1 q1 / 16),
-// DFT-4 over r1 for each q1; output index q1 + 4 q2
-template <> __device__ __forceinline__ void dft<16>(float2 *a, float s) {
-    const float c1 = 0.92387953251128675613f;  // cos(pi/8)
-    const float s1 = 0.38268343236508977173f;  // sin(pi/8)
-    const float h = 0.70710678118654752440f;
-    float2 y[4][4];
-#pragma unroll
-    for (int r1 = 0; r1 < 4; ++r1) {
-        float2 t[4] = {a[r1], a[r1 + 4], a[r1 + 8], a[r1 + 12]};
-        dft<4>(t, s);
-#pragma unroll
-        for (int q1 = 0; q1 < 4; ++q1) y[r1][q1] = t[q1];
-    }
-    y[1][1] = cmul(y[1][1], make_float2(c1, s * s1));   // e = 1
-    y[1][2] = cmul(y[1][2], make_float2(h, s * h));     // e = 2
-    y[1][3] = cmul(y[1][3], make_float2(s1, s * c1));   // e = 3
-    y[2][1] = cmul(y[2][1], make_float2(h, s * h));     // e = 2
-    y[2][2] = mul_si(y[2][2], s);                       // e = 4
-    y[2][3] = cmul(y[2][3], make_float2(-h, s * h));    // e = 6
-    y[3][1] = cmul(y[3][1], make_float2(s1, s * c1));   // e = 3
-    y[3][2] = cmul(y[3][2], make_float2(-h, s * h));    // e = 6
-    y[3][3] = cmul(y[3][3], make_float2(-c1, -s * s1)); // e = 9
-#pragma unroll
-    for (int q1 = 0; q1 < 4; ++q1) {
-        float2 t[4] = {y[0][q1], y[1][q1], y[2][q1], y[3][q1]};
-        dft<4>(t, s);
-#pragma unroll
-        for (int q2 = 0; q2 < 4; ++q2) a[q1 + 4 * q2] = t[q2];
-    }
-}
-
-// One Stockham stage of radix R over L lines stored as buf[e * ls + l]
-// (e = element index, l = line).  Ns = product of the earlier radices.
-template <int R, int L>
-__device__ __forceinline__ void stage(const float2 *__restrict__ A, float2 *__restrict__ B,
-                                      int n, int Ns, int ls, const float2 *__restrict__ tw,
-                                      float s) {
-    const int nb = n / R;
-    const int work = nb * L;
-    const int tstride = n / (Ns * R);
-    for (int t = threadIdx.x; t < work; t += blockDim.x) {
-        const int l = t % L;
-        const int j = t / L;
-        const int k = j % Ns;
-        float2 a[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = A[(j + r * nb) * ls + l];
-        if (k != 0) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(tw + r * k * tstride);
-                w.y *= -s;  // table holds exp(-2 pi i t/n); s = +1 conjugates
-                a[r] = cmul(a[r], w);
-            }
-        }
-        dft<R>(a, s);
-        const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) B[(base + r * Ns) * ls + l] = a[r];
-    }
-}
-
-// Full FFT of L lines of length p.n, data in A, B as scratch.  s = -1
-// forward, +1 inverse (unnormalized).  Returns the buffer holding the result.
-// Leaves a __syncthreads() after every stage.
-template <int L>
-__device__ float2 *fft_lines(float2 *A, float2 *B, const FftPlan &p, int ls, float s) {
-    int Ns = 1;
-    for (int st = 0; st < p.nst; ++st) {
-        const int R = p.rad[st];
-        switch (R) {
-            case 2: stage<2, L>(A, B, p.n, Ns, ls, p.tw, s); break;
-            case 3: stage<3, L>(A, B, p.n, Ns, ls, p.tw, s); break;
-            case 4: stage<4, L>(A, B, p.n, Ns, ls, p.tw, s); break;
-            default: stage<5, L>(A, B, p.n, Ns, ls, p.tw, s); break;
-        }
-        __syncthreads();
-        float2 *t = A;
-        A = B;
-        B = t;
-        Ns *= R;
-    }
-    return A;
-}
-
-// ---------------------------------------------------------------------------
-// Compile-time plans for the common grid sizes: radix 16 while it divides the
-// power-of-two part, then one 8, 4 or 2, then 3s, then 5s.  With the length,
-// radices and strides known, every index division folds into shifts or
-// multiplications and the loops unroll; radix 8 and 16 keep more of the
-// transform in registers (fewer shared-memory passes and barriers).
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr int pow2_part(int n) {
-    int p = 1;
-    while (n % 2 == 0) { n /= 2; p *= 2; }
-    return p;
-}
-__host__ __device__ constexpr int radix_at(int n, int s) {
-    int p2 = pow2_part(n), rest = n / p2, st = 0;
-    while (p2 >= 16) { if (st == s) return 16; p2 /= 16; ++st; }
-    if (p2 > 1) { if (st == s) return p2; ++st; }
-    while (rest % 3 == 0) { if (st == s) return 3; rest /= 3; ++st; }
-    while (rest % 5 == 0) { if (st == s) return 5; rest /= 5; ++st; }
-    return 0;
-}
-__host__ __device__ constexpr int num_stages(int n) {
-    int s = 0;
-    while (radix_at(n, s) != 0) ++s;
-    return s;
-}
-__host__ __device__ constexpr int ns_before(int n, int s) {
-    int p = 1;
-    for (int i = 0; i < s; ++i) p *= radix_at(n, i);
-    return p;
-}
-
-template <int N, int R, int NS, int L>
-__device__ __forceinline__ void stage_ct(const float2 *__restrict__ A, float2 *__restrict__ B,
-                                         int ls, const float2 *__restrict__ tw, float s) {
-    constexpr int NB = N / R, WORK = NB * L, TSTRIDE = N / (NS * R);
-#pragma unroll 2
-    for (int t = threadIdx.x; t < WORK; t += kThreads) {
-        const int l = t % L;
-        const int j = t / L;
-        const int k = j % NS;
-        float2 a[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) a[r] = A[(j + r * NB) * ls + l];
-        if (NS > 1 && k != 0) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(tw + r * k * TSTRIDE);
-                w.y *= -s;
-                a[r] = cmul(a[r], w);
-            }
-        }
-        dft<R>(a, s);
-        const int base = (j / NS) * NS * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) B[(base + r * NS) * ls + l] = a[r];
-    }
-}
-
-template <int N, int L, int S = 0>
-__device__ __forceinline__ float2 *fft_ct(float2 *A, float2 *B, const float2 *__restrict__ tw,
-                                          int ls, float s) {
-    if constexpr (S == num_stages(N)) {
-        return A;
-    } else {
-        stage_ct<N, radix_at(N, S), ns_before(N, S), L>(A, B, ls, tw, s);
-        __syncthreads();
-        return fft_ct<N, L, S + 1>(B, A, tw, ls, s);
-    }
-}
-
-// N > 0: compile-time plan of that length; N == 0: the runtime plan p
-template <int N>
-struct Fft {
-    __device__ __forceinline__ static int size(const FftPlan &p) { return N > 0 ? N : p.n; }
-    template <int L>
-    __device__ __forceinline__ static float2 *run(float2 *A, float2 *B, const FftPlan &p, int ls,
-                                                  float s) {
-        if constexpr (N > 0) return fft_ct<N, L>(A, B, p.tw, ls, s);
-        else return fft_lines<L>(A, B, p, ls, s);
-    }
-};
-
 // ---------------------------------------------------------------- pass 1 ---
 // x3 forward real -> half spectrum.  Block: L complex lines = 2L real lines.
 template <int N, int L, typename TI = float>
@@ -330,21 +85,14 @@ k_c2c_x2(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s) {
     }
 }
 
-__device__ __forceinline__ float wavenumber(int i, int n) { return (2 * i < n) ? (float)i : (float)(i - n); }
-__device__ __forceinline__ float wavenumber_d1(int i, int n) {
-    return ((n & 1) == 0 && 2 * i == n) ? 0.f : wavenumber(i, n);
-}
-
 // ---------------------------------------------------------------- pass 3 ---
 // x1 forward, multiplier, x1 inverse, in place.  Block: (k3 tile, k2 index).
-// Buffers: NB = max(nin, nout) component tiles of n1*TK plus one scratch.
+// Buffers: three component tiles of n1*TK plus one scratch.
 template <int N, int TK, int OP>
 __global__ void __launch_bounds__(kThreads)
 k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
          long long cstride, SpecParams sp) {
-    constexpr int NIN = (OP == OP_GRAD) ? 1 : 3;
-    constexpr int NOUT = (OP == OP_DIV) ? 1 : 3;
-    constexpr int NB = NIN > NOUT ? NIN : NOUT;
+    constexpr int NIN = 3, NOUT = 3, NB = 3;  // A, A^-1 and the x1-only passes couple all components
     constexpr bool FWD = OP != OP_X1INV, INV = OP != OP_X1FWD;
     extern __shared__ float2 sm[];
     const int n1 = Fft<N>::size(p1);
@@ -388,17 +136,6 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
                 const float2 f = buf[c][id];
                 buf[c][id] = make_float2(f.x * sp.scale, f.y * sp.scale);
             }
-        } else if (OP == OP_GRAD) {
-            const float2 f = buf[0][id];
-            // i k_d f * scale
-            buf[0][id] = make_float2(-k1d * f.y * sp.scale, k1d * f.x * sp.scale);
-            buf[1][id] = make_float2(-k2d * f.y * sp.scale, k2d * f.x * sp.scale);
-            buf[2][id] = make_float2(-k3d * f.y * sp.scale, k3d * f.x * sp.scale);
-        } else if (OP == OP_DIV) {
-            const float2 a = buf[0][id], b = buf[1][id], c = buf[2][id];
-            const float re = k1d * a.x + k2d * b.x + k3d * c.x;
-            const float im = k1d * a.y + k2d * b.y + k3d * c.y;
-            buf[0][id] = make_float2(-im * sp.scale, re * sp.scale);
         } else {
             const float2 a = buf[0][id], b = buf[1][id], c = buf[2][id];
             const float kk = k1 * k1 + k2 * k2 + k3 * k3;
@@ -495,25 +232,6 @@ k_c2r_x3(const float2 *__restrict__ in, TO *__restrict__ out, const float *__res
 
 // -------------------------------------------------------------- launchers --
 
-template <typename K>
-void set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-// lines per block of the x3 passes and column tile of the strided passes,
-// chosen so that a block's shared memory stays near or below ~112 KB
-constexpr int lines_x3(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
-constexpr int tile_cols(int n, int nbuf) {
-    // nbuf data buffers + one scratch of n*TK float2
-    return (size_t)(nbuf + 1) * n * 16 * sizeof(float2) <= 112 * 1024 ? 16
-         : (size_t)(nbuf + 1) * n * 8 * sizeof(float2) <= 112 * 1024 ? 8 : 4;
-}
-
-// the axis lengths with a compile-time plan; other valid lengths use the
-// runtime plan (N = 0)
-#define CLAIRE_CT_SIZES(X) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(384) X(512) X(768)
-
 template <int N, int L, typename TI>
 void r2c_l(const Dims &d, const FftPlan &p, const TI *in, float2 *out, long long nlines,
            cudaStream_t st) {
@@ -581,9 +299,7 @@ void c2c_x2(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, c
 
 template <int N, int TK, int OP>
 void mul_t(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
-    constexpr int NIN = (OP == OP_GRAD) ? 1 : 3;
-    constexpr int NOUT = (OP == OP_DIV) ? 1 : 3;
-    constexpr int NB = NIN > NOUT ? NIN : NOUT;
+    constexpr int NB = 3;
     const size_t smem = (size_t)(NB + 1) * d.n1 * TK * sizeof(float2);
     const long long cstride = (long long)d.n1 * d.n2 * d.p3;
     dim3 grid((d.h3 + TK - 1) / TK, d.n2);
@@ -724,8 +440,17 @@ __global__ void k_spec_twolevel(float2 *__restrict__ sf, Dims df, const float2 *
 void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParams &sp,
                     const float *in, float *out, const float *add, float2 *spec, cudaStream_t st,
                     Profiler *prof) {
-    const int nin = (op == OP_GRAD) ? 1 : 3;
-    const int nout = (op == OP_DIV) ? 1 : 3;
+    // first derivatives go through the axis transforms (fft_axis.cu); the
+    // 3D passes below serve the operators that couple wavenumbers, A and A^-1
+    if (op == OP_GRAD) {
+        spectral_grad_1d(d, ax, in, out, st, prof);
+        return;
+    }
+    if (op == OP_DIV) {
+        spectral_div_1d(d, ax, in, out, st, prof);
+        return;
+    }
+    const int nin = 3, nout = 3;
     // algorithmic bytes: real fields 4 B/voxel, half spectra 8 B per stored mode
     const double R = 4.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
     {
@@ -739,8 +464,6 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
     {
         ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, (nin + nout) * C);
         switch (op) {
-            case OP_GRAD: mul_x1_op<OP_GRAD>(d, ax[0], spec, sp, st); break;
-            case OP_DIV: mul_x1_op<OP_DIV>(d, ax[0], spec, sp, st); break;
             case OP_A: mul_x1_op<OP_A>(d, ax[0], spec, sp, st); break;
             case OP_AINV: mul_x1_op<OP_AINV>(d, ax[0], spec, sp, st); break;
             default: break;
@@ -753,32 +476,6 @@ void spectral_apply(const Dims &d, const FftPlan *ax, SpecOp op, const SpecParam
     {
         ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, nout * (R + C + (add ? R : 0.0)));
         c2r_x3(d, ax[2], spec, out, add, nout, st);
-    }
-}
-
-void spectral_grad_h(const Dims &d, const FftPlan *ax, const float *in, __half *out, float2 *spec,
-                     cudaStream_t st, Profiler *prof) {
-    const double R = 4.0 * d.N, Rh = 2.0 * d.N, C = 8.0 * d.n1 * d.n2 * d.h3;
-    const SpecParams sp{0.f, 0.f, (float)(1.0 / (double)d.N)};
-    {
-        ProfScope ps(prof, CLAIRE_K_FFT_R2C, st, R + C);
-        r2c_x3(d, ax[2], in, spec, 1, st);
-    }
-    {
-        ProfScope ps(prof, CLAIRE_K_FFT_C2C, st, 2 * C);
-        c2c_x2(d, ax[1], spec, 1, -1.f, st);
-    }
-    {
-        ProfScope ps(prof, CLAIRE_K_FFT_MUL, st, 4 * C);
-        mul_x1_op<OP_GRAD>(d, ax[0], spec, sp, st);
-    }
-    {
-        ProfScope ps(prof, CLAIRE_K_FFT_C2C, st, 3 * 2 * C);
-        c2c_x2(d, ax[1], spec, 3, +1.f, st);
-    }
-    {
-        ProfScope ps(prof, CLAIRE_K_FFT_C2R, st, 3 * (Rh + C));
-        c2r_x3(d, ax[2], spec, out, nullptr, 3, st);
     }
 }
 
