@@ -385,28 +385,30 @@ struct claire_ctx {
                   bool state_ready = false) {
         linearize(v, state_ready);
         const size_t N = d.N;
-        if (h16) {
-            // FP32 adjoint transport with FP16 copies of lambda^j
-            float *a = s1a, *b = s1b;
-            launch_sub(d, m1, m1f, a, st, &prof);
-            launch_f2h(a, hist(lhist_h, nt), (long long)N, st, &prof);
-            for (int j = nt; j >= 1; --j) {
-                launch_adjoint_step(d, a, dispp, rng_p(), cfac, b, st, &prof, CLAIRE_K_ADJOINT,
-                                    hist(lhist_h, j - 1));
-                std::swap(a, b);
-            }
-        } else {
-            launch_sub(d, m1, hist(mhist, nt), hist(lhist, nt), st, &prof);
-            for (int j = nt; j >= 1; --j)
-                launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
-                                    CLAIRE_K_ADJOINT);
-        }
         if (!Av) {
             spectral(OP_A, vlin, s3a, nullptr);
             Av = s3a;
         }
-        if (h16) launch_bodyforce(d, nt, lhist_h, gmhist_h, Av, g, st, &prof);
-        else launch_bodyforce(d, nt, lhist, gmhist, Av, g, st, &prof);
+        // g = beta A v + the body force of Eq. 3.3 by the trapezoidal rule,
+        // each term added by the adjoint step that makes its lambda^j
+        const float dt = 1.f / nt;
+        auto wt = [&](int j) { return (j == 0 || j == nt) ? 0.5f * dt : dt; };
+        if (h16) {
+            // FP32 adjoint transport with FP16 copies of lambda^j
+            float *a = s1a, *b = s1b;
+            launch_adjfinal_acc(d, m1, m1f, a, hist(lhist_h, nt), hist(gmhist_h, nt, 3), Av, g, wt(nt), st, &prof);
+            for (int j = nt; j >= 1; --j) {
+                launch_adjoint_acc(d, a, dispp, rng_p(), cfac, b, hist(gmhist_h, j - 1, 3), g, wt(j - 1), nullptr,
+                                   nullptr, nullptr, nullptr, st, &prof, CLAIRE_K_ADJOINT, hist(lhist_h, j - 1));
+                std::swap(a, b);
+            }
+        } else {
+            launch_adjfinal_acc(d, m1, hist(mhist, nt), hist(lhist, nt), nullptr, hist(gmhist, nt, 3), Av, g, wt(nt),
+                                st, &prof);
+            for (int j = nt; j >= 1; --j)
+                launch_adjoint_acc(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), hist(gmhist, j - 1, 3),
+                                   g, wt(j - 1), nullptr, nullptr, nullptr, nullptr, st, &prof, CLAIRE_K_ADJOINT);
+        }
         check_launch("gradient");
         if (J || mis_out) {
             const double H3 = h3();
@@ -425,45 +427,43 @@ struct claire_ctx {
     // capture there) and while the profiler records per-launch events.
     struct MvGraph {
         cudaGraphExec_t exec = nullptr;
-        const float *vt = nullptr, *Avt = nullptr;
+        const float *vt = nullptr;
         float *Hvt = nullptr;
-        bool want_dot = false, u0_ready = false;
         unsigned long long epoch = ~0ULL;
         int seen = 0;       // calls with this signature so far
         long kernels = 0;   // kernel launches one replay stands for
-        bool same(const float *a, float *b, const float *c, bool w, bool u, unsigned long long e) const {
-            return vt == a && Hvt == b && Avt == c && want_dot == w && u0_ready == u && epoch == e;
+        bool same(const float *a, float *b, unsigned long long e) const {
+            return vt == a && Hvt == b && epoch == e;
         }
     } mvg;
     unsigned long long lin_epoch = 0;  // bumped by every linearization
     bool use_graphs = true;
 
-    // Hvt = beta A vt + int lt grad m dt.  Avt, if given, is beta*A vt already
-    // at hand (PCG carries it along); otherwise it is applied spectrally.
-    // With Avt and want_dot, dres[0] receives vt . Hvt from the same pass.
-    // u0_ready: s1a already holds u0 = dt/2 f^0 (written by the PCG direction
-    // update, launch_pcg_dir_u0).
-    void matvec(const float *vt, float *Hvt, const float *Avt = nullptr, bool want_dot = false,
-                bool u0_ready = false) {
+    // Hvt = beta A vt + int lt grad m dt (Eq. 3.4-3.6).  The PCG form (pcg):
+    // s1a already holds u0 = dt/2 f^0 and dres[8] holds vt . beta A vt (both
+    // written by the PCG direction update, launch_pcg_dir_u0); Hvt receives
+    // the body force only (the PCG update adds beta A vt, which it carries)
+    // and dres[0] receives vt . H vt.
+    void matvec(const float *vt, float *Hvt, bool pcg = false) {
         if (!have_lin) throw Error(CLAIRE_ERR_STATE, "no linearization (call claire_gradient or claire_linearize)");
-        const bool graph = use_graphs && Avt && capturable(st) && !prof.on;
+        const bool graph = use_graphs && pcg && capturable(st) && !prof.on;
         if (graph) {
-            if (mvg.same(vt, Hvt, Avt, want_dot, u0_ready, lin_epoch)) {
+            if (mvg.same(vt, Hvt, lin_epoch)) {
                 if (mvg.exec) {
                     CK(cudaGraphLaunch(mvg.exec, st));
                     prof.launches += mvg.kernels;
                     return;
                 }
-                if (mvg.seen >= 1 && capture_matvec(vt, Hvt, Avt, want_dot, u0_ready)) return;
+                if (mvg.seen >= 1 && capture_matvec(vt, Hvt)) return;
             } else {
                 drop_graph();
-                mvg.vt = vt; mvg.Hvt = Hvt; mvg.Avt = Avt; mvg.want_dot = want_dot; mvg.u0_ready = u0_ready;
+                mvg.vt = vt; mvg.Hvt = Hvt;
                 mvg.epoch = lin_epoch;
                 mvg.seen = 0;
             }
             ++mvg.seen;
         }
-        matvec_launches(vt, Hvt, Avt, want_dot, u0_ready);
+        matvec_launches(vt, Hvt, pcg);
         check_launch("hess_matvec");
     }
 
@@ -480,7 +480,7 @@ struct claire_ctx {
 
     // captures and runs the matvec as a graph; false (and graphs off for this
     // context, the launches not yet run) if the runtime refuses the capture
-    bool capture_matvec(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
+    bool capture_matvec(const float *vt, float *Hvt) {
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
             use_graphs = false;
@@ -488,7 +488,7 @@ struct claire_ctx {
         }
         const long before = prof.launches;
         try {
-            matvec_launches(vt, Hvt, Avt, want_dot, u0_ready);
+            matvec_launches(vt, Hvt, true);
             mvg.kernels = prof.launches - before;
         } catch (...) {
             cudaGraph_t g = nullptr;
@@ -512,10 +512,10 @@ struct claire_ctx {
         return true;
     }
 
-    void matvec_launches(const float *vt, float *Hvt, const float *Avt, bool want_dot, bool u0_ready) {
+    void matvec_launches(const float *vt, float *Hvt, bool pcg) {
         const float dt = 1.f / nt;
         float *u = s1a, *un = s1b;
-        if (!u0_ready) {
+        if (!pcg) {
             if (h16) launch_incstate_init(d, dt, vt, hist(gmhist_h, 0, 3), u, st, &prof);
             else launch_incstate_init(d, dt, vt, hist(gmhist, 0, 3), u, st, &prof);
         }
@@ -524,20 +524,26 @@ struct claire_ctx {
             else launch_incstate_step(d, dt, u, dispm, rng_m(), vt, hist(gmhist, j + 1, 3), un, st, &prof);
             float *t = u; u = un; un = t;
         }
-        // the last step writes the incremental adjoint's final condition
-        if (h16) launch_incstate_last(d, dt, u, dispm, rng_m(), vt, hist(gmhist_h, nt, 3), hist(lhist, nt), mt, st, &prof);
-        else launch_incstate_last(d, dt, u, dispm, rng_m(), vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, st, &prof);
-        for (int j = nt; j >= 1; --j)
-            launch_adjoint_step(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), st, &prof,
-                                CLAIRE_K_INCADJ);
-        if (Avt && want_dot) {
-            if (h16) launch_bodyforce_dot(d.N, nt, lhist, gmhist_h, Avt, vt, Hvt, partial, dres, st, &prof);
-            else launch_bodyforce_dot(d.N, nt, lhist, gmhist, Avt, vt, Hvt, partial, dres, st, &prof);
-        } else {
-            if (h16) launch_bodyforce(d, nt, lhist, gmhist_h, Avt, Hvt, st, &prof);
-            else launch_bodyforce(d, nt, lhist, gmhist, Avt, Hvt, st, &prof);
-            if (!Avt) spectral(OP_A, vt, Hvt, Hvt);
+        // the last step writes the incremental adjoint's final condition and
+        // starts the body force (Eq. 3.6) in Hvt; every incremental-adjoint
+        // step adds its own trapezoid term, the last one also forms vt . H vt
+        if (h16)
+            launch_incstate_last(d, dt, u, dispm, rng_m(), vt, hist(gmhist_h, nt, 3), hist(lhist, nt), mt, Hvt, st,
+                                 &prof);
+        else
+            launch_incstate_last(d, dt, u, dispm, rng_m(), vt, hist(gmhist, nt, 3), hist(lhist, nt), mt, Hvt, st,
+                                 &prof);
+        for (int j = nt; j >= 1; --j) {
+            const float w = j == 1 ? 0.5f * dt : dt;
+            const float *p = (pcg && j == 1) ? vt : nullptr;
+            if (h16)
+                launch_adjoint_acc(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), hist(gmhist_h, j - 1, 3),
+                                   Hvt, w, p, partial, dres + 8, dres, st, &prof, CLAIRE_K_INCADJ);
+            else
+                launch_adjoint_acc(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), hist(gmhist, j - 1, 3),
+                                   Hvt, w, p, partial, dres + 8, dres, st, &prof, CLAIRE_K_INCADJ);
         }
+        if (!pcg) spectral(OP_A, vt, Hvt, Hvt);
     }
 
     // ---- differentiable transport with state checkpointing -----------------
@@ -793,7 +799,7 @@ int claire_create_ex(int nx, int ny, int nz, int nt, double beta, double gamma, 
         c->fdisp = c->alloc_f(3 * N);
         c->spec = (float2 *)c->alloc_bytes((size_t)3 * nx * ny * c->d.p3 * sizeof(float2));
         c->partial = (double *)c->alloc_bytes(4 * kReduceBlocks * sizeof(double));
-        c->dres = (double *)c->alloc_bytes(8 * sizeof(double));
+        c->dres = (double *)c->alloc_bytes(16 * sizeof(double));
         c->dflag = (int *)c->alloc_bytes(sizeof(int));
         c->rng = (int *)c->alloc_bytes(24 * sizeof(int));
         c->fpart = (int *)c->alloc_bytes((size_t)footpoint_parts(c->d) * sizeof(int));
@@ -1131,14 +1137,15 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                 return q;
             };
             // the direction update also writes u0 of the next matvec into s1a
+            // and p . beta A p into dres[8] (the matvec's PCG form)
             auto pcg_dir = [&](const float *Az, float b, bool init) {
                 const float hdt = 0.5f / ctx->nt;
                 if (ctx->h16)
                     launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, b, N, init, ctx->hist(ctx->gmhist_h, 0, 3),
-                                      ctx->s1a, hdt, st, &ctx->prof);
+                                      ctx->s1a, hdt, ctx->partial, ctx->dres + 8, st, &ctx->prof);
                 else
                     launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, b, N, init, ctx->hist(ctx->gmhist, 0, 3),
-                                      ctx->s1a, hdt, st, &ctx->prof);
+                                      ctx->s1a, hdt, ctx->partial, ctx->dres + 8, st, &ctx->prof);
             };
             if (r0 > 0) {
                 const float *Az = apply_pc();
@@ -1147,7 +1154,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                 while (it < maxit) {
                     {
                         EvTimer t(st, &rep.t_hess_ms);
-                        ctx->matvec(p, q, Ap, true, true);
+                        ctx->matvec(p, q, true);
                     }
                     rep.n_matvec++;
                     const double pq = ctx->fetch(0);
@@ -1163,7 +1170,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                     }
                     const double alpha = rz / pq;
                     launch_pcg_update(x, Ax, r, p, Ap, q, (float)alpha, N, ctx->partial, ctx->dres, st,
-                                      &ctx->prof);
+                                      &ctx->prof, true);
                     ++it;
                     const double rn = std::sqrt(ctx->fetch(0));
                     if (o.fixed_pcg == 0 && rn <= epsk * r0) break;

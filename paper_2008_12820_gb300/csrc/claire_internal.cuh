@@ -108,15 +108,32 @@ void launch_incstate_step(const Dims &d, float dt, const float *src, const float
                           const int *range_m, const float *vt, const float *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof);
 // the last incremental-state step fused with the incremental adjoint's final
-// condition: lt_last = -mt(1), mt_out (nullable) = mt(1)
+// condition: lt_last = -mt(1), mt_out (nullable) = mt(1), b_out (nullable)
+// [3][N] = the body force's first term dt/2 lt(1) grad m(1)
 void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
-                          const float *vt, const float *gm_last, float *lt_last, float *mt_out,
+                          const float *vt, const float *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof);
 void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
-                          const float *vt, const __half *gm_last, float *lt_last, float *mt_out,
+                          const float *vt, const __half *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof);
-void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
-                Profiler *prof);  // out = a - b
+// adjoint step dst = c src(X+) that also adds w dst grad m^{j-1} to the body
+// force b [3][N] in place (gm = grad m^{j-1}).  With p non-null it also
+// forms p . b of the updated b: block partials in partial, their sum plus
+// *dot_add (nullable) in *dot_out.  dst_h: optional FP16 copy of dst.
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+                        float *dst, const float *gm, float *b, float w, const float *p, double *partial,
+                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
+                        __half *dst_h = nullptr);
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+                        float *dst, const __half *gm, float *b, float w, const float *p, double *partial,
+                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
+                        __half *dst_h = nullptr);
+// the adjoint's final condition l = m1 - m (l_h: optional FP16 copy) and the
+// gradient started as g = Av + w l gm  (gm = grad m(1), w = dt/2)
+void launch_adjfinal_acc(const Dims &d, const float *m1, const float *m, float *l, __half *l_h, const float *gm,
+                         const float *Av, float *g, float w, cudaStream_t st, Profiler *prof);
+void launch_adjfinal_acc(const Dims &d, const float *m1, const float *m, float *l, __half *l_h, const __half *gm,
+                         const float *Av, float *g, float w, cudaStream_t st, Profiler *prof);
 // b += w * l * gm
 void launch_bodyforce_acc(const Dims &d, float *b, const float *l, const float *gm, float w,
                           cudaStream_t st, Profiler *prof);
@@ -124,8 +141,6 @@ void launch_bodyforce_acc(const Dims &d, float *b, const float *l, const float *
 void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float *m,
                           const float *gm_final, float gmis, float inv_h3, cudaStream_t st,
                           Profiler *prof);
-void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,
-                      const float *add, float *out, cudaStream_t st, Profiler *prof);
 
 // FP16-storage form: the stored trajectories (m^j, grad m^j, lambda^j) are
 // FP16; these overloads read them as such and compute in FP32
@@ -134,13 +149,6 @@ void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
                           const int *range_m, const float *vt, const __half *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof);
-void launch_bodyforce(const Dims &d, int nt, const float *lhist, const __half *gmhist,
-                      const float *add, float *out, cudaStream_t st, Profiler *prof);
-void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *gmhist,
-                      const float *add, float *out, cudaStream_t st, Profiler *prof);
-void launch_bodyforce_dot(long long N, int nt, const float *lhist, const __half *gmhist,
-                          const float *Ap, const float *p, float *q, double *partial,
-                          double *dev_out, cudaStream_t st, Profiler *prof);
 // FP16 <-> FP32 copies of n values
 void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof);
 void launch_h2f(const __half *in, float *out, long long n, cudaStream_t st, Profiler *prof);
@@ -153,6 +161,8 @@ void launch_grad_fd8(const Dims &d, const float *f, __half *g, cudaStream_t st, 
 
 // ------------------------------------------------------------- vectors ----
 // FP64 reductions; results land in dev_out[0..k) (device doubles)
+// dev_out[0] = sum of partial[0..nb) (+ add[0] if add is non-null)
+void launch_finalize(const double *partial, int nb, const double *add, double *dev_out, cudaStream_t st);
 void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
                 cudaStream_t st, Profiler *prof);
 void launch_sqdiff(const float *a, const float *b, long long n, double *partial,
@@ -169,27 +179,25 @@ void launch_diff_flag(const float *a, const float *b, long long n, int *flag, cu
 // stats of a vector field [3][N]: dev_out[0] = r.r, dev_out[1..3] = component sums
 void launch_stats(const float *r, long long N, double *partial, double *dev_out, cudaStream_t st,
                   Profiler *prof);
-// x += a p; Ax += a Ap; r -= a q; then the stats of r into dev_out[0..3]
+// x += a p; Ax += a Ap; r -= a q (q_adds_Ap: r -= a (q + Ap), q holding the
+// body force of H p only); then the stats of r into dev_out[0..3]
 void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
-                       cudaStream_t st, Profiler *prof);
+                       cudaStream_t st, Profiler *prof, bool q_adds_Ap = false);
 // p = z + b p; Ap = (r - mean r) + b Ap (rsum: device component sums of r);
 // with Az given (beta*A z), Ap = Az + b Ap instead.  x += a p skips Ax if NULL.
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
                     const float *Az, float b, long long N, bool init, cudaStream_t st,
                     Profiler *prof);
 // launch_pcg_dir that also writes u0 = dt/2 * (-p . gm0) (N floats), the
-// first incremental-state field of the next matvec (hdt = dt/2)
+// first incremental-state field of the next matvec (hdt = dt/2), and, with
+// pap_out non-null, p . Ap of the new direction into *pap_out
 void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
-                       float b, long long N, bool init, const float *gm0, float *u0, float hdt, cudaStream_t st,
-                       Profiler *prof);
+                       float b, long long N, bool init, const float *gm0, float *u0, float hdt, double *partial,
+                       double *pap_out, cudaStream_t st, Profiler *prof);
 void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
-                       float b, long long N, bool init, const __half *gm0, float *u0, float hdt, cudaStream_t st,
-                       Profiler *prof);
-// q = Ap + body force of (lhist, gmhist); dev_out[0] = p . q (fused curvature)
-void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
-                          const float *Ap, const float *p, float *q, double *partial,
-                          double *dev_out, cudaStream_t st, Profiler *prof);
+                       float b, long long N, bool init, const __half *gm0, float *u0, float hdt, double *partial,
+                       double *pap_out, cudaStream_t st, Profiler *prof);
 // q = Ap + gm (gm . p): the zero-velocity Hessian given beta0*A p
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
                      cudaStream_t st, Profiler *prof);

@@ -10,6 +10,10 @@
 //   adjoint (Eq. 3.2, 3.6)         l^{j-1}   = c * l^j(X+)
 //   incremental state (Eq. 3.5)    u^{j+1}   = u^j(X-) + dt f^{j+1},
 //                                   f = -vt . grad m,  u = mt + dt/2 f
+// The adjoint steps can also carry the body force of Eq. 3.3 / 3.6,
+// b = sum_j w_j l^j grad m^j (trapezoid weights w_j), along: each step adds
+// its own term to b while l^{j-1} is still in registers, so no later pass
+// re-reads the whole trajectories.
 // The foot points are stored as displacements in grid-index units, so the
 // integer part and the interpolation weight of each axis come from a small
 // number (no loss of precision at large grid indices).
@@ -27,6 +31,7 @@
 #include <type_traits>
 
 #include "claire_internal.cuh"
+#include "reduce.cuh"
 
 namespace claire {
 
@@ -253,8 +258,11 @@ __global__ void __launch_bounds__(256) k_range_parts(const int *__restrict__ par
 // Arguments shared by the semi-Lagrangian step kernels.
 // ---------------------------------------------------------------------------
 // SL_INCLAST: the last incremental-state step, whose epilogue writes the
-// incremental adjoint's final condition lt(1) = -mt(1) (and mt(1)) directly
-enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3, SL_INCLAST = 4 };
+// incremental adjoint's final condition lt(1) = -mt(1) (and mt(1)) directly,
+// and optionally the first body-force term w_nt lt(1) grad m(1).
+// SL_ADJACC: adjoint step that adds w l^{j-1} grad m^{j-1} to the body force;
+// SL_ADJDOT: the same, and the block partials of p . b of the finished sum.
+enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3, SL_INCLAST = 4, SL_ADJACC = 5, SL_ADJDOT = 6 };
 
 // TS: storage type of the gathered and written field; TG: of grad m
 template <typename TS = float, typename TG = float>
@@ -264,10 +272,14 @@ struct SlArgsT {
     TS *dst;
     const float *aux;   // SL_ADJ: c;  SL_ADJFAC: div v on the grid
     const float *vt;    // SL_INCSTATE: vt [3][N]
-    const TG *gm;       // SL_INCSTATE: grad m^{j+1} [3][N]
+    const TG *gm;       // SL_INCSTATE: grad m^{j+1};  SL_ADJACC/SL_ADJDOT: grad m^{j-1}  [3][N]
     float dt;
-    __half *dst_h = nullptr;  // SL_PLAIN / SL_ADJ: optional FP16 copy of dst (stored trajectories)
+    __half *dst_h = nullptr;  // SL_PLAIN / SL_ADJ / SL_ADJACC: optional FP16 copy of dst (stored trajectories)
     float *dst2 = nullptr;    // SL_INCLAST: mt(1) (optional)
+    float *acc = nullptr;     // body force b [3][N]: SL_ADJACC/SL_ADJDOT update it, SL_INCLAST starts it (optional)
+    float w = 0.f;            // SL_ADJACC/SL_ADJDOT: trapezoid weight of the new term (dt, dt/2 at j = 0)
+    const float *pv = nullptr;      // SL_ADJDOT: p [3][N]
+    double *partial = nullptr;      // SL_ADJDOT: one partial sum of p . b per block
 };
 using SlArgs = SlArgsT<float, float>;
 
@@ -348,12 +360,32 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
+// epilogue inputs prefetched with the next tile's displacements
 template <int MODE> struct EpiCount {
     static constexpr int v = (MODE == SL_INCSTATE || MODE == SL_INCLAST) ? 6 : (MODE == SL_PLAIN ? 0 : 1);
 };
+// epilogue inputs of the accumulating adjoint steps, loaded when a tile
+// starts (grad m^{j-1}, b, and p for the dot): prefetching them a tile ahead
+// as well would hold twice as many registers
+template <int MODE> struct EarlyCount {
+    static constexpr int v = MODE == SL_ADJACC ? 6 : (MODE == SL_ADJDOT ? 9 : 0);
+};
 
 template <int MODE, typename A>
-__device__ __forceinline__ void sl_epilogue(const A &a, long long id, float val, const float *e) {
+__device__ __forceinline__ void sl_load_early(const A &a, long long id, long long N, float *x) {
+    if (MODE == SL_ADJACC || MODE == SL_ADJDOT) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            x[k] = ldf(a.gm + k * N + id);
+            x[3 + k] = a.acc[k * N + id];
+            if (MODE == SL_ADJDOT) x[6 + k] = a.pv[k * N + id];
+        }
+    }
+}
+
+template <int MODE, typename A>
+__device__ __forceinline__ void sl_epilogue(const A &a, long long id, long long N, float val, const float *e,
+                                            const float *x, Acc2 &dot) {
     if (MODE == SL_PLAIN) {
         stf(a.dst + id, val);
         if (a.dst_h) a.dst_h[id] = __float2half_rn(val);
@@ -367,18 +399,34 @@ __device__ __forceinline__ void sl_epilogue(const A &a, long long id, float val,
     } else if (MODE == SL_INCSTATE) {
         const float f = -(e[0] * e[3] + e[1] * e[4] + e[2] * e[5]);
         stf(a.dst + id, fmaf(a.dt, f, val));
-    } else {
+    } else if (MODE == SL_INCLAST) {
         // u(1) = u^{nt-1}(X-) + dt f(1); mt(1) = u(1) - dt/2 f(1); lt(1) = -mt(1)
         const float f = -(e[0] * e[3] + e[1] * e[4] + e[2] * e[5]);
         const float m = fmaf(a.dt, f, val) - 0.5f * a.dt * f;
         stf(a.dst + id, -m);
         if (a.dst2) a.dst2[id] = m;
+        if (a.acc) {
+            const float l = (0.5f * a.dt) * (-m);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) a.acc[k * N + id] = l * e[3 + k];
+        }
+    } else if (MODE == SL_ADJACC || MODE == SL_ADJDOT) {
+        const float r = e[0] * val;
+        stf(a.dst + id, r);
+        if (a.dst_h) a.dst_h[id] = __float2half_rn(r);
+        const float l = a.w * r;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float b = fmaf(l, x[k], x[3 + k]);
+            a.acc[k * N + id] = b;
+            if (MODE == SL_ADJDOT) dot.add_prod(x[6 + k], b);
+        }
     }
 }
 
 template <int MODE, typename A>
 __device__ __forceinline__ void sl_load_epi(const A &a, long long id, long long N, float *e) {
-    if (MODE == SL_ADJ || MODE == SL_ADJFAC) {
+    if (MODE == SL_ADJ || MODE == SL_ADJFAC || MODE == SL_ADJACC || MODE == SL_ADJDOT) {
         e[0] = a.aux[id];
     } else if (MODE == SL_INCSTATE || MODE == SL_INCLAST) {
         e[0] = a.vt[id]; e[1] = a.vt[N + id]; e[2] = a.vt[2 * N + id];
@@ -479,9 +527,13 @@ __device__ __forceinline__ float box_linear(const float *p, float u1, float u2, 
     return fmaf(u1, y1 - y0, y0);
 }
 
-// resident blocks per SM: the incremental-state step carries six epilogue
-// inputs per voxel and keeps two; the others fit three
-template <int MODE> struct SlOcc { static constexpr int v = (MODE == SL_INCSTATE || MODE == SL_INCLAST) ? 2 : 3; };
+// resident blocks per SM: the incremental-state steps carry six epilogue
+// inputs per voxel and the accumulating adjoint steps six or nine more loaded
+// per tile; they keep two, the others fit three
+template <int MODE> struct SlOcc {
+    static constexpr int v =
+        (MODE == SL_INCSTATE || MODE == SL_INCLAST || MODE == SL_ADJACC || MODE == SL_ADJDOT) ? 2 : 3;
+};
 
 // tiles of block b: a contiguous range, so neighbouring tiles (which share
 // halo rows in L2) run on the same block one after the other
@@ -495,6 +547,7 @@ __global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE>::v)
 k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_in) {
     static_assert(std::is_same<TS, float>::value, "the box path stages FP32 source fields");
     constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
+    constexpr int NX = EarlyCount<MODE>::v > 0 ? EarlyCount<MODE>::v : 1;
     extern __shared__ float smem[];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool chunked = chunked_in != 0;
@@ -507,8 +560,8 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
     const long long N = d.N, plane = (long long)d.n2 * d.n3;
     int tbeg, tend;
     tile_range(ntiles, tbeg, tend);
-    if (tbeg >= tend) return;
-    if (!use_box) {
+    Acc2 dot;
+    if (tbeg < tend && !use_box) {
         for (int tile = tbeg; tile < tend; ++tile) {
             const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
             const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
@@ -520,88 +573,98 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
                 const float val = ORDER == 1
                     ? gather8(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id])
                     : gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
-                float e[NE];
+                float e[NE], x[NX];
                 sl_load_epi<MODE>(a, id, N, e);
-                sl_epilogue<MODE>(a, id, val, e);
+                sl_load_early<MODE>(a, id, N, x);
+                sl_epilogue<MODE>(a, id, N, val, e, x, dot);
             }
         }
-        return;
-    }
-
-    auto issue_box = [&](int t1, int t2, int t3, float *buf) {
-        box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
-    };
-    auto load_regs = [&](int t1, int t2, int t3, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
-        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
-        const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
-#pragma unroll
-        for (int t = 0; t < PT1; ++t) {
-            if (i3 < d.n3 && i2 < d.n2 && t1 * PT1 + t < d.n1) {
-                const long long id = id0 + t * plane;
-                dd[t][0] = a.disp[id];
-                dd[t][1] = a.disp[N + id];
-                dd[t][2] = a.disp[2 * N + id];
-                sl_load_epi<MODE>(a, id, N, ee[t]);
-            }
-        }
-    };
-
-    // tile counters of the next tile to fetch (x3 fastest)
-    int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
-    float nd[PT1][3], ne[PT1][NE];
-    issue_box(c1, c2, c3, smem);
-    load_regs(c1, c2, c3, nd, ne);
-    int cur = 0;
-    for (int tile = tbeg; tile < tend; ++tile) {
-        const int t1 = c1, t2 = c2, t3 = c3;
-        if (++c3 == nb3) {
-            c3 = 0;
-            if (++c2 == nb2) { c2 = 0; ++c1; }
-        }
-        float cd[PT1][3], ce[PT1][NE];
-#pragma unroll
-        for (int t = 0; t < PT1; ++t) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) cd[t][c] = nd[t][c];
-#pragma unroll
-            for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
-        }
-        if (tile + 1 < tend) {
-            issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
-            load_regs(c1, c2, c3, nd, ne);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const float *bx = smem + cur * BOX_FLOATS;
-        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
-        const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
-        const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
-        if (i3 < d.n3 && i2 < d.n2) {
+    } else if (tbeg < tend) {
+        auto issue_box = [&](int t1, int t2, int t3, float *buf) {
+            box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
+        };
+        auto load_regs = [&](int t1, int t2, int t3, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
+            const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+            const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
 #pragma unroll
             for (int t = 0; t < PT1; ++t) {
-                if (t1 * PT1 + t < d.n1) {
-                    const float fl0 = floorf(cd[t][0]), fl1 = floorf(cd[t][1]), fl2 = floorf(cd[t][2]);
-                    // stencil origin inside the box; every tap is an immediate offset
-                    const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
-                    const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
-                    float acc;
-                    if (ORDER == 1) {
-                        acc = box_linear(p, cd[t][0] - fl0, cd[t][1] - fl1, cd[t][2] - fl2);
-                    } else {
-                        float w1[4], w2[4], w3[4];
-                        lagrange4(cd[t][0] - fl0, w1);
-                        lagrange4(cd[t][1] - fl1, w2);
-                        lagrange4(cd[t][2] - fl2, w3);
-                        acc = box_cubic(p, w1, w2, w3);
-                    }
-                    sl_epilogue<MODE>(a, id0 + t * plane, acc, ce[t]);
+                if (i3 < d.n3 && i2 < d.n2 && t1 * PT1 + t < d.n1) {
+                    const long long id = id0 + t * plane;
+                    dd[t][0] = a.disp[id];
+                    dd[t][1] = a.disp[N + id];
+                    dd[t][2] = a.disp[2 * N + id];
+                    sl_load_epi<MODE>(a, id, N, ee[t]);
                 }
             }
+        };
+
+        // tile counters of the next tile to fetch (x3 fastest)
+        int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
+        float nd[PT1][3], ne[PT1][NE];
+        issue_box(c1, c2, c3, smem);
+        load_regs(c1, c2, c3, nd, ne);
+        int cur = 0;
+        for (int tile = tbeg; tile < tend; ++tile) {
+            const int t1 = c1, t2 = c2, t3 = c3;
+            if (++c3 == nb3) {
+                c3 = 0;
+                if (++c2 == nb2) { c2 = 0; ++c1; }
+            }
+            float cd[PT1][3], ce[PT1][NE], cx[PT1][NX];
+#pragma unroll
+            for (int t = 0; t < PT1; ++t) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cd[t][c] = nd[t][c];
+#pragma unroll
+                for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
+            }
+            const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+            const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
+            const bool inplane = i3 < d.n3 && i2 < d.n2;
+            if (EarlyCount<MODE>::v > 0 && inplane) {
+#pragma unroll
+                for (int t = 0; t < PT1; ++t)
+                    if (t1 * PT1 + t < d.n1) sl_load_early<MODE>(a, id0 + t * plane, N, cx[t]);
+            }
+            if (tile + 1 < tend) {
+                issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
+                load_regs(c1, c2, c3, nd, ne);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const float *bx = smem + cur * BOX_FLOATS;
+            const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
+            if (inplane) {
+#pragma unroll
+                for (int t = 0; t < PT1; ++t) {
+                    if (t1 * PT1 + t < d.n1) {
+                        const float fl0 = floorf(cd[t][0]), fl1 = floorf(cd[t][1]), fl2 = floorf(cd[t][2]);
+                        // stencil origin inside the box; every tap is an immediate offset
+                        const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
+                        const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
+                        float acc;
+                        if (ORDER == 1) {
+                            acc = box_linear(p, cd[t][0] - fl0, cd[t][1] - fl1, cd[t][2] - fl2);
+                        } else {
+                            float w1[4], w2[4], w3[4];
+                            lagrange4(cd[t][0] - fl0, w1);
+                            lagrange4(cd[t][1] - fl1, w2);
+                            lagrange4(cd[t][2] - fl2, w3);
+                            acc = box_cubic(p, w1, w2, w3);
+                        }
+                        sl_epilogue<MODE>(a, id0 + t * plane, N, acc, ce[t], cx[t], dot);
+                    }
+                }
+            }
+            __syncthreads();
+            cur ^= 1;
         }
-        __syncthreads();
-        cur ^= 1;
+    }
+    if (MODE == SL_ADJDOT) {
+        const double s = block_sum_n<PT3 * PT2>(dot.value(), ty * PT3 + tx);
+        if (tx == 0 && ty == 0) a.partial[blockIdx.x] = s;
     }
 }
 
@@ -718,36 +781,20 @@ __global__ void k_incstate_init(const float *__restrict__ vt, const TG *__restri
     }
 }
 
-template <typename TB, typename TO>
-__global__ void k_sub(const float *__restrict__ a, const TB *__restrict__ b,
-                      TO *__restrict__ out, long long N) {
-    for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT)
-        stf(out + i, a[i] - ldf(b + i));
-}
-
-// body force by the trapezoidal rule: out_d = add_d + dt sum_j w_j l^j dm^j/dx_d
-template <typename TL, typename TG>
-__global__ void k_bodyforce(const TL *__restrict__ lh, const TG *__restrict__ gmh,
-                            const float *__restrict__ add, float *__restrict__ out, long long N,
-                            int nt, float dt) {
+// the adjoint's final condition (Eq. 3.2) and the first term of the body
+// force, with the gradient started at beta A v:
+//   l = m1 - m(1),  g = Av + w l grad m(1)   (w = dt/2, trapezoid end point)
+template <typename TG>
+__global__ void k_adjfinal_acc(const float *__restrict__ m1, const float *__restrict__ m, float *__restrict__ l,
+                               __half *__restrict__ l_h, const TG *__restrict__ gm, const float *__restrict__ Av,
+                               float *__restrict__ g, float w, long long N) {
     for (long long i = blockIdx.x * (long long)PT + threadIdx.x; i < N; i += (long long)gridDim.x * PT) {
-        float b1 = 0.f, b2 = 0.f, b3 = 0.f;
-        for (int j = 0; j <= nt; ++j) {
-            const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
-            const float l = w * ldf(lh + (long long)j * N + i);
-            const TG *g = gmh + (long long)j * 3 * N;
-            b1 = fmaf(l, ldf(g + i), b1);
-            b2 = fmaf(l, ldf(g + N + i), b2);
-            b3 = fmaf(l, ldf(g + 2 * N + i), b3);
-        }
-        if (add) {
-            b1 += add[i];
-            b2 += add[N + i];
-            b3 += add[2 * N + i];
-        }
-        out[i] = b1;
-        out[N + i] = b2;
-        out[2 * N + i] = b3;
+        const float li = m1[i] - m[i];
+        l[i] = li;
+        if (l_h) l_h[i] = __float2half_rn(li);
+        const float x = w * li;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g[k * N + i] = fmaf(x, ldf(gm + k * N + i), Av[k * N + i]);
     }
 }
 
@@ -852,24 +899,57 @@ void incstate_step(const Dims &d, float dt, const float *src, const float *dispm
 }
 template <typename TG>
 void incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
-                   const float *vt, const TG *gm_last, float *lt_last, float *mt_out, cudaStream_t st,
-                   Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_INCSTATE, st, (32.0 + 3 * sizeof(TG) + (mt_out ? 4 : 0)) * d.N);
+                   const float *vt, const TG *gm_last, float *lt_last, float *mt_out, float *b_out,
+                   cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_INCSTATE, st, (32.0 + 3 * sizeof(TG) + (mt_out ? 4 : 0) + (b_out ? 12 : 0)) * d.N);
     SlArgsT<float, TG> a{src, dispm, lt_last, nullptr, vt, gm_last, dt};
     a.dst2 = mt_out;
+    a.acc = b_out;
     launch_pipe<SL_INCLAST>(d, a, range_m, st);
+}
+
+template <typename TG>
+void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+                 float *dst, const TG *gm, float *b, float w, const float *p, double *partial,
+                 const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
+                 __half *dst_h) {
+    ProfScope ps(prof, kclass, st, (48.0 + 3 * sizeof(TG) + (p ? 12 : 0) + (dst_h ? 2 : 0)) * d.N, p ? 2 : 1);
+    SlArgsT<float, TG> a{src, dispp, dst, cfac, nullptr, gm, 0.f, dst_h};
+    a.acc = b;
+    a.w = w;
+    if (p) {
+        a.pv = p;
+        a.partial = partial;
+        launch_pipe<SL_ADJDOT>(d, a, range_p, st);
+        launch_finalize(partial, pipe_blocks(d, SlOcc<SL_ADJDOT>::v), dot_add, dot_out, st);
+    } else {
+        launch_pipe<SL_ADJACC>(d, a, range_p, st);
+    }
 }
 }  // namespace
 
 void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
-                          const float *vt, const float *gm_last, float *lt_last, float *mt_out,
+                          const float *vt, const float *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof) {
-    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, st, prof);
+    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, b_out, st, prof);
 }
 void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
-                          const float *vt, const __half *gm_last, float *lt_last, float *mt_out,
+                          const float *vt, const __half *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof) {
-    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, st, prof);
+    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, b_out, st, prof);
+}
+
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+                        float *dst, const float *gm, float *b, float w, const float *p, double *partial,
+                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
+                        __half *dst_h) {
+    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, p, partial, dot_add, dot_out, st, prof, kclass, dst_h);
+}
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+                        float *dst, const __half *gm, float *b, float w, const float *p, double *partial,
+                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
+                        __half *dst_h) {
+    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, p, partial, dot_add, dot_out, st, prof, kclass, dst_h);
 }
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
@@ -894,10 +974,22 @@ void launch_incstate_step(const Dims &d, float dt, const float *src, const float
     incstate_step(d, dt, src, dispm, range_m, vt, gm_next, dst, st, prof);
 }
 
-void launch_sub(const Dims &d, const float *a, const float *b, float *out, cudaStream_t st,
-                Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_VECTOR, st, 12.0 * d.N);
-    k_sub<<<grid1(d.N), PT, 0, st>>>(a, b, out, d.N);
+namespace {
+template <typename TG>
+void adjfinal_acc(const Dims &d, const float *m1, const float *m, float *l, __half *l_h, const TG *gm,
+                  const float *Av, float *g, float w, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, (36.0 + 3 * sizeof(TG) + (l_h ? 2 : 0)) * d.N);
+    k_adjfinal_acc<<<grid1(d.N), PT, 0, st>>>(m1, m, l, l_h, gm, Av, g, w, d.N);
+}
+}  // namespace
+
+void launch_adjfinal_acc(const Dims &d, const float *m1, const float *m, float *l, __half *l_h, const float *gm,
+                         const float *Av, float *g, float w, cudaStream_t st, Profiler *prof) {
+    adjfinal_acc(d, m1, m, l, l_h, gm, Av, g, w, st, prof);
+}
+void launch_adjfinal_acc(const Dims &d, const float *m1, const float *m, float *l, __half *l_h, const __half *gm,
+                         const float *Av, float *g, float w, cudaStream_t st, Profiler *prof) {
+    adjfinal_acc(d, m1, m, l, l_h, gm, Av, g, w, st, prof);
 }
 
 void launch_bodyforce_acc(const Dims &d, float *b, const float *l, const float *gm, float w,
@@ -911,29 +1003,6 @@ void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float 
                           Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)d.N * (gm_final ? 16 : 12));
     k_adjoint_final<<<grid1(d.N), PT, 0, st>>>(l, m1, m, gm_final, gmis, inv_h3, d.N);
-}
-
-namespace {
-template <typename TL, typename TG>
-void bodyforce(const Dims &d, int nt, const TL *lhist, const TG *gmhist, const float *add, float *out,
-               cudaStream_t st, Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st,
-                 (double)d.N * ((sizeof(TL) + 3.0 * sizeof(TG)) * (nt + 1) + 12 + (add ? 12 : 0)));
-    k_bodyforce<<<grid1(d.N), PT, 0, st>>>(lhist, gmhist, add, out, d.N, nt, 1.f / nt);
-}
-}  // namespace
-
-void launch_bodyforce(const Dims &d, int nt, const float *lhist, const float *gmhist,
-                      const float *add, float *out, cudaStream_t st, Profiler *prof) {
-    bodyforce(d, nt, lhist, gmhist, add, out, st, prof);
-}
-void launch_bodyforce(const Dims &d, int nt, const float *lhist, const __half *gmhist,
-                      const float *add, float *out, cudaStream_t st, Profiler *prof) {
-    bodyforce(d, nt, lhist, gmhist, add, out, st, prof);
-}
-void launch_bodyforce(const Dims &d, int nt, const __half *lhist, const __half *gmhist,
-                      const float *add, float *out, cudaStream_t st, Profiler *prof) {
-    bodyforce(d, nt, lhist, gmhist, add, out, st, prof);
 }
 
 }  // namespace claire

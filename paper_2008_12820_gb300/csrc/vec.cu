@@ -3,17 +3,16 @@
 //
 // Reductions: FP64 is slow on this part, so a thread does not widen every
 // element.  It accumulates its grid-stride range with error-free
-// transformations in FP32 (the compensated dot product of Ogita, Rump and
-// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005: TwoProduct
-// by fma, TwoSum by Knuth), which is as accurate as summing in twice the
-// working precision; the pair (sum, compensation) is widened to FP64 once, a
-// block reduces in FP64 by warp shuffles, block partials go to a fixed-size
-// array, and one block sums them in a fixed order: deterministic for a given
-// grid.
+// transformations in FP32 (Acc2, reduce.cuh), as accurate as summing in twice
+// the working precision; the pair (sum, compensation) is widened to FP64
+// once, a block reduces in FP64 by warp shuffles, block partials go to a
+// fixed-size array, and one block sums them in a fixed order: deterministic
+// for a given grid.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "claire_internal.cuh"
+#include "reduce.cuh"
 
 namespace claire {
 
@@ -24,48 +23,8 @@ __device__ __forceinline__ float ldv(const __half *p) { return __half2float(*p);
 
 constexpr int RT = 256;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// block sum of v; valid in thread 0
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double ws[RT / 32];
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) ws[w] = v;
-    __syncthreads();
-    v = 0.0;
-    if (w == 0) {
-        v = lane < RT / 32 ? ws[lane] : 0.0;
-        v = warp_sum(v);
-    }
-    return v;
-}
-
-// compensated accumulator: the exact value of the sum so far is s + c up to
-// O(eps^2) relative terms.  The _rn intrinsics keep the compiler from fusing
-// a product into a neighbouring add, which would break the error terms.
-struct Acc2 {
-    float s = 0.f, c = 0.f;
-    // add the exact product x*y
-    __device__ __forceinline__ void add_prod(float x, float y) {
-        const float p = __fmul_rn(x, y);
-        const float ep = fmaf(x, y, -p);  // TwoProduct error
-        add(p, ep);
-    }
-    // add p + ep (ep a small correction)
-    __device__ __forceinline__ void add(float p, float ep) {
-        const float t = __fadd_rn(s, p);
-        const float z = __fsub_rn(t, s);
-        const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // TwoSum error
-        s = t;
-        c = __fadd_rn(c, __fadd_rn(es, ep));
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
+// block sum of v (1D blocks of RT threads); valid in thread 0
+__device__ __forceinline__ double block_sum(double v) { return block_sum_n<RT>(v, threadIdx.x); }
 
 // MODE 0: sum a*b;  MODE 1: sum (a-b)^2
 template <int MODE, typename TA = float>
@@ -91,11 +50,11 @@ __global__ void __launch_bounds__(RT) k_reduce2(const TA *__restrict__ a, const 
 }
 
 __global__ void __launch_bounds__(RT) k_finalize(const double *__restrict__ partial, int nb,
-                                                 double *__restrict__ out) {
+                                                 double *__restrict__ out, const double *__restrict__ add = nullptr) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nb; i += RT) s += partial[i];
     s = block_sum(s);
-    if (threadIdx.x == 0) out[0] = s;
+    if (threadIdx.x == 0) out[0] = add ? s + add[0] : s;
 }
 
 // x += alpha p ; r -= alpha q ; partial sums of r.r
@@ -179,20 +138,23 @@ __global__ void __launch_bounds__(RT) k_stats(const float *__restrict__ r, long 
 }
 
 // PCG update with the regularization term carried along (x, A x, r):
-// x += a p; Ax += a Ap; r -= a q; statistics of the new r
+// x += a p; Ax += a Ap; r -= a q; statistics of the new r.  q_adds_Ap: q
+// holds only the body force of H p, and H p = Ap + q is formed here.
 __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float *__restrict__ Ax,
                                                    float *__restrict__ r, const float *__restrict__ p,
                                                    const float *__restrict__ Ap,
                                                    const float *__restrict__ q, float alpha,
-                                                   long long N, double *__restrict__ partial) {
+                                                   long long N, double *__restrict__ partial, int q_adds_Ap) {
     Acc2 rr, sc[3];
     const long long stride = (long long)gridDim.x * RT;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
             x[i] = fmaf(alpha, p[i], x[i]);
-            if (Ax) Ax[i] = fmaf(alpha, Ap[i], Ax[i]);
-            const float ri = fmaf(-alpha, q[i], r[i]);
+            const float Api = (Ax || q_adds_Ap) ? Ap[i] : 0.f;
+            if (Ax) Ax[i] = fmaf(alpha, Api, Ax[i]);
+            const float qi = q_adds_Ap ? q[i] + Api : q[i];
+            const float ri = fmaf(-alpha, qi, r[i]);
             r[i] = ri;
             rr.add_prod(ri, ri);
             sc[c].add(ri, 0.f);
@@ -247,8 +209,10 @@ __global__ void __launch_bounds__(RT) k_pcg_dir_u0(float *__restrict__ p, float 
                                                    const float *__restrict__ z, const float *__restrict__ r,
                                                    const double *__restrict__ rsum, const float *__restrict__ Az,
                                                    float b, long long N, int init, const TG *__restrict__ gm0,
-                                                   float *__restrict__ u0, float hdt) {
+                                                   float *__restrict__ u0, float hdt,
+                                                   double *__restrict__ partial) {
     const long long stride = (long long)gridDim.x * RT;
+    Acc2 pap;
     float mean[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mean[c] = Az ? 0.f : (float)(rsum[c] / (double)N);
@@ -258,17 +222,24 @@ __global__ void __launch_bounds__(RT) k_pcg_dir_u0(float *__restrict__ p, float 
         for (int c = 0; c < 3; ++c) {
             const long long k = c * N + i;
             const float ar = Az ? Az[k] : r[k] - mean[c];
+            float apc;
             if (init) {
                 pc[c] = z[k];
-                Ap[k] = ar;
+                apc = ar;
             } else {
                 pc[c] = fmaf(b, p[k], z[k]);
-                Ap[k] = fmaf(b, Ap[k], ar);
+                apc = fmaf(b, Ap[k], ar);
             }
+            Ap[k] = apc;
             p[k] = pc[c];
+            if (partial) pap.add_prod(pc[c], apc);
         }
         const float f = -(pc[0] * ldv(gm0 + i) + pc[1] * ldv(gm0 + N + i) + pc[2] * ldv(gm0 + 2 * N + i));
         u0[i] = hdt * f;
+    }
+    if (partial) {
+        const double s = block_sum(pap.value());
+        if (threadIdx.x == 0) partial[blockIdx.x] = s;
     }
 }
 
@@ -289,39 +260,6 @@ __global__ void __launch_bounds__(RT) k_h0_apply(float *__restrict__ q, const fl
 // Body force of the Hessian matvec plus the carried beta*A p, and p . q:
 //   q_d = Ap_d + dt sum_j w_j l^j d_d m^j,   partial sums of sum_d p_d q_d
 // (fuses the PCG curvature product into the pass that writes q)
-template <typename TG>
-__global__ void __launch_bounds__(RT) k_bodyforce_dot(const float *__restrict__ lh,
-                                                      const TG *__restrict__ gmh,
-                                                      const float *__restrict__ Ap,
-                                                      const float *__restrict__ p,
-                                                      float *__restrict__ q, long long N, int nt,
-                                                      float dt, double *__restrict__ partial) {
-    Acc2 acc;
-    const long long stride = (long long)gridDim.x * RT;
-    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
-        float b1 = 0.f, b2 = 0.f, b3 = 0.f;
-        for (int j = 0; j <= nt; ++j) {
-            const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
-            const float l = w * lh[(long long)j * N + i];
-            const TG *g = gmh + (long long)j * 3 * N;
-            b1 = fmaf(l, ldv(g + i), b1);
-            b2 = fmaf(l, ldv(g + N + i), b2);
-            b3 = fmaf(l, ldv(g + 2 * N + i), b3);
-        }
-        b1 += Ap[i];
-        b2 += Ap[N + i];
-        b3 += Ap[2 * N + i];
-        q[i] = b1;
-        q[N + i] = b2;
-        q[2 * N + i] = b3;
-        acc.add_prod(p[i], b1);
-        acc.add_prod(p[N + i], b2);
-        acc.add_prod(p[2 * N + i], b3);
-    }
-    const double s = block_sum(acc.value());
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
 __global__ void k_f2h(const float *__restrict__ in, __half *__restrict__ out, long long n) {
     for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT)
         out[i] = __float2half_rn(in[i]);
@@ -337,6 +275,10 @@ inline int blocks_for(long long n) {
 }
 
 }  // namespace
+
+void launch_finalize(const double *partial, int nb, const double *add, double *dev_out, cudaStream_t st) {
+    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out, add);
+}
 
 void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
                 cudaStream_t st, Profiler *prof) {
@@ -401,10 +343,10 @@ void launch_stats(const float *r, long long N, double *partial, double *dev_out,
 
 void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
-                       cudaStream_t st, Profiler *prof) {
+                       cudaStream_t st, Profiler *prof, bool q_adds_Ap) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (Ax ? 36 : 24), 2);
     const int nb = blocks_for(N);
-    k_pcg_update<<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial);
+    k_pcg_update<<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0);
     k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
@@ -417,42 +359,25 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
 
 template <typename TG>
 static void pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
-                       float b, long long N, bool init, const TG *gm0, float *u0, float hdt, cudaStream_t st,
-                       Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)N * (3.0 * (init ? 16 : 24) + 3 * sizeof(TG) + 4));
-    k_pcg_dir_u0<<<blocks_for(N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt);
-}
-
-void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
-                       float b, long long N, bool init, const float *gm0, float *u0, float hdt, cudaStream_t st,
-                       Profiler *prof) {
-    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, st, prof);
-}
-void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
-                       float b, long long N, bool init, const __half *gm0, float *u0, float hdt, cudaStream_t st,
-                       Profiler *prof) {
-    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, st, prof);
-}
-
-template <typename TG>
-static void bodyforce_dot(long long N, int nt, const float *lhist, const TG *gmhist, const float *Ap,
-                          const float *p, float *q, double *partial, double *dev_out, cudaStream_t st,
-                          Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_BODYFORCE, st, (double)N * ((4.0 + 3 * sizeof(TG)) * (nt + 1) + 36), 2);
+                       float b, long long N, bool init, const TG *gm0, float *u0, float hdt, double *partial,
+                       double *pap_out, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)N * (3.0 * (init ? 16 : 24) + 3 * sizeof(TG) + 4),
+                 pap_out ? 2 : 1);
     const int nb = blocks_for(N);
-    k_bodyforce_dot<<<nb, RT, 0, st>>>(lhist, gmhist, Ap, p, q, N, nt, 1.f / nt, partial);
-    k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
+    k_pcg_dir_u0<<<nb, RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt,
+                                    pap_out ? partial : nullptr);
+    if (pap_out) k_finalize<<<1, RT, 0, st>>>(partial, nb, pap_out);
 }
 
-void launch_bodyforce_dot(long long N, int nt, const float *lhist, const float *gmhist,
-                          const float *Ap, const float *p, float *q, double *partial,
-                          double *dev_out, cudaStream_t st, Profiler *prof) {
-    bodyforce_dot(N, nt, lhist, gmhist, Ap, p, q, partial, dev_out, st, prof);
+void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const float *gm0, float *u0, float hdt, double *partial,
+                       double *pap_out, cudaStream_t st, Profiler *prof) {
+    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, partial, pap_out, st, prof);
 }
-void launch_bodyforce_dot(long long N, int nt, const float *lhist, const __half *gmhist,
-                          const float *Ap, const float *p, float *q, double *partial,
-                          double *dev_out, cudaStream_t st, Profiler *prof) {
-    bodyforce_dot(N, nt, lhist, gmhist, Ap, p, q, partial, dev_out, st, prof);
+void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
+                       float b, long long N, bool init, const __half *gm0, float *u0, float hdt, double *partial,
+                       double *pap_out, cudaStream_t st, Profiler *prof) {
+    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, partial, pap_out, st, prof);
 }
 
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
