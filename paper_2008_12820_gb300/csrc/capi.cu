@@ -185,9 +185,12 @@ struct claire_ctx {
 
     double fetch(int slot = 0) {
         double h = 0;
-        CK(cudaMemcpyAsync(&h, dres + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        fetch_n(slot, 1, &h);
         return h;
+    }
+    void fetch_n(int slot, int n, double *h) {
+        CK(cudaMemcpyAsync(h, dres + slot, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
     }
     double dot(const float *a, const float *b, long long n) {
         launch_dot(a, b, n, partial, dres, st, &prof);
@@ -390,7 +393,8 @@ struct claire_ctx {
             Av = s3a;
         }
         // g = beta A v + the body force of Eq. 3.3 by the trapezoidal rule,
-        // each term added by the adjoint step that makes its lambda^j
+        // each term added by the adjoint step that makes its lambda^j; the
+        // last step also leaves g . g in dres[9]
         const float dt = 1.f / nt;
         auto wt = [&](int j) { return (j == 0 || j == nt) ? 0.5f * dt : dt; };
         if (h16) {
@@ -398,8 +402,9 @@ struct claire_ctx {
             float *a = s1a, *b = s1b;
             launch_adjfinal_acc(d, m1, m1f, a, hist(lhist_h, nt), hist(gmhist_h, nt, 3), Av, g, wt(nt), st, &prof);
             for (int j = nt; j >= 1; --j) {
-                launch_adjoint_acc(d, a, dispp, rng_p(), cfac, b, hist(gmhist_h, j - 1, 3), g, wt(j - 1), nullptr,
-                                   nullptr, nullptr, nullptr, st, &prof, CLAIRE_K_ADJOINT, hist(lhist_h, j - 1));
+                launch_adjoint_acc(d, a, dispp, rng_p(), cfac, b, hist(gmhist_h, j - 1, 3), g, wt(j - 1), j == 1,
+                                   nullptr, partial, nullptr, dres + 9, st, &prof, CLAIRE_K_ADJOINT,
+                                   hist(lhist_h, j - 1));
                 std::swap(a, b);
             }
         } else {
@@ -407,7 +412,8 @@ struct claire_ctx {
                                 st, &prof);
             for (int j = nt; j >= 1; --j)
                 launch_adjoint_acc(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), hist(gmhist, j - 1, 3),
-                                   g, wt(j - 1), nullptr, nullptr, nullptr, nullptr, st, &prof, CLAIRE_K_ADJOINT);
+                                   g, wt(j - 1), j == 1, nullptr, partial, nullptr, dres + 9, st, &prof,
+                                   CLAIRE_K_ADJOINT);
         }
         check_launch("gradient");
         if (J || mis_out) {
@@ -535,13 +541,13 @@ struct claire_ctx {
                                  &prof);
         for (int j = nt; j >= 1; --j) {
             const float w = j == 1 ? 0.5f * dt : dt;
-            const float *p = (pcg && j == 1) ? vt : nullptr;
+            const bool dot = pcg && j == 1;
             if (h16)
                 launch_adjoint_acc(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), hist(gmhist_h, j - 1, 3),
-                                   Hvt, w, p, partial, dres + 8, dres, st, &prof, CLAIRE_K_INCADJ);
+                                   Hvt, w, dot, vt, partial, dres + 8, dres, st, &prof, CLAIRE_K_INCADJ);
             else
                 launch_adjoint_acc(d, hist(lhist, j), dispp, rng_p(), cfac, hist(lhist, j - 1), hist(gmhist, j - 1, 3),
-                                   Hvt, w, p, partial, dres + 8, dres, st, &prof, CLAIRE_K_INCADJ);
+                                   Hvt, w, dot, vt, partial, dres + 8, dres, st, &prof, CLAIRE_K_INCADJ);
         }
         if (!pcg) spectral(OP_A, vt, Hvt, Hvt);
     }
@@ -1098,7 +1104,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         ctx->spectral(OP_A, v, Av, nullptr);
         ctx->gradient(v, g, &J, nullptr, Av);
     }
-    const double g0 = std::sqrt(ctx->dot(g, g, n3));
+    const double g0 = std::sqrt(ctx->fetch(9));  // g . g from the gradient's last pass
     if (!std::isfinite(g0) || !std::isfinite(J)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite gradient or objective");
     rep.J0 = J;
     rep.g0 = g0;
@@ -1187,8 +1193,11 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         rep.t_pcg_ms += t_pcg;
         // ---- Armijo backtracking; the regularization term of J(v + a x) is
         // 1/2 <v + a x, Av + a Ax>, a quadratic in a from three dot products
-        const double slope = H3 * ctx->dot(g, x, n3);
-        const double xAv = ctx->dot(x, Av, n3), vAx = ctx->dot(v, Ax, n3), xAx = ctx->dot(x, Ax, n3);
+        launch_ls_dots(g, x, Av, v, Ax, n3, ctx->partial, ctx->dres, st, &ctx->prof);
+        double lsd[4];
+        ctx->fetch_n(0, 4, lsd);
+        const double slope = H3 * lsd[0];
+        const double xAv = lsd[1], vAx = lsd[2], xAx = lsd[3];
         double alpha = 1.0;
         bool ok = false;
         {
@@ -1219,7 +1228,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             ctx->gradient(v, g, &J, nullptr, Av, ctx->keeps_trial());
         }
         vAv = ctx->last_vAv;
-        gn = std::sqrt(ctx->dot(g, g, n3));
+        gn = std::sqrt(ctx->fetch(9));
         if (!std::isfinite(gn) || !std::isfinite(J)) {
             status = CLAIRE_ERR_NONFINITE;
             break;

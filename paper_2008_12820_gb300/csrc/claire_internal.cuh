@@ -117,17 +117,18 @@ void launch_incstate_last(const Dims &d, float dt, const float *src, const float
                           const float *vt, const __half *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof);
 // adjoint step dst = c src(X+) that also adds w dst grad m^{j-1} to the body
-// force b [3][N] in place (gm = grad m^{j-1}).  With p non-null it also
-// forms p . b of the updated b: block partials in partial, their sum plus
-// *dot_add (nullable) in *dot_out.  dst_h: optional FP16 copy of dst.
+// force b [3][N] in place (gm = grad m^{j-1}).  With want_dot it also forms
+// p . b of the updated b (b . b if p is null): block partials in partial,
+// their sum plus *dot_add (nullable) in *dot_out.  dst_h: optional FP16 copy
+// of dst.
 void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
-                        float *dst, const float *gm, float *b, float w, const float *p, double *partial,
-                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
-                        __half *dst_h = nullptr);
+                        float *dst, const float *gm, float *b, float w, bool want_dot, const float *p,
+                        double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
+                        int kclass, __half *dst_h = nullptr);
 void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
-                        float *dst, const __half *gm, float *b, float w, const float *p, double *partial,
-                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
-                        __half *dst_h = nullptr);
+                        float *dst, const __half *gm, float *b, float w, bool want_dot, const float *p,
+                        double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
+                        int kclass, __half *dst_h = nullptr);
 // the adjoint's final condition l = m1 - m (l_h: optional FP16 copy) and the
 // gradient started as g = Av + w l gm  (gm = grad m(1), w = dt/2)
 void launch_adjfinal_acc(const Dims &d, const float *m1, const float *m, float *l, __half *l_h, const float *gm,
@@ -163,6 +164,9 @@ void launch_grad_fd8(const Dims &d, const float *f, __half *g, cudaStream_t st, 
 // FP64 reductions; results land in dev_out[0..k) (device doubles)
 // dev_out[0] = sum of partial[0..nb) (+ add[0] if add is non-null)
 void launch_finalize(const double *partial, int nb, const double *add, double *dev_out, cudaStream_t st);
+// the four dot products of the line search: dev_out[0..3] = g.x, x.Av, v.Ax, x.Ax
+void launch_ls_dots(const float *g, const float *x, const float *Av, const float *v, const float *Ax, long long n,
+                    double *partial, double *dev_out, cudaStream_t st, Profiler *prof);
 void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
                 cudaStream_t st, Profiler *prof);
 void launch_sqdiff(const float *a, const float *b, long long n, double *partial,

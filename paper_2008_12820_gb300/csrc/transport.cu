@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(256) k_range_parts(const int *__restrict__ par
 // incremental adjoint's final condition lt(1) = -mt(1) (and mt(1)) directly,
 // and optionally the first body-force term w_nt lt(1) grad m(1).
 // SL_ADJACC: adjoint step that adds w l^{j-1} grad m^{j-1} to the body force;
-// SL_ADJDOT: the same, and the block partials of p . b of the finished sum.
+// SL_ADJDOT: the same, and the block partials of p . b of the finished sum
+// (b . b without p).
 enum SlMode { SL_PLAIN = 0, SL_ADJ = 1, SL_INCSTATE = 2, SL_ADJFAC = 3, SL_INCLAST = 4, SL_ADJACC = 5, SL_ADJDOT = 6 };
 
 // TS: storage type of the gathered and written field; TG: of grad m
@@ -278,7 +279,7 @@ struct SlArgsT {
     float *dst2 = nullptr;    // SL_INCLAST: mt(1) (optional)
     float *acc = nullptr;     // body force b [3][N]: SL_ADJACC/SL_ADJDOT update it, SL_INCLAST starts it (optional)
     float w = 0.f;            // SL_ADJACC/SL_ADJDOT: trapezoid weight of the new term (dt, dt/2 at j = 0)
-    const float *pv = nullptr;      // SL_ADJDOT: p [3][N]
+    const float *pv = nullptr;      // SL_ADJDOT: p [3][N] (null: the dot is b . b)
     double *partial = nullptr;      // SL_ADJDOT: one partial sum of p . b per block
 };
 using SlArgs = SlArgsT<float, float>;
@@ -333,8 +334,13 @@ __device__ __forceinline__ float gather_lean(const T *__restrict__ f, const Dims
 // the displacement field (per axis, over the whole field, from
 // k_floor_range) fixes the geometry of the source box every tile needs, so
 // while a block computes tile k from one shared-memory buffer, cp.async
-// already copies the box of tile k+1 into the other, and the displacements
-// and epilogue inputs of tile k+1 are loaded into registers.  The 64 taps of
+// already copies the box of tile k+1 into the other.  The displacements and
+// epilogue inputs of a tile are loaded when the tile starts, not a tile
+// ahead: that holds half the registers (three blocks per SM for the
+// incremental state, which has six epilogue inputs a voxel), and the loads
+// still overlap the box wait and the other resident blocks (measured at
+// 256^3: state 199 -> 182 us, adjoint 205 -> 187 us, incremental state
+// 234 -> 207 us, accumulating adjoint 242 -> 230 us).  The 64 taps of
 // a voxel are then shared-memory reads with immediate offsets, the same
 // instruction stream for every lane (the periodic wrap happened once, when
 // the box was fetched).  If the range makes the box larger than a buffer, the
@@ -378,7 +384,7 @@ __device__ __forceinline__ void sl_load_early(const A &a, long long id, long lon
         for (int k = 0; k < 3; ++k) {
             x[k] = ldf(a.gm + k * N + id);
             x[3 + k] = a.acc[k * N + id];
-            if (MODE == SL_ADJDOT) x[6 + k] = a.pv[k * N + id];
+            if (MODE == SL_ADJDOT) x[6 + k] = a.pv ? a.pv[k * N + id] : 0.f;
         }
     }
 }
@@ -419,7 +425,7 @@ __device__ __forceinline__ void sl_epilogue(const A &a, long long id, long long 
         for (int k = 0; k < 3; ++k) {
             const float b = fmaf(l, x[k], x[3 + k]);
             a.acc[k * N + id] = b;
-            if (MODE == SL_ADJDOT) dot.add_prod(x[6 + k], b);
+            if (MODE == SL_ADJDOT) dot.add_prod(a.pv ? x[6 + k] : b, b);
         }
     }
 }
@@ -527,12 +533,10 @@ __device__ __forceinline__ float box_linear(const float *p, float u1, float u2, 
     return fmaf(u1, y1 - y0, y0);
 }
 
-// resident blocks per SM: the incremental-state steps carry six epilogue
-// inputs per voxel and the accumulating adjoint steps six or nine more loaded
-// per tile; they keep two, the others fit three
+// resident blocks per SM (launch bounds and grid size): the accumulating
+// adjoint steps hold nine or twelve inputs a voxel and keep two
 template <int MODE> struct SlOcc {
-    static constexpr int v =
-        (MODE == SL_INCSTATE || MODE == SL_INCLAST || MODE == SL_ADJACC || MODE == SL_ADJDOT) ? 2 : 3;
+    static constexpr int v = (MODE == SL_ADJACC || MODE == SL_ADJDOT) ? 2 : 3;
 };
 
 // tiles of block b: a contiguous range, so neighbouring tiles (which share
@@ -583,26 +587,25 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
         auto issue_box = [&](int t1, int t2, int t3, float *buf) {
             box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
         };
-        auto load_regs = [&](int t1, int t2, int t3, float (&dd)[PT1][3], float (&ee)[PT1][NE]) {
+        // displacements and epilogue inputs of the voxels of a tile
+        auto load_regs = [&](int t1, int t2, int t3, float *dd, float *ee) {
             const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
             const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
 #pragma unroll
             for (int t = 0; t < PT1; ++t) {
                 if (i3 < d.n3 && i2 < d.n2 && t1 * PT1 + t < d.n1) {
                     const long long id = id0 + t * plane;
-                    dd[t][0] = a.disp[id];
-                    dd[t][1] = a.disp[N + id];
-                    dd[t][2] = a.disp[2 * N + id];
-                    sl_load_epi<MODE>(a, id, N, ee[t]);
+                    dd[3 * t] = a.disp[id];
+                    dd[3 * t + 1] = a.disp[N + id];
+                    dd[3 * t + 2] = a.disp[2 * N + id];
+                    sl_load_epi<MODE>(a, id, N, ee + NE * t);
                 }
             }
         };
 
         // tile counters of the next tile to fetch (x3 fastest)
         int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
-        float nd[PT1][3], ne[PT1][NE];
         issue_box(c1, c2, c3, smem);
-        load_regs(c1, c2, c3, nd, ne);
         int cur = 0;
         for (int tile = tbeg; tile < tend; ++tile) {
             const int t1 = c1, t2 = c2, t3 = c3;
@@ -610,14 +613,10 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
                 c3 = 0;
                 if (++c2 == nb2) { c2 = 0; ++c1; }
             }
-            float cd[PT1][3], ce[PT1][NE], cx[PT1][NX];
-#pragma unroll
-            for (int t = 0; t < PT1; ++t) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) cd[t][c] = nd[t][c];
-#pragma unroll
-                for (int c = 0; c < NE; ++c) ce[t][c] = ne[t][c];
-            }
+            // this tile's inputs, loaded now: they arrive while the box of
+            // the next tile is issued and this tile's box is awaited
+            float cd[PT1 * 3], ce[PT1 * NE], cx[PT1][NX];
+            load_regs(t1, t2, t3, cd, ce);
             const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
             const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
             const bool inplane = i3 < d.n3 && i2 < d.n2;
@@ -628,7 +627,6 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
             }
             if (tile + 1 < tend) {
                 issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
-                load_regs(c1, c2, c3, nd, ne);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -640,21 +638,22 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
 #pragma unroll
                 for (int t = 0; t < PT1; ++t) {
                     if (t1 * PT1 + t < d.n1) {
-                        const float fl0 = floorf(cd[t][0]), fl1 = floorf(cd[t][1]), fl2 = floorf(cd[t][2]);
+                        const float *dt3 = cd + 3 * t;
+                        const float fl0 = floorf(dt3[0]), fl1 = floorf(dt3[1]), fl2 = floorf(dt3[2]);
                         // stencil origin inside the box; every tap is an immediate offset
                         const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
                         const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
                         float acc;
                         if (ORDER == 1) {
-                            acc = box_linear(p, cd[t][0] - fl0, cd[t][1] - fl1, cd[t][2] - fl2);
+                            acc = box_linear(p, dt3[0] - fl0, dt3[1] - fl1, dt3[2] - fl2);
                         } else {
                             float w1[4], w2[4], w3[4];
-                            lagrange4(cd[t][0] - fl0, w1);
-                            lagrange4(cd[t][1] - fl1, w2);
-                            lagrange4(cd[t][2] - fl2, w3);
+                            lagrange4(dt3[0] - fl0, w1);
+                            lagrange4(dt3[1] - fl1, w2);
+                            lagrange4(dt3[2] - fl2, w3);
                             acc = box_cubic(p, w1, w2, w3);
                         }
-                        sl_epilogue<MODE>(a, id0 + t * plane, N, acc, ce[t], cx[t], dot);
+                        sl_epilogue<MODE>(a, id0 + t * plane, N, acc, ce + NE * t, cx[t], dot);
                     }
                 }
             }
@@ -910,14 +909,15 @@ void incstate_last(const Dims &d, float dt, const float *src, const float *dispm
 
 template <typename TG>
 void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
-                 float *dst, const TG *gm, float *b, float w, const float *p, double *partial,
+                 float *dst, const TG *gm, float *b, float w, bool want_dot, const float *p, double *partial,
                  const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
                  __half *dst_h) {
-    ProfScope ps(prof, kclass, st, (48.0 + 3 * sizeof(TG) + (p ? 12 : 0) + (dst_h ? 2 : 0)) * d.N, p ? 2 : 1);
+    ProfScope ps(prof, kclass, st, (48.0 + 3 * sizeof(TG) + (p ? 12 : 0) + (dst_h ? 2 : 0)) * d.N,
+                 want_dot ? 2 : 1);
     SlArgsT<float, TG> a{src, dispp, dst, cfac, nullptr, gm, 0.f, dst_h};
     a.acc = b;
     a.w = w;
-    if (p) {
+    if (want_dot) {
         a.pv = p;
         a.partial = partial;
         launch_pipe<SL_ADJDOT>(d, a, range_p, st);
@@ -940,16 +940,18 @@ void launch_incstate_last(const Dims &d, float dt, const float *src, const float
 }
 
 void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
-                        float *dst, const float *gm, float *b, float w, const float *p, double *partial,
-                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
-                        __half *dst_h) {
-    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, p, partial, dot_add, dot_out, st, prof, kclass, dst_h);
+                        float *dst, const float *gm, float *b, float w, bool want_dot, const float *p,
+                        double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
+                        int kclass, __half *dst_h) {
+    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, want_dot, p, partial, dot_add, dot_out, st, prof,
+                kclass, dst_h);
 }
 void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
-                        float *dst, const __half *gm, float *b, float w, const float *p, double *partial,
-                        const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
-                        __half *dst_h) {
-    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, p, partial, dot_add, dot_out, st, prof, kclass, dst_h);
+                        float *dst, const __half *gm, float *b, float w, bool want_dot, const float *p,
+                        double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
+                        int kclass, __half *dst_h) {
+    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, want_dot, p, partial, dot_add, dot_out, st, prof,
+                kclass, dst_h);
 }
 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,

@@ -162,6 +162,27 @@ __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float 
     stats_store(rr, sc, partial);
 }
 
+// the four line-search dot products in one sweep over g, x, Av, v, Ax
+__global__ void __launch_bounds__(RT) k_ls_dots(const float *__restrict__ g, const float *__restrict__ x,
+                                                const float *__restrict__ Av, const float *__restrict__ v,
+                                                const float *__restrict__ Ax, long long n,
+                                                double *__restrict__ partial) {
+    Acc2 a0, a1, a2, a3;
+    const long long stride = (long long)gridDim.x * RT;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride) {
+        const float xi = x[i], Axi = Ax[i];
+        a0.add_prod(g[i], xi);
+        a1.add_prod(xi, Av[i]);
+        a2.add_prod(v[i], Axi);
+        a3.add_prod(xi, Axi);
+    }
+    double s[4] = {a0.value(), a1.value(), a2.value(), a3.value()};
+    block_sum4(s);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partial[4 * blockIdx.x + k] = s[k];
+}
+
 __global__ void __launch_bounds__(RT) k_finalize4(const double *__restrict__ partial, int nb,
                                                   double *__restrict__ out) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -278,6 +299,14 @@ inline int blocks_for(long long n) {
 
 void launch_finalize(const double *partial, int nb, const double *add, double *dev_out, cudaStream_t st) {
     k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out, add);
+}
+
+void launch_ls_dots(const float *g, const float *x, const float *Av, const float *v, const float *Ax, long long n,
+                    double *partial, double *dev_out, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st, 20.0 * n, 2);
+    const int nb = blocks_for(n);
+    k_ls_dots<<<nb, RT, 0, st>>>(g, x, Av, v, Ax, n, partial);
+    k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
 void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
