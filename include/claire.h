@@ -257,6 +257,22 @@ void claire_solve_opts_default(claire_solve_opts *opts);
 int claire_solve(claire_ctx *ctx, float *v_inout, const claire_solve_opts *opts,
                  claire_solve_report *report);
 
+/* claire_set_images + claire_solve with HOST buffers, the host<->device
+ * copies overlapped with the computation: m0, m1 (float[N] each), v_in (the
+ * initial velocity) and v_out (the result; may be v_in) are host memory,
+ * float[3][N] for the velocities.  The images are copied in on a second
+ * stream while the first foot points (which need only v) run; each accepted
+ * iterate is copied out while the gradient at it is computed, so the result
+ * is in v_out when the call returns.  The results equal claire_set_images +
+ * claire_solve on device copies, bit for bit.  Page-locked host memory is
+ * needed for the copies to overlap (pageable memory works, without overlap).
+ * The context keeps a device copy of v (12 B/voxel) from the first call on.
+ * Errors: as claire_solve, plus CLAIRE_ERR_ARG for NULL pointers; v_out is
+ * unspecified after an error other than CLAIRE_ERR_LINESEARCH /
+ * CLAIRE_ERR_NONFINITE (which leave the last accepted iterate there). */
+int claire_solve_host(claire_ctx *ctx, const float *m0, const float *m1, const float *v_in, float *v_out,
+                      const claire_solve_opts *opts, claire_solve_report *report);
+
 /* Batched form (no counterpart in the paper, which registers one pair at a
  * time): solve n independent registrations together, one per context, each
  * exactly as claire_solve would (same options for all; contexts may differ

@@ -37,7 +37,7 @@ EXPORTED = [
     "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
     "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization", "claire_solve_batch",
-    "claire_mismatch_forward", "claire_mismatch_backward",
+    "claire_mismatch_forward", "claire_mismatch_backward", "claire_solve_host",
 ]
 
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "claire_apply_A": [P, V, V], "claire_interp": [P, V, V, V],
         "claire_get_field": [P, I, I, V],
         "claire_solve": [P, V, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
+        "claire_solve_host": [P, V, V, V, V, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)],
         "claire_solve_batch": [ctypes.POINTER(P), ctypes.POINTER(V), I, ctypes.POINTER(SolveOpts),
                                ctypes.POINTER(SolveReport)],
         "claire_profile_enable": [P, I],
@@ -126,6 +127,14 @@ def _ptr(t):
         raise TypeError("expected a torch tensor")
     if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
         raise ValueError("fields must be contiguous float32 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("host fields must be contiguous float32 CPU tensors (page-locked for overlap)")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -358,6 +367,25 @@ class Registration:
         o = self.default_opts(**opts)
         rep = SolveReport()
         rc = load().claire_solve(self._h, _ptr(v_inout), ctypes.byref(o), ctypes.byref(rep))
+        if check and rc not in (CLAIRE_OK,):
+            _check(self._h, rc)
+        return Report(**rep.as_dict())
+
+    def solve_host(self, m0, m1, v_in, v_out=None, check=True, **opts):
+        """set_images + solve with host (CPU) tensors, the copies overlapped
+        with the computation (pin the tensors for the overlap); the result
+        lands in v_out (default: v_in) before the call returns."""
+        if isinstance(opts.get("precond"), str):
+            opts["precond"] = self.PRECOND[opts["precond"]]
+        if v_out is None:
+            v_out = v_in
+        n = self.shape[0] * self.shape[1] * self.shape[2]
+        if m0.numel() != n or m1.numel() != n or v_in.numel() != 3 * n or v_out.numel() != 3 * n:
+            raise ValueError("solve_host: m0, m1 need N values, v_in and v_out 3N")
+        o = self.default_opts(**opts)
+        rep = SolveReport()
+        rc = load().claire_solve_host(self._h, _host_ptr(m0), _host_ptr(m1), _host_ptr(v_in), _host_ptr(v_out),
+                                      ctypes.byref(o), ctypes.byref(rep))
         if check and rc not in (CLAIRE_OK,):
             _check(self._h, rc)
         return Report(**rep.as_dict())

@@ -145,6 +145,27 @@ struct claire_ctx {
     float *mhist_t = nullptr;
 
     bool have_images = false, have_lin = false;
+    // host-buffer solves (claire_solve_host): a second stream copies the
+    // images in while the first foot points run, and v out while the final
+    // gradient runs; vdev holds v on the device
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_main = nullptr, ev_img = nullptr, ev_vout = nullptr;
+    bool img_pending = false;  // the image copies on aux may still be running
+    float *vdev = nullptr;
+    void ensure_aux() {
+        if (aux) return;
+        CK(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ev_main, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_img, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_vout, cudaEventDisableTiming));
+    }
+    // order the main stream after the image copies (before m0 or m1 is read)
+    void wait_images() {
+        if (img_pending) {
+            CK(cudaStreamWaitEvent(st, ev_img, 0));
+            img_pending = false;
+        }
+    }
     // grad m^0 = grad m0 in gmhist slot 0 is current (m0 and the derivative
     // scheme unchanged since it was computed; a solve recomputes it once)
     bool gm0_valid = false;
@@ -162,6 +183,13 @@ struct claire_ctx {
     }
     ~claire_ctx() {
         if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
+        if (aux) {
+            cudaStreamSynchronize(aux);
+            cudaStreamDestroy(aux);
+            cudaEventDestroy(ev_main);
+            cudaEventDestroy(ev_img);
+            cudaEventDestroy(ev_vout);
+        }
         for (void *p : allocs) cudaFree(p);
         for (int a = 0; a < 3; ++a) cudaFree((void *)ax[a].tw);
     }
@@ -351,6 +379,7 @@ struct claire_ctx {
             // FP32 transport; FP16 copies of m^j and of grad m^j (taken of the
             // FP32 state); m(1) and grad m(1) also kept in FP32
             launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
+            wait_images();
             launch_f2h(m0, mhist_h, (long long)N, st, &prof);
             if (!gm0_valid) grad_h(m0, hist(gmhist_h, 0, 3));
             const float *src = m0;
@@ -366,10 +395,12 @@ struct claire_ctx {
             launch_f2h(gm1f, hist(gmhist_h, nt, 3), 3 * (long long)N, st, &prof);
         } else {
             launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
+            wait_images();
             CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
             for (int j = 0; j < nt; ++j)
                 launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
         }
+        wait_images();
         if (!h16)
             for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
         gm0_valid = true;
@@ -1074,7 +1105,12 @@ struct EvTimer {
 // One Gauss-Newton-Krylov solve (Algorithm 1) at the context's beta; returns
 // CLAIRE_OK, CLAIRE_ERR_LINESEARCH or CLAIRE_ERR_NONFINITE (v then holds the
 // last accepted iterate); other failures throw.
-static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, claire_solve_report *rep_out) {
+// v_host (optional): host buffer that receives the result.  Each accepted
+// step's v is copied there on the auxiliary stream while the gradient at
+// the new v runs (the last such copy is the result); the main stream waits
+// for a copy to finish before it overwrites v again.
+static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, claire_solve_report *rep_out,
+                    float *v_host = nullptr) {
     if (o.max_gn < 0 || o.max_pcg < 1 || o.fixed_pcg < 0 || !(o.eps_n >= 0) || o.max_ls < 0 ||
         o.precond < CLAIRE_PC_INVA || o.precond > CLAIRE_PC_2LINVH0 || !(o.eps_h0 > 0) || o.max_inner < 1)
         throw Error(CLAIRE_ERR_ARG, "invalid solve options");
@@ -1089,6 +1125,23 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
     const long long N = ctx->d.N;
     const double H3 = ctx->h3();
     cudaStream_t st = ctx->st;
+    bool exported = false;  // a copy of the current v to v_host is issued
+    auto export_v = [&]() {
+        if (!v_host) return;
+        CK(cudaEventRecord(ctx->ev_main, st));
+        CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_main, 0));
+        CK(cudaMemcpyAsync(v_host, v, n3 * sizeof(float), cudaMemcpyDeviceToHost, ctx->aux));
+        CK(cudaEventRecord(ctx->ev_vout, ctx->aux));
+        exported = true;
+    };
+    // the copy out must end before v is overwritten, and before returning
+    struct VoutWait {
+        claire_ctx *c;
+        const bool *on;
+        ~VoutWait() {
+            if (*on) cudaEventSynchronize(c->ev_vout);
+        }
+    } vout_wait{ctx, &exported};
     cudaEvent_t ev0, ev1;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
@@ -1219,7 +1272,9 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             status = CLAIRE_ERR_LINESEARCH;
             break;
         }
+        if (exported) CK(cudaStreamWaitEvent(st, ctx->ev_vout, 0));
         CK(cudaMemcpyAsync(v, vn, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        export_v();
         launch_axpby(Av, 1.f, Av, (float)alpha, Ax, n3, st, &ctx->prof);
         if (ctx->keeps_trial()) ctx->adopt_trial();
         ++k;
@@ -1245,6 +1300,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         const double b = ctx->fetch();
         rep.mismatch_rel = b > 0 ? std::sqrt(a / b) : 0.0;
     }
+    if (v_host && !exported) export_v();  // no accepted step: v as it came in
     rep.status = status;
     {
         float ms = 0;
@@ -1265,6 +1321,41 @@ int claire_solve(claire_ctx *ctx, float *v, const claire_solve_opts *opts, clair
     claire_solve_opts o;
     if (opts) o = *opts; else claire_solve_opts_default(&o);
     const int status = do_solve(ctx, v, o, rep_out);
+    if (status != CLAIRE_OK) return status;
+    API_END(ctx)
+}
+
+int claire_solve_host(claire_ctx *ctx, const float *m0, const float *m1, const float *v_in, float *v_out,
+                      const claire_solve_opts *opts, claire_solve_report *rep_out) {
+    API_BEGIN(ctx)
+    need(m0, "m0");
+    need(m1, "m1");
+    need(v_in, "v_in");
+    need(v_out, "v_out");
+    claire_solve_opts o;
+    if (opts) o = *opts; else claire_solve_opts_default(&o);
+    ctx->ensure_aux();
+    const long long N = ctx->d.N;
+    if (!ctx->vdev) ctx->vdev = ctx->alloc_f((size_t)3 * N);
+    // the images go in on the auxiliary stream once the work already queued
+    // on the context's stream (which may read the old images) is done; v on
+    // the main stream meanwhile; the solve waits for the images only where it
+    // first reads them, after its first foot points
+    CK(cudaEventRecord(ctx->ev_main, ctx->st));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_main, 0));
+    CK(cudaMemcpyAsync(ctx->m0, m0, N * sizeof(float), cudaMemcpyHostToDevice, ctx->aux));
+    CK(cudaMemcpyAsync(ctx->m1, m1, N * sizeof(float), cudaMemcpyHostToDevice, ctx->aux));
+    CK(cudaEventRecord(ctx->ev_img, ctx->aux));
+    ctx->img_pending = true;
+    ctx->have_images = true;
+    ctx->have_lin = false;
+    ctx->gm0_valid = false;
+    struct ImgWait {
+        claire_ctx *c;
+        ~ImgWait() { c->wait_images(); }
+    } img_wait{ctx};
+    CK(cudaMemcpyAsync(ctx->vdev, v_in, 3 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->st));
+    const int status = do_solve(ctx, ctx->vdev, o, rep_out, v_out);
     if (status != CLAIRE_OK) return status;
     API_END(ctx)
 }
