@@ -546,10 +546,16 @@ __device__ __forceinline__ void tile_range(int ntiles, int &tbeg, int &tend) {
     tend = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
 }
 
+// floors inside the clamp of floor_int: a non-finite or huge displacement
+// (clamped to +-1e6 there, while the box path converts floorf directly) sends
+// the block to the gather path, whose stencil clamps
+__device__ __forceinline__ bool floor_sane(int lo, int hi) { return lo > -1000000 && hi < 1000000; }
+
 // the box of a displacement field's floor range fits a buffer
 __device__ __forceinline__ bool box_fits(const int *__restrict__ range) {
     return range[1] - range[0] <= BOX_SPAN && range[3] - range[2] <= BOX_SPAN && range[5] - range[4] <= BOX_SPAN &&
-           range[0] <= range[1] && range[2] <= range[3] && range[4] <= range[5];
+           range[0] <= range[1] && range[2] <= range[3] && range[4] <= range[5] && floor_sane(range[0], range[1]) &&
+           floor_sane(range[2], range[3]) && floor_sane(range[4], range[5]);
 }
 
 // block partial of the dot product of the accumulating adjoint step
@@ -694,6 +700,162 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
         }
     }
     sl_dot_store<MODE>(dot, a.partial);
+}
+
+// ---------------------------------------------------------------------------
+// Foot points from shared-memory boxes (cubic interpolation of v at the RK2
+// predictor).  Persistent blocks walk the 32 x 8 x 4 tiles of the SL steps.
+// For each side the block reduces the floor range of its own predictor
+// displacements s dt v(x)/h over the tile, copies the three components of v
+// over that box into shared memory, and sums the 64 taps of all three
+// components with one set of weights: one shared-memory wavefront per tap and
+// warp, where the global-memory gather of a misaligned 32-float row costs two
+// L1 wavefronts.  A tile whose predictor floors span more than the box allows
+// gathers from global memory instead (the decision is uniform per block).
+// The block also reduces the floor range of what it wrote (the SL steps' box
+// geometry) into part[block][12], as k_footpoints does.
+// ---------------------------------------------------------------------------
+constexpr int FP_OCC = 2;  // resident blocks per SM: three component boxes each
+
+// v at the predictor point i + q by global-memory gathers (tiles whose
+// predictor floors span more than the box).  Not inlined: its registers stay
+// out of the box path's allocation.
+__device__ __noinline__ float3 fp_gather3(const float *__restrict__ v, const Dims &d, int i1, int i2, int i3,
+                                          float q1, float q2, float q3) {
+    Axis4 a1, a2, a3;
+    axis_stencil(i1, q1, d.n1, d.n2 * d.n3, a1);
+    axis_stencil(i2, q2, d.n2, d.n3, a2);
+    axis_stencil(i3, q3, d.n3, 1, a3);
+    return make_float3(gather64(v, a1, a2, a3), gather64(v + d.N, a1, a2, a3), gather64(v + 2 * d.N, a1, a2, a3));
+}
+
+__global__ void __launch_bounds__(PT3 * PT2, FP_OCC)
+k_footpoints_box(const float *__restrict__ v, float *__restrict__ dispm, float *__restrict__ dispp, Dims d,
+                 float dt, float ih1, float ih2, float ih3, int chunked_in, int *__restrict__ part) {
+    extern __shared__ float smem[];
+    __shared__ int red[PT2][12];
+    __shared__ int rng[6];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool chunked = chunked_in != 0;
+    const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
+    const long long N = d.N, plane = (long long)d.n2 * d.n3;
+    const float ih[3] = {ih1, ih2, ih3};
+    // floor range of the outputs: [side * 3 + axis]
+    int omn[6], omx[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) { omn[k] = 0x7fffffff; omx[k] = -0x7fffffff; }
+    int tbeg, tend;
+    tile_range(nb3 * nb2 * nb1, tbeg, tend);
+    for (int tile = tbeg; tile < tend; ++tile) {
+        const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
+        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+        const long long id0 = (long long)t1 * PT1 * plane + (long long)i2 * d.n3 + i3;
+        bool ok[PT1];
+        float vx[PT1][3];
+#pragma unroll
+        for (int t = 0; t < PT1; ++t) {
+            ok[t] = i3 < d.n3 && i2 < d.n2 && t1 * PT1 + t < d.n1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vx[t][c] = ok[t] ? v[c * N + id0 + t * plane] : 0.f;
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float *out = s == 0 ? dispm : dispp;
+            if (!out) continue;
+            const float sdt = s == 0 ? -dt : dt, hs = 0.5f * sdt;
+            // floor range of the predictor displacements over the tile
+            int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+#pragma unroll
+            for (int t = 0; t < PT1; ++t) {
+                if (ok[t]) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int f = floor_int(sdt * vx[t][c] * ih[c]);
+                        lo[c] = min(lo[c], f);
+                        hi[c] = max(hi[c], f);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int a = __reduce_min_sync(0xffffffffu, lo[c]), b = __reduce_max_sync(0xffffffffu, hi[c]);
+                if (tx == 0) {
+                    red[ty][2 * c] = a;
+                    red[ty][2 * c + 1] = b;
+                }
+            }
+            __syncthreads();
+            if (ty == 0 && tx < 6) {
+                int x = red[0][tx];
+                for (int y = 1; y < PT2; ++y) x = (tx & 1) ? max(x, red[y][tx]) : min(x, red[y][tx]);
+                rng[tx] = x;
+            }
+            __syncthreads();
+            const int f0 = rng[0], f1 = rng[2], f2 = rng[4];
+            const bool fits = rng[1] - f0 <= BOX_SPAN && rng[3] - f1 <= BOX_SPAN && rng[5] - f2 <= BOX_SPAN &&
+                              floor_sane(f0, rng[1]) && floor_sane(f1, rng[3]) && floor_sane(f2, rng[5]);
+            if (fits) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    box_copy(v + c * N, d, plane, t1 * PT1 + f0 - 1, t2 * PT2 + f1 - 1, t3 * PT3 + f2 - 1,
+                             smem + c * BOX_FLOATS, chunked);
+                cp_async_wait<0>();
+                __syncthreads();
+            }
+            const int sh = box_shift(t3 * PT3 + f2 - 1, chunked);
+#pragma unroll
+            for (int t = 0; t < PT1; ++t) {
+                if (!ok[t]) continue;
+                const float q1 = sdt * vx[t][0] * ih1, q2 = sdt * vx[t][1] * ih2, q3 = sdt * vx[t][2] * ih3;
+                float w[3];
+                if (fits) {
+                    const float fl1 = floorf(q1), fl2 = floorf(q2), fl3 = floorf(q3);
+                    const int b1 = t + (int)fl1 - f0, b2 = ty + (int)fl2 - f1, b3 = tx + (int)fl3 - f2 + sh;
+                    const float *p = smem + (b1 * BS2 + b2) * BOX_PITCH + b3;
+                    float w1[4], w2[4], w3[4];
+                    lagrange4(q1 - fl1, w1);
+                    lagrange4(q2 - fl2, w2);
+                    lagrange4(q3 - fl3, w3);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) w[c] = box_cubic(p + c * BOX_FLOATS, w1, w2, w3);
+                } else {
+                    const float3 g = fp_gather3(v, d, t1 * PT1 + t, i2, i3, q1, q2, q3);
+                    w[0] = g.x;
+                    w[1] = g.y;
+                    w[2] = g.z;
+                }
+                const long long id = id0 + t * plane;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float o = hs * (vx[t][c] + w[c]) * ih[c];
+                    out[c * N + id] = o;
+                    const int f = floor_int(o);
+                    omn[3 * s + c] = min(omn[3 * s + c], f);
+                    omx[3 * s + c] = max(omx[3 * s + c], f);
+                }
+            }
+            // the boxes and rng are rewritten by the next side or tile
+            __syncthreads();
+        }
+    }
+    // block partial of the output floor ranges
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int a = __reduce_min_sync(0xffffffffu, omn[k]), b = __reduce_max_sync(0xffffffffu, omx[k]);
+        if (tx == 0) {
+            red[ty][2 * k] = a;
+            red[ty][2 * k + 1] = b;
+        }
+    }
+    __syncthreads();
+    if (ty == 0 && tx < 12) {
+        const int k = tx;
+        const bool on = k < 6 ? dispm != nullptr : dispp != nullptr;
+        int x = (k & 1) ? -0x7fffffff : 0x7fffffff;
+        if (on)
+            for (int y = 0; y < PT2; ++y) x = (k & 1) ? max(x, red[y][k]) : min(x, red[y][k]);
+        part[(long long)blockIdx.x * 12 + k] = x;
+    }
 }
 
 // per-axis [min, max] of floor(disp) over the field (6 ints: min0, max0, ...)
@@ -889,14 +1051,26 @@ void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, floa
     const double two_pi = 6.283185307179586476925286766559;
     ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)), 4);
     const float i1 = (float)(d.n1 / two_pi), i2 = (float)(d.n2 / two_pi), i3 = (float)(d.n3 / two_pi);
-    const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
-    if (d.iorder == 1)
+    long long nblocks;
+    if (d.iorder == 1) {
+        const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
         k_footpoints<1><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, part);
-    else
-        k_footpoints<3><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, part);
+        nblocks = (long long)grid.x * grid.y * grid.z;
+    } else {
+        const size_t smem = 3 * BOX_FLOATS * sizeof(float);
+        // set once, so that launches being captured make no other runtime call
+        static std::once_flag attr;
+        std::call_once(attr, [] {
+            cudaFuncSetAttribute(k_footpoints_box, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(3 * BOX_FLOATS * sizeof(float)));
+        });
+        const int grid = pipe_blocks(d, FP_OCC);
+        k_footpoints_box<<<grid, dim3(PT3, PT2), smem, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, chunk_ok(d, v),
+                                                             part);
+        nblocks = grid;
+    }
     if (dispm) k_range_init<<<1, 32, 0, st>>>(range_m);
     if (dispp) k_range_init<<<1, 32, 0, st>>>(range_p);
-    const long long nblocks = (long long)grid.x * grid.y * grid.z;
     k_range_parts<<<num_sms(), 256, 0, st>>>(part, nblocks, dispm ? range_m : nullptr, dispp ? range_p : nullptr);
 }
 
@@ -959,7 +1133,8 @@ void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int 
                  float *dst, const TG *gm, float *b, float w, bool want_dot, const float *p, double *partial,
                  const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
                  __half *dst_h) {
-    ProfScope ps(prof, kclass, st, (48.0 + 3 * sizeof(TG) + (p ? 12 : 0) + (dst_h ? 2 : 0)) * d.N,
+    // p is read only by the step that forms the dot product
+    ProfScope ps(prof, kclass, st, (48.0 + 3 * sizeof(TG) + (want_dot && p ? 12 : 0) + (dst_h ? 2 : 0)) * d.N,
                  kSlLaunches + (want_dot ? 1 : 0));
     SlArgsT<float, TG> a{src, dispp, dst, cfac, nullptr, gm, 0.f, dst_h};
     a.acc = b;
