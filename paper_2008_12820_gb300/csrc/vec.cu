@@ -9,6 +9,7 @@
 // fixed-size array, and one block sums them in a fixed order: deterministic
 // for a given grid.
 #include <cuda_fp16.h>
+#include <cstdint>
 #include <cuda_runtime.h>
 
 #include "claire_internal.cuh"
@@ -26,24 +27,50 @@ constexpr int RT = 256;
 // block sum of v (1D blocks of RT threads); valid in thread 0
 __device__ __forceinline__ double block_sum(double v) { return block_sum_n<RT>(v, threadIdx.x); }
 
+// Four consecutive elements at once (16-byte loads and stores) where the
+// length is a multiple of 4 and the pointers are 16-byte aligned: four times
+// the bytes in flight per instruction, which the scalar grid-stride loops
+// lack to cover HBM latency.  Element k of a float4 as an lvalue (k is a
+// compile-time constant after unrolling).
+__device__ __forceinline__ float &lane(float4 &v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+__device__ __forceinline__ float4 ld4(const float *p, long long i) { return reinterpret_cast<const float4 *>(p)[i]; }
+__device__ __forceinline__ float4 ld4(const __half *p, long long i) {
+    const uint2 u = reinterpret_cast<const uint2 *>(p)[i];
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(float *p, long long i, const float4 &v) { reinterpret_cast<float4 *>(p)[i] = v; }
+
 // MODE 0: sum a*b;  MODE 1: sum (a-b)^2
-template <int MODE, typename TA = float>
+template <int MODE>
+__device__ __forceinline__ void reduce2_add(Acc2 &acc, float x, float y) {
+    if (MODE == 0) {
+        acc.add_prod(x, y);
+    } else {
+        // d = x - y exactly as dh + dl (TwoSum), then d^2 ~ dh^2 + 2 dh dl
+        const float dh = __fsub_rn(x, y);
+        const float z = __fsub_rn(dh, x);
+        const float dl = __fadd_rn(__fsub_rn(x, __fsub_rn(dh, z)), __fsub_rn(-y, z));
+        const float p = __fmul_rn(dh, dh);
+        acc.add(p, fmaf(dh, dh, -p) + 2.f * dh * dl);
+    }
+}
+
+template <int MODE, typename TA = float, bool V4 = false>
 __global__ void __launch_bounds__(RT) k_reduce2(const TA *__restrict__ a, const float *__restrict__ b,
                                                 long long n, double *__restrict__ partial) {
     Acc2 acc;
     const long long stride = (long long)gridDim.x * RT;
-    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride) {
-        const float x = ldv(a + i), y = b[i];
-        if (MODE == 0) {
-            acc.add_prod(x, y);
-        } else {
-            // d = x - y exactly as dh + dl (TwoSum), then d^2 ~ dh^2 + 2 dh dl
-            const float dh = __fsub_rn(x, y);
-            const float z = __fsub_rn(dh, x);
-            const float dl = __fadd_rn(__fsub_rn(x, __fsub_rn(dh, z)), __fsub_rn(-y, z));
-            const float p = __fmul_rn(dh, dh);
-            acc.add(p, fmaf(dh, dh, -p) + 2.f * dh * dl);
+    if (V4) {
+        for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < (n >> 2); i += stride) {
+            float4 x = ld4(a, i), y = ld4(b, i);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) reduce2_add<MODE>(acc, lane(x, k), lane(y, k));
         }
+    } else {
+        for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += stride)
+            reduce2_add<MODE>(acc, ldv(a + i), b[i]);
     }
     double s = block_sum(acc.value());
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -123,23 +150,39 @@ __device__ __forceinline__ void stats_store(Acc2 &rr, Acc2 *sc, double *partial)
     }
 }
 
+template <bool V4>
 __global__ void __launch_bounds__(RT) k_stats(const float *__restrict__ r, long long N,
                                               double *__restrict__ partial) {
     Acc2 rr, sc[3];
     const long long stride = (long long)gridDim.x * RT;
+    if (V4) {
+        const long long N4 = N >> 2;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
-            const float ri = r[c * N + i];
-            rr.add_prod(ri, ri);
-            sc[c].add(ri, 0.f);
-        }
+        for (int c = 0; c < 3; ++c)
+            for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N4; i += stride) {
+                float4 rv = ld4(r, c * N4 + i);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    rr.add_prod(lane(rv, k), lane(rv, k));
+                    sc[c].add(lane(rv, k), 0.f);
+                }
+            }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
+                const float ri = r[c * N + i];
+                rr.add_prod(ri, ri);
+                sc[c].add(ri, 0.f);
+            }
+    }
     stats_store(rr, sc, partial);
 }
 
 // PCG update with the regularization term carried along (x, A x, r):
 // x += a p; Ax += a Ap; r -= a q; statistics of the new r.  q_adds_Ap: q
 // holds only the body force of H p, and H p = Ap + q is formed here.
+template <bool V4>
 __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float *__restrict__ Ax,
                                                    float *__restrict__ r, const float *__restrict__ p,
                                                    const float *__restrict__ Ap,
@@ -147,18 +190,45 @@ __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float 
                                                    long long N, double *__restrict__ partial, int q_adds_Ap) {
     Acc2 rr, sc[3];
     const long long stride = (long long)gridDim.x * RT;
+    const bool wantAp = Ax || q_adds_Ap;
+    if (V4) {
+        const long long N4 = N >> 2;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
-            x[i] = fmaf(alpha, p[i], x[i]);
-            const float Api = (Ax || q_adds_Ap) ? Ap[i] : 0.f;
-            if (Ax) Ax[i] = fmaf(alpha, Api, Ax[i]);
-            const float qi = q_adds_Ap ? q[i] + Api : q[i];
-            const float ri = fmaf(-alpha, qi, r[i]);
-            r[i] = ri;
-            rr.add_prod(ri, ri);
-            sc[c].add(ri, 0.f);
-        }
+        for (int c = 0; c < 3; ++c)
+            for (long long i = c * N4 + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N4; i += stride) {
+                float4 xv = ld4(x, i), rv = ld4(r, i);
+                const float4 pv = ld4(p, i), qv = ld4(q, i);
+                const float4 apv = wantAp ? ld4(Ap, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 axv = Ax ? ld4(Ax, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float4 pk = pv, qk = qv, ak = apv;
+                    lane(xv, k) = fmaf(alpha, lane(pk, k), lane(xv, k));
+                    lane(axv, k) = fmaf(alpha, lane(ak, k), lane(axv, k));
+                    const float qi = q_adds_Ap ? lane(qk, k) + lane(ak, k) : lane(qk, k);
+                    const float ri = fmaf(-alpha, qi, lane(rv, k));
+                    lane(rv, k) = ri;
+                    rr.add_prod(ri, ri);
+                    sc[c].add(ri, 0.f);
+                }
+                st4(x, i, xv);
+                if (Ax) st4(Ax, i, axv);
+                st4(r, i, rv);
+            }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
+                x[i] = fmaf(alpha, p[i], x[i]);
+                const float Api = wantAp ? Ap[i] : 0.f;
+                if (Ax) Ax[i] = fmaf(alpha, Api, Ax[i]);
+                const float qi = q_adds_Ap ? q[i] + Api : q[i];
+                const float ri = fmaf(-alpha, qi, r[i]);
+                r[i] = ri;
+                rr.add_prod(ri, ri);
+                sc[c].add(ri, 0.f);
+            }
+    }
     stats_store(rr, sc, partial);
 }
 
@@ -225,7 +295,7 @@ __global__ void __launch_bounds__(RT) k_pcg_dir(float *__restrict__ p, float *__
 
 // k_pcg_dir per voxel, also writing the first incremental-state field of the
 // next matvec, u0 = dt/2 f^0 with f^0 = -p . grad m^0 (saves that pass)
-template <typename TG>
+template <typename TG, bool V4>
 __global__ void __launch_bounds__(RT) k_pcg_dir_u0(float *__restrict__ p, float *__restrict__ Ap,
                                                    const float *__restrict__ z, const float *__restrict__ r,
                                                    const double *__restrict__ rsum, const float *__restrict__ Az,
@@ -237,26 +307,68 @@ __global__ void __launch_bounds__(RT) k_pcg_dir_u0(float *__restrict__ p, float 
     float mean[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) mean[c] = Az ? 0.f : (float)(rsum[c] / (double)N);
-    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
-        float pc[3];
+    if (V4) {
+        const long long N4 = N >> 2;
+        for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N4; i += stride) {
+            float4 pc[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const long long k = c * N + i;
-            const float ar = Az ? Az[k] : r[k] - mean[c];
-            float apc;
-            if (init) {
-                pc[c] = z[k];
-                apc = ar;
-            } else {
-                pc[c] = fmaf(b, p[k], z[k]);
-                apc = fmaf(b, Ap[k], ar);
+            for (int c = 0; c < 3; ++c) {
+                const long long k4 = c * N4 + i;
+                float4 arv = Az ? ld4(Az, k4) : ld4(r, k4);
+                const float4 zv = ld4(z, k4);
+                float4 pv = init ? zv : ld4(p, k4);
+                float4 apv = init ? arv : ld4(Ap, k4);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float4 zk = zv;
+                    const float ar = Az ? lane(arv, k) : lane(arv, k) - mean[c];
+                    float apc;
+                    if (init) {
+                        apc = ar;
+                    } else {
+                        lane(pv, k) = fmaf(b, lane(pv, k), lane(zk, k));
+                        apc = fmaf(b, lane(apv, k), ar);
+                    }
+                    lane(apv, k) = apc;
+                    if (partial) pap.add_prod(lane(pv, k), apc);
+                }
+                st4(Ap, k4, apv);
+                st4(p, k4, pv);
+                pc[c] = pv;
             }
-            Ap[k] = apc;
-            p[k] = pc[c];
-            if (partial) pap.add_prod(pc[c], apc);
+            const float4 g0 = ld4(gm0, i), g1 = ld4(gm0 + N, i), g2 = ld4(gm0 + 2 * N, i);
+            float4 uv;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4 a0 = g0, a1 = g1, a2 = g2;
+                const float f = -(lane(pc[0], k) * lane(a0, k) + lane(pc[1], k) * lane(a1, k) +
+                                  lane(pc[2], k) * lane(a2, k));
+                lane(uv, k) = hdt * f;
+            }
+            st4(u0, i, uv);
         }
-        const float f = -(pc[0] * ldv(gm0 + i) + pc[1] * ldv(gm0 + N + i) + pc[2] * ldv(gm0 + 2 * N + i));
-        u0[i] = hdt * f;
+    } else {
+        for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < N; i += stride) {
+            float pc[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long k = c * N + i;
+                const float ar = Az ? Az[k] : r[k] - mean[c];
+                float apc;
+                if (init) {
+                    pc[c] = z[k];
+                    apc = ar;
+                } else {
+                    pc[c] = fmaf(b, p[k], z[k]);
+                    apc = fmaf(b, Ap[k], ar);
+                }
+                Ap[k] = apc;
+                p[k] = pc[c];
+                if (partial) pap.add_prod(pc[c], apc);
+            }
+            const float f = -(pc[0] * ldv(gm0 + i) + pc[1] * ldv(gm0 + N + i) + pc[2] * ldv(gm0 + 2 * N + i));
+            u0[i] = hdt * f;
+        }
     }
     if (partial) {
         const double s = block_sum(pap.value());
@@ -295,6 +407,14 @@ inline int blocks_for(long long n) {
     return (int)(b < kReduceBlocks ? b : kReduceBlocks);
 }
 
+// the float4 forms apply: a whole number of float4 per component and every
+// pointer 16-byte aligned (8-byte for FP16 fields); null pointers pass
+template <typename T>
+inline bool al16(const T *p) { return ((uintptr_t)p & (sizeof(T) == 2 ? 7 : 15)) == 0; }
+inline bool v4_ok(long long N) { return (N & 3) == 0; }
+template <typename T, typename... R>
+inline bool v4_ok(long long N, const T *p, const R *...rest) { return al16(p) && v4_ok(N, rest...); }
+
 }  // namespace
 
 void launch_finalize(const double *partial, int nb, const double *add, double *dev_out, cudaStream_t st) {
@@ -312,16 +432,20 @@ void launch_ls_dots(const float *g, const float *x, const float *Av, const float
 void launch_dot(const float *a, const float *b, long long n, double *partial, double *dev_out,
                 cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st, 8.0 * n, 2);
-    const int nb = blocks_for(n);
-    k_reduce2<0><<<nb, RT, 0, st>>>(a, b, n, partial);
+    const bool v4 = v4_ok(n, a, b);
+    const int nb = blocks_for(v4 ? n / 4 : n);
+    if (v4) k_reduce2<0, float, true><<<nb, RT, 0, st>>>(a, b, n, partial);
+    else k_reduce2<0><<<nb, RT, 0, st>>>(a, b, n, partial);
     k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
 void launch_sqdiff(const float *a, const float *b, long long n, double *partial, double *dev_out,
                    cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st, 8.0 * n, 2);
-    const int nb = blocks_for(n);
-    k_reduce2<1><<<nb, RT, 0, st>>>(a, b, n, partial);
+    const bool v4 = v4_ok(n, a, b);
+    const int nb = blocks_for(v4 ? n / 4 : n);
+    if (v4) k_reduce2<1, float, true><<<nb, RT, 0, st>>>(a, b, n, partial);
+    else k_reduce2<1><<<nb, RT, 0, st>>>(a, b, n, partial);
     k_finalize<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
@@ -365,8 +489,10 @@ void launch_diff_flag(const float *a, const float *b, long long n, int *flag, cu
 void launch_stats(const float *r, long long N, double *partial, double *dev_out, cudaStream_t st,
                   Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st, 12.0 * N, 2);
-    const int nb = blocks_for(N);
-    k_stats<<<nb, RT, 0, st>>>(r, N, partial);
+    const bool v4 = v4_ok(N, r);
+    const int nb = blocks_for(v4 ? N / 4 : N);
+    if (v4) k_stats<true><<<nb, RT, 0, st>>>(r, N, partial);
+    else k_stats<false><<<nb, RT, 0, st>>>(r, N, partial);
     k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
@@ -374,8 +500,10 @@ void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const floa
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
                        cudaStream_t st, Profiler *prof, bool q_adds_Ap) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (Ax ? 36 : 24), 2);
-    const int nb = blocks_for(N);
-    k_pcg_update<<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0);
+    const bool v4 = v4_ok(N, x, Ax, r, p, Ap, q);
+    const int nb = blocks_for(v4 ? N / 4 : N);
+    if (v4) k_pcg_update<true><<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0);
+    else k_pcg_update<false><<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0);
     k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
@@ -392,9 +520,14 @@ static void pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, cons
                        double *pap_out, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)N * (3.0 * (init ? 16 : 24) + 3 * sizeof(TG) + 4),
                  pap_out ? 2 : 1);
-    const int nb = blocks_for(N);
-    k_pcg_dir_u0<<<nb, RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt,
-                                    pap_out ? partial : nullptr);
+    const bool v4 = v4_ok(N, p, Ap, z, r, Az, gm0, u0);
+    const int nb = blocks_for(v4 ? N / 4 : N);
+    if (v4)
+        k_pcg_dir_u0<TG, true><<<nb, RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt,
+                                                  pap_out ? partial : nullptr);
+    else
+        k_pcg_dir_u0<TG, false><<<nb, RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt,
+                                                   pap_out ? partial : nullptr);
     if (pap_out) k_finalize<<<1, RT, 0, st>>>(partial, nb, pap_out);
 }
 
