@@ -83,6 +83,8 @@ def parse():
                     help="fp16: stored state / adjoint trajectories in FP16 (FP32 arithmetic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fft-reference", action="store_true",
+                    help="skip the cuFFT reference point (profiling captures of the library's kernels)")
     ap.add_argument("--grid", type=int, default=0,
                     help="run the same generator on an n^3 grid (profiling captures; not a bench line)")
     return ap.parse_args()
@@ -277,7 +279,7 @@ def run_ours(args):
     mv_ms = e0.elapsed_time(e1) / nmv
     mv_gvox = N / (mv_ms * 1e-3) / 1e9
 
-    fft_ref = fft_reference(reg, vt, beta, gamma, stream) if rank == 0 else None
+    fft_ref = fft_reference(reg, vt, beta, gamma, stream) if rank == 0 and not args.no_fft_reference else None
 
     # ---- roofline of the dominant kernel class ----------------------------
     peak, peak_src = read_peaks()
