@@ -253,7 +253,8 @@ void claire_solve_opts_default(claire_solve_opts *opts);
  * current iterate).  Armijo: alpha = 1, halve until
  * J(v + alpha vt) <= J(v) + c1 alpha <g, vt>_{L2}.  report may be NULL.
  * Returns CLAIRE_OK, or CLAIRE_ERR_LINESEARCH / CLAIRE_ERR_NONFINITE (v_inout
- * then holds the last accepted iterate). */
+ * then holds the last accepted iterate, and the report is filled with the
+ * status, e.g. a NaN in an image gives CLAIRE_ERR_NONFINITE with n_gn = 0). */
 int claire_solve(claire_ctx *ctx, float *v_inout, const claire_solve_opts *opts,
                  claire_solve_report *report);
 
@@ -328,6 +329,17 @@ int claire_launch_count(const claire_ctx *ctx, long *launches);
 
 /* Device bytes held by the context. */
 int claire_workspace_bytes(const claire_ctx *ctx, size_t *bytes);
+
+/* Cap, for every context of the process, on the device bytes one context may
+ * allocate (its workspace at claire_create and buffers it allocates later,
+ * e.g. the checkpoints of the differentiable form); 0 (the default) removes
+ * the cap.  An allocation that would pass the cap fails with CLAIRE_ERR_OOM
+ * before cudaMalloc is called, exactly as a failed cudaMalloc does: the
+ * context (or claire_create) reports the error and stays usable.  For
+ * callers that budget device memory, and to test the out-of-memory paths
+ * without exhausting the device.  Contexts created earlier keep what they
+ * hold.  No counterpart in the paper. */
+int claire_set_workspace_limit(size_t bytes);
 
 /* ---- preconditioner without device allocation --------------------------
  * The paper has no counterpart of this entry point; it exists for callers

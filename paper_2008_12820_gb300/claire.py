@@ -37,7 +37,7 @@ EXPORTED = [
     "claire_solve", "claire_profile_enable", "claire_profile_read", "claire_launch_count",
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
     "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization", "claire_solve_batch",
-    "claire_mismatch_forward", "claire_mismatch_backward", "claire_solve_host",
+    "claire_mismatch_forward", "claire_mismatch_backward", "claire_solve_host", "claire_set_workspace_limit",
 ]
 
 
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "claire_profile_read": [P, I, ctypes.POINTER(ctypes.c_long), pd, pd],
         "claire_launch_count": [P, ctypes.POINTER(ctypes.c_long)],
         "claire_workspace_bytes": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "claire_set_workspace_limit": [ctypes.c_size_t],
         "claire_precond_noalloc": [I, I, I, D, D, V, V, V],
         "claire_precond_h0": [P, V, V, D, I, I, ctypes.POINTER(ctypes.c_int)],
         "claire_set_discretization": [P, I, I],
@@ -165,6 +166,14 @@ class Report:
     t_obj_ms: float
     t_pcg_ms: float
     t_total_ms: float
+
+
+def set_workspace_limit(nbytes):
+    """Cap the device bytes any one context may allocate (0: no cap); an
+    allocation past it fails with CLAIRE_ERR_OOM (claire_set_workspace_limit)."""
+    rc = load().claire_set_workspace_limit(int(nbytes))
+    if rc != CLAIRE_OK:
+        raise ClaireError(rc, "claire_set_workspace_limit")
 
 
 def precond_noalloc(r, s, beta, gamma, stream=None):

@@ -18,6 +18,8 @@
 #include <utility>
 #include <vector>
 
+#include <atomic>
+
 #include "claire.h"
 #include "claire_internal.cuh"
 
@@ -50,6 +52,8 @@ void check_launch(const char *where) {
 }
 
 thread_local std::string g_create_error = "no error";
+// process-wide cap on the device bytes one context may allocate (0: none)
+std::atomic<size_t> g_workspace_limit{0};
 
 bool valid_n(int n) {
     if (n < 4 || n > 1024) return false;
@@ -175,11 +179,24 @@ struct claire_ctx {
     float *alloc_f(size_t n) { return (float *)alloc_bytes(n * sizeof(float)); }
     __half *alloc_h(size_t n) { return (__half *)alloc_bytes(n * sizeof(__half)); }
     void *alloc_bytes(size_t b) {
+        const size_t cap = g_workspace_limit.load();
+        if (cap && bytes + b > cap)
+            throw Error(CLAIRE_ERR_OOM, "workspace limit of " + std::to_string(cap) + " bytes: the context holds " +
+                                            std::to_string(bytes) + " and needs " + std::to_string(b) + " more");
         void *p = nullptr;
         CK(cudaMalloc(&p, b));
         allocs.push_back(p);
         bytes += b;
         return p;
+    }
+    // free what was allocated after a mark (a lazy allocation group that
+    // failed part way: its members are only assigned once all succeeded)
+    void rollback(size_t mark, size_t bytes0) {
+        while (allocs.size() > mark) {
+            cudaFree(allocs.back());
+            allocs.pop_back();
+        }
+        bytes = bytes0;
     }
     ~claire_ctx() {
         if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
@@ -595,12 +612,24 @@ struct claire_ctx {
     void ensure_ck(int stride) {
         if (stride != ck_stride) {
             if (ck) throw Error(CLAIRE_ERR_STATE, "checkpoint stride is fixed after the first differentiable forward");
-            ck_stride = stride;
-            ck = alloc_f((size_t)n_ck() * d.N);
-            seg_m = alloc_f((size_t)(stride + 1) * d.N);
-            seg_g = alloc_f((size_t)(stride + 1) * 3 * d.N);
-            bacc = alloc_f(3 * (size_t)d.N);
-            lam2 = alloc_f(2 * (size_t)d.N);
+            // all or nothing: a failed allocation leaves the context as it was
+            const size_t mark = allocs.size(), bytes0 = bytes;
+            try {
+                float *c0 = alloc_f((size_t)((nt + stride - 1) / stride + 1) * d.N);
+                float *c1 = alloc_f((size_t)(stride + 1) * d.N);
+                float *c2 = alloc_f((size_t)(stride + 1) * 3 * d.N);
+                float *c3 = alloc_f(3 * (size_t)d.N);
+                float *c4 = alloc_f(2 * (size_t)d.N);
+                ck = c0;
+                seg_m = c1;
+                seg_g = c2;
+                bacc = c3;
+                lam2 = c4;
+                ck_stride = stride;
+            } catch (...) {
+                rollback(mark, bytes0);
+                throw;
+            }
         }
     }
 
@@ -1158,14 +1187,15 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         ctx->gradient(v, g, &J, nullptr, Av);
     }
     const double g0 = std::sqrt(ctx->fetch(9));  // g . g from the gradient's last pass
-    if (!std::isfinite(g0) || !std::isfinite(J)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite gradient or objective");
+    // a non-finite start (e.g. a NaN image) ends the solve with its report
+    // filled and v as it came in, like a non-finite gradient later on
+    int status = (std::isfinite(g0) && std::isfinite(J)) ? CLAIRE_OK : CLAIRE_ERR_NONFINITE;
     rep.J0 = J;
     rep.g0 = g0;
     double gn = g0;
     double vAv = ctx->last_vAv;  // <v, beta A v> (sum over the grid)
     int k = 0;
-    int status = CLAIRE_OK;
-    for (;;) {
+    while (status == CLAIRE_OK) {
         const double grel = g0 > 0 ? gn / g0 : 0.0;
         if (grel <= o.eps_n || k >= o.max_gn) break;
         const double epsk = std::fmin(std::sqrt(grel), 0.5);
@@ -1522,6 +1552,11 @@ int claire_profile_read(claire_ctx *ctx, int cls, long *launches, double *total_
 int claire_launch_count(const claire_ctx *ctx, long *launches) {
     if (!ctx || !launches) return CLAIRE_ERR_ARG;
     *launches = ctx->prof.launches;
+    return CLAIRE_OK;
+}
+
+int claire_set_workspace_limit(size_t bytes) {
+    g_workspace_limit.store(bytes);
     return CLAIRE_OK;
 }
 
