@@ -1227,26 +1227,40 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             };
             // the direction update also writes u0 of the next matvec into s1a
             // and p . beta A p into dres[8] (the matvec's PCG form)
-            auto pcg_dir = [&](const float *Az, float b, bool init) {
+            // init: b = 0; otherwise b = dres[bn] / dres[bd] on the device
+            auto pcg_dir = [&](const float *Az, bool init, int bn, int bd) {
                 const float hdt = 0.5f / ctx->nt;
+                const double *dbn = init ? nullptr : ctx->dres + bn, *dbd = init ? nullptr : ctx->dres + bd;
                 if (ctx->h16)
-                    launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, b, N, init, ctx->hist(ctx->gmhist_h, 0, 3),
-                                      ctx->s1a, hdt, ctx->partial, ctx->dres + 8, st, &ctx->prof);
+                    launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, 0.f, N, init, ctx->hist(ctx->gmhist_h, 0, 3),
+                                      ctx->s1a, hdt, ctx->partial, ctx->dres + 8, st, &ctx->prof, dbn, dbd);
                 else
-                    launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, b, N, init, ctx->hist(ctx->gmhist, 0, 3),
-                                      ctx->s1a, hdt, ctx->partial, ctx->dres + 8, st, &ctx->prof);
+                    launch_pcg_dir_u0(p, Ap, z, r, ctx->dres + 1, Az, 0.f, N, init, ctx->hist(ctx->gmhist, 0, 3),
+                                      ctx->s1a, hdt, ctx->partial, ctx->dres + 8, st, &ctx->prof, dbn, dbd);
             };
+            // The scalars of the recurrence stay on the device: r . z of the
+            // current direction in dres[rz] (slots 10 and 11 in turn), p . Hp
+            // in dres[0] from the matvec; the update takes alpha = rz / pq and
+            // the direction update beta = rz_new / rz from there.  One host
+            // read per iteration (r . r for the stopping test, p . Hp kept in
+            // dres[12] for the curvature test) instead of three.
             if (r0 > 0) {
                 const float *Az = apply_pc();
-                pcg_dir(Az, 0.f, true);
-                double rz = ctx->dot(r, z, n3);
+                pcg_dir(Az, true, 0, 0);
+                int rz = 10;
+                launch_dot(r, z, n3, ctx->partial, ctx->dres + rz, st, &ctx->prof);
                 while (it < maxit) {
                     {
                         EvTimer t(st, &rep.t_hess_ms);
                         ctx->matvec(p, q, true);
                     }
                     rep.n_matvec++;
-                    const double pq = ctx->fetch(0);
+                    // x, Ax, r change only when p . Hp > 0
+                    launch_pcg_update(x, Ax, r, p, Ap, q, 0.f, N, ctx->partial, ctx->dres, st, &ctx->prof, true,
+                                      ctx->dres, ctx->dres + rz, ctx->dres + 12);
+                    double h[13];
+                    ctx->fetch_n(0, 13, h);
+                    const double pq = h[12];
                     if (!std::isfinite(pq)) throw Error(CLAIRE_ERR_NONFINITE, "non-finite p.Hp in PCG");
                     if (pq <= 0) {
                         if (it == 0) {
@@ -1257,18 +1271,15 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                         ++it;
                         break;
                     }
-                    const double alpha = rz / pq;
-                    launch_pcg_update(x, Ax, r, p, Ap, q, (float)alpha, N, ctx->partial, ctx->dres, st,
-                                      &ctx->prof, true);
                     ++it;
-                    const double rn = std::sqrt(ctx->fetch(0));
+                    const double rn = std::sqrt(h[0]);
                     if (o.fixed_pcg == 0 && rn <= epsk * r0) break;
                     if (it >= maxit) break;
                     const float *Az = apply_pc();
-                    const double rz_new = ctx->dot(r, z, n3);
-                    const double beta = rz_new / rz;
+                    const int rz_new = 21 - rz;
+                    launch_dot(r, z, n3, ctx->partial, ctx->dres + rz_new, st, &ctx->prof);
+                    pcg_dir(Az, false, rz_new, rz);
                     rz = rz_new;
-                    pcg_dir(Az, (float)beta, false);
                 }
             }
             rep.n_pcg += it;

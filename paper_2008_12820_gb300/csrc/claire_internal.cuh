@@ -187,7 +187,8 @@ void launch_stats(const float *r, long long N, double *partial, double *dev_out,
 // body force of H p only); then the stats of r into dev_out[0..3]
 void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
-                       cudaStream_t st, Profiler *prof, bool q_adds_Ap = false);
+                       cudaStream_t st, Profiler *prof, bool q_adds_Ap = false, const double *dpq = nullptr,
+                       const double *drz = nullptr, double *pq_out = nullptr);
 // p = z + b p; Ap = (r - mean r) + b Ap (rsum: device component sums of r);
 // with Az given (beta*A z), Ap = Az + b Ap instead.  x += a p skips Ax if NULL.
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
@@ -198,10 +199,12 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
 // pap_out non-null, p . Ap of the new direction into *pap_out
 void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
                        float b, long long N, bool init, const float *gm0, float *u0, float hdt, double *partial,
-                       double *pap_out, cudaStream_t st, Profiler *prof);
+                       double *pap_out, cudaStream_t st, Profiler *prof, const double *dbn = nullptr,
+                       const double *dbd = nullptr);
 void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
                        float b, long long N, bool init, const __half *gm0, float *u0, float hdt, double *partial,
-                       double *pap_out, cudaStream_t st, Profiler *prof);
+                       double *pap_out, cudaStream_t st, Profiler *prof, const double *dbn = nullptr,
+                       const double *dbd = nullptr);
 // q = Ap + gm (gm . p): the zero-velocity Hessian given beta0*A p
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
                      cudaStream_t st, Profiler *prof);

@@ -182,15 +182,28 @@ __global__ void __launch_bounds__(RT) k_stats(const float *__restrict__ r, long 
 // PCG update with the regularization term carried along (x, A x, r):
 // x += a p; Ax += a Ap; r -= a q; statistics of the new r.  q_adds_Ap: q
 // holds only the body force of H p, and H p = Ap + q is formed here.
+// dpq, drz (optional): the step length is alpha = rz / pq from device
+// memory (no host round trip); with pq <= 0 or non-finite nothing is updated
+// (negative curvature: the caller stops) and the statistics are those of the
+// unchanged r.  pq_out keeps pq for the caller.
 template <bool V4>
 __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float *__restrict__ Ax,
                                                    float *__restrict__ r, const float *__restrict__ p,
                                                    const float *__restrict__ Ap,
                                                    const float *__restrict__ q, float alpha,
-                                                   long long N, double *__restrict__ partial, int q_adds_Ap) {
+                                                   long long N, double *__restrict__ partial, int q_adds_Ap,
+                                                   const double *__restrict__ dpq, const double *__restrict__ drz,
+                                                   double *__restrict__ pq_out) {
     Acc2 rr, sc[3];
     const long long stride = (long long)gridDim.x * RT;
     const bool wantAp = Ax || q_adds_Ap;
+    bool upd = true;
+    if (dpq) {
+        const double pq = *dpq;
+        upd = pq > 0.0 && pq <= 1.7976931348623157e308;
+        alpha = upd ? (float)(*drz / pq) : 0.f;
+        if (pq_out && blockIdx.x == 0 && threadIdx.x == 0) *pq_out = pq;
+    }
     if (V4) {
         const long long N4 = N >> 2;
 #pragma unroll
@@ -206,25 +219,30 @@ __global__ void __launch_bounds__(RT) k_pcg_update(float *__restrict__ x, float 
                     lane(xv, k) = fmaf(alpha, lane(pk, k), lane(xv, k));
                     lane(axv, k) = fmaf(alpha, lane(ak, k), lane(axv, k));
                     const float qi = q_adds_Ap ? lane(qk, k) + lane(ak, k) : lane(qk, k);
-                    const float ri = fmaf(-alpha, qi, lane(rv, k));
+                    const float ri = upd ? fmaf(-alpha, qi, lane(rv, k)) : lane(rv, k);
                     lane(rv, k) = ri;
                     rr.add_prod(ri, ri);
                     sc[c].add(ri, 0.f);
                 }
-                st4(x, i, xv);
-                if (Ax) st4(Ax, i, axv);
-                st4(r, i, rv);
+                if (upd) {
+                    st4(x, i, xv);
+                    if (Ax) st4(Ax, i, axv);
+                    st4(r, i, rv);
+                }
             }
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             for (long long i = c * N + blockIdx.x * (long long)RT + threadIdx.x; i < (c + 1) * N; i += stride) {
-                x[i] = fmaf(alpha, p[i], x[i]);
-                const float Api = wantAp ? Ap[i] : 0.f;
-                if (Ax) Ax[i] = fmaf(alpha, Api, Ax[i]);
-                const float qi = q_adds_Ap ? q[i] + Api : q[i];
-                const float ri = fmaf(-alpha, qi, r[i]);
-                r[i] = ri;
+                float ri = r[i];
+                if (upd) {
+                    x[i] = fmaf(alpha, p[i], x[i]);
+                    const float Api = wantAp ? Ap[i] : 0.f;
+                    if (Ax) Ax[i] = fmaf(alpha, Api, Ax[i]);
+                    const float qi = q_adds_Ap ? q[i] + Api : q[i];
+                    ri = fmaf(-alpha, qi, ri);
+                    r[i] = ri;
+                }
                 rr.add_prod(ri, ri);
                 sc[c].add(ri, 0.f);
             }
@@ -301,8 +319,12 @@ __global__ void __launch_bounds__(RT) k_pcg_dir_u0(float *__restrict__ p, float 
                                                    const double *__restrict__ rsum, const float *__restrict__ Az,
                                                    float b, long long N, int init, const TG *__restrict__ gm0,
                                                    float *__restrict__ u0, float hdt,
-                                                   double *__restrict__ partial) {
+                                                   double *__restrict__ partial, const double *__restrict__ dbn,
+                                                   const double *__restrict__ dbd) {
     const long long stride = (long long)gridDim.x * RT;
+    // dbn, dbd (optional): b = num / den from device memory (the PCG ratio of
+    // successive r . z, without a host round trip)
+    if (dbn) b = (float)(*dbn / *dbd);
     Acc2 pap;
     float mean[3];
 #pragma unroll
@@ -498,12 +520,17 @@ void launch_stats(const float *r, long long N, double *partial, double *dev_out,
 
 void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const float *Ap,
                        const float *q, float alpha, long long N, double *partial, double *dev_out,
-                       cudaStream_t st, Profiler *prof, bool q_adds_Ap) {
+                       cudaStream_t st, Profiler *prof, bool q_adds_Ap, const double *dpq, const double *drz,
+                       double *pq_out) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (Ax ? 36 : 24), 2);
     const bool v4 = v4_ok(N, x, Ax, r, p, Ap, q);
     const int nb = blocks_for(v4 ? N / 4 : N);
-    if (v4) k_pcg_update<true><<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0);
-    else k_pcg_update<false><<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0);
+    if (v4)
+        k_pcg_update<true><<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0, dpq, drz,
+                                             pq_out);
+    else
+        k_pcg_update<false><<<nb, RT, 0, st>>>(x, Ax, r, p, Ap, q, alpha, N, partial, q_adds_Ap ? 1 : 0, dpq, drz,
+                                              pq_out);
     k_finalize4<<<1, RT, 0, st>>>(partial, nb, dev_out);
 }
 
@@ -517,29 +544,29 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
 template <typename TG>
 static void pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
                        float b, long long N, bool init, const TG *gm0, float *u0, float hdt, double *partial,
-                       double *pap_out, cudaStream_t st, Profiler *prof) {
+                       double *pap_out, cudaStream_t st, Profiler *prof, const double *dbn, const double *dbd) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, (double)N * (3.0 * (init ? 16 : 24) + 3 * sizeof(TG) + 4),
                  pap_out ? 2 : 1);
     const bool v4 = v4_ok(N, p, Ap, z, r, Az, gm0, u0);
     const int nb = blocks_for(v4 ? N / 4 : N);
     if (v4)
         k_pcg_dir_u0<TG, true><<<nb, RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt,
-                                                  pap_out ? partial : nullptr);
+                                                  pap_out ? partial : nullptr, dbn, dbd);
     else
         k_pcg_dir_u0<TG, false><<<nb, RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, gm0, u0, hdt,
-                                                   pap_out ? partial : nullptr);
+                                                   pap_out ? partial : nullptr, dbn, dbd);
     if (pap_out) k_finalize<<<1, RT, 0, st>>>(partial, nb, pap_out);
 }
 
 void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
                        float b, long long N, bool init, const float *gm0, float *u0, float hdt, double *partial,
-                       double *pap_out, cudaStream_t st, Profiler *prof) {
-    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, partial, pap_out, st, prof);
+                       double *pap_out, cudaStream_t st, Profiler *prof, const double *dbn, const double *dbd) {
+    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, partial, pap_out, st, prof, dbn, dbd);
 }
 void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, const double *rsum, const float *Az,
                        float b, long long N, bool init, const __half *gm0, float *u0, float hdt, double *partial,
-                       double *pap_out, cudaStream_t st, Profiler *prof) {
-    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, partial, pap_out, st, prof);
+                       double *pap_out, cudaStream_t st, Profiler *prof, const double *dbn, const double *dbd) {
+    pcg_dir_u0(p, Ap, z, r, rsum, Az, b, N, init, gm0, u0, hdt, partial, pap_out, st, prof, dbn, dbd);
 }
 
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
