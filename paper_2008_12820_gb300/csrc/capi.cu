@@ -20,6 +20,8 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "claire.h"
 #include "claire_internal.cuh"
 
@@ -758,8 +760,18 @@ struct claire_ctx {
 };
 
 // -------------------------------------------------------------- helpers ----
+// NVTX range for an external profiler's timeline (named after the ABI call
+// or the solver phase); costs a few host instructions when no tool listens
+struct Nvtx {
+    explicit Nvtx(const char *name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+    Nvtx(const Nvtx &) = delete;
+    Nvtx &operator=(const Nvtx &) = delete;
+};
+
 #define API_BEGIN(ctx)                                                        \
     if (!(ctx)) return CLAIRE_ERR_ARG;                                        \
+    Nvtx nvtx_call_(__func__);                                                \
     try {
 #define API_END(ctx)                                                          \
     }                                                                         \
@@ -1182,6 +1194,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
     ctx->gm0_valid = false;  // grad m0 is computed once per solve
     double J = 0;
     {
+        Nvtx nv("gradient");
         EvTimer t(st, &rep.t_grad_ms);
         ctx->spectral(OP_A, v, Av, nullptr);
         ctx->gradient(v, g, &J, nullptr, Av);
@@ -1202,6 +1215,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         // ---- PCG on H x = -g, x0 = 0
         double t_pcg = 0;
         {
+            Nvtx nv("pcg");
             EvTimer tp(st, &t_pcg);
             CK(cudaMemsetAsync(x, 0, n3 * sizeof(float), st));
             CK(cudaMemsetAsync(Ax, 0, n3 * sizeof(float), st));
@@ -1212,6 +1226,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             int it = 0;
             // preconditioner z = M r; Az = beta*A z (NULL: the recurrence holds)
             auto apply_pc = [&]() -> const float * {
+                Nvtx nv("precond");
                 EvTimer t(st, &rep.t_pc_ms);
                 rep.n_precond++;
                 if (o.precond == CLAIRE_PC_INVA) {
@@ -1251,6 +1266,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                 launch_dot(r, z, n3, ctx->partial, ctx->dres + rz, st, &ctx->prof);
                 while (it < maxit) {
                     {
+                        Nvtx nv("hess_matvec");
                         EvTimer t(st, &rep.t_hess_ms);
                         ctx->matvec(p, q, true);
                     }
@@ -1295,6 +1311,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         double alpha = 1.0;
         bool ok = false;
         {
+            Nvtx nv("line_search");
             EvTimer t(st, &rep.t_obj_ms);
             for (int ls = 0; ls <= o.max_ls; ++ls) {
                 launch_axpby(vn, 1.f, v, (float)alpha, x, n3, st, &ctx->prof);
@@ -1320,6 +1337,7 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
         if (ctx->keeps_trial()) ctx->adopt_trial();
         ++k;
         {
+            Nvtx nv("gradient");
             EvTimer t(st, &rep.t_grad_ms);
             ctx->gradient(v, g, &J, nullptr, Av, ctx->keeps_trial());
         }
