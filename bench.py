@@ -72,6 +72,12 @@ KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3, 
           "deriv": "k_deriv_x3, k_deriv_strided"}
 
 
+# the transport and transform classes (every one of them is asked to reach
+# 60% of the HBM peak); the others are streaming vector work and reductions
+TRANSPORT_FFT = ("footpoint", "state", "adjoint", "incstate", "incadj", "fft_r2c", "fft_c2c", "fft_mul",
+                 "fft_c2r", "deriv")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -83,6 +89,8 @@ def parse():
                     help="fp16: stored state / adjoint trajectories in FP16 (FP32 arithmetic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the InvH0 / 2LInvH0 solves and the batched form in the default line")
     ap.add_argument("--no-fft-reference", action="store_true",
                     help="skip the cuFFT reference point (profiling captures of the library's kernels)")
     ap.add_argument("--grid", type=int, default=0,
@@ -287,8 +295,11 @@ def run_ours(args):
     nl, kms, kby = prof[dom]
     achieved = (kby / nl) / ((kms / nl) * 1e-3) / 1e9 if nl else 0.0
     breakdown = {k: {"launches": n_, "ms_per_step": round(t_, 4),
-                     "GBps": round(b_ / (t_ * 1e-3) / 1e9, 1) if t_ > 0 else None}
+                     "GBps": round(b_ / (t_ * 1e-3) / 1e9, 1) if t_ > 0 else None,
+                     "frac": round(b_ / (t_ * 1e-3) / 1e9 / peak, 4) if t_ > 0 else None}
                  for k, (n_, t_, b_) in prof.items() if n_}
+    tf = {k: e["frac"] for k, e in breakdown.items() if k in TRANSPORT_FFT and e["frac"] is not None}
+    min_tf = min(tf, key=tf.get) if tf else None
     roofline = {"bound": "hbm", "kernel": dom, "kernels": KNAMES[dom],
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
@@ -313,10 +324,15 @@ def run_ours(args):
                   "t_grad_ms": round(rep.t_grad_ms, 3), "t_pc_ms": round(rep.t_pc_ms, 3),
                   "t_obj_ms": round(rep.t_obj_ms, 3)},
         "roofline": roofline, "kernel_breakdown": breakdown,
+        "min_frac_transport_fft": {"class": min_tf, "frac": tf.get(min_tf)} if min_tf else None,
         "gpu_launches": int(launches), "clocks": clk,
     }
     if fft_ref is not None:
         out["fft_reference"] = fft_ref
+
+    # ---- the same solve with the paper's H0-based preconditioners ---------
+    if not args.no_extra:
+        out["precond_solves"] = precond_solves(reg, v, stream)
 
     # ---- end to end through the C ABI with host buffers --------------------
     # claire_solve_host: images and initial v from page-locked host memory,
@@ -348,13 +364,45 @@ def run_ours(args):
 
     # ---- CPU baseline (FP64 oracle) and error vs FP64, rank 0 at N = 1 ------
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        err, t_or = error_vs_oracle(claire, synth, args.precision)
         out["cpu_baseline"] = cpu_baseline_sample()
-        out["err_vs_fp64"] = error_vs_oracle(claire, synth, args.precision)
+        out["cpu_baseline"].update(t_or)
+        out["err_vs_fp64"] = err
     reg.close()
+    # ---- the batched form (16 pairs of uneven grids), rank 0 at N = 1 ------
+    if rank == 0 and ws == 1 and not args.no_extra:
+        b = run_batch(args, as_extra=True)
+        out["batch16"] = {k: b[k] for k in ("value", "unit", "ms_per_step", "one_by_one", "batch_speedup",
+                                            "same_results_as_one_by_one", "gpu_launches")}
+        out["batch16"]["config"] = b["config"]["workload"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def precond_solves(reg, v, stream, reps=3):
+    """The benchmark's solve with the InvH0 and two-level InvH0 preconditioners
+    (Section 3 "Preconditioning", Algorithm 2; inner tolerance 1e-3 times the
+    forcing term): device time per solve, PCG and inner iteration counts."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name in ("invH0", "2LinvH0"):
+        v.zero_()
+        reg.solve(v, precond=name)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            v.zero_()
+            rep = reg.solve(v, precond=name)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"solve_ms": round(ms, 3), "n_gn": rep.n_gn, "n_pcg": rep.n_pcg, "n_inner": rep.n_inner,
+                     "grel": rep.grel, "J": rep.J, "t_pc_ms": round(rep.t_pc_ms, 3),
+                     "t_hess_ms": round(rep.t_hess_ms, 3)}
+    return out
 
 
 def fft_reference(reg, r, beta, gamma, stream, reps=20):
@@ -456,8 +504,13 @@ def error_vs_oracle(claire, synth, precision="fp32"):
     v = (0.5 * w["v_true"]).astype(np.float32)
     vt = synth.smooth_direction((n, n, n), 7)
     P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
+    t0 = time.perf_counter()
     go, Jo = P.gradient(v)
+    t1 = time.perf_counter()
     Ho = P.matvec(vt)
+    t2 = time.perf_counter()
+    t_or = {"oracle_gradient_s_128": round(t1 - t0, 3), "oracle_matvec_s_128": round(t2 - t1, 3),
+            "oracle_matvec_gvoxel_s_128": round(n ** 3 / (t2 - t1) / 1e9, 6)}
     with claire.Registration((n, n, n), w["nt"], w["beta"], w["gamma"], precision=precision) as reg:
         reg.set_images(torch.from_numpy(w["m0"]).cuda(), torch.from_numpy(w["m1"]).cuda())
         g, J = reg.gradient(torch.from_numpy(v).cuda())
@@ -477,11 +530,11 @@ def error_vs_oracle(claire, synth, precision="fp32"):
         eb = sum(float(np.sum(np.abs(np.fft.fftn(b[c])) ** 2 * wgt)) for c in range(3))
         return (ea / eb) ** 0.5
 
-    return {"grid": [n, n, n], "storage": precision, "gradient": rel(g, go), "hess_matvec": rel(H, Ho),
-            "objective": abs(J - Jo) / abs(Jo), "gradient_Hm1": rel_hm1(g, go),
-            "hess_matvec_Hm1": rel_hm1(H, Ho),
-            "note": "L2 errors of fields containing beta*A of a smooth field sit at the FP32 "
-                    "noise floor of the forward FFT amplified by |k|^2; H^-1 norm alongside"}
+    return ({"grid": [n, n, n], "storage": precision, "gradient": rel(g, go), "hess_matvec": rel(H, Ho),
+             "objective": abs(J - Jo) / abs(Jo), "gradient_Hm1": rel_hm1(g, go),
+             "hess_matvec_Hm1": rel_hm1(H, Ho),
+             "note": "L2 errors of fields containing beta*A of a smooth field sit at the FP32 "
+                     "noise floor of the forward FFT amplified by |k|^2; H^-1 norm alongside"}, t_or)
 
 
 # ---------------------------------------------------------------------------
@@ -512,8 +565,9 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "grid": [256, 256, 256], "nt": 4, "beta": 1e-2,
-                   "gamma": 1.0, "precond": "InvA", "eps_n": 5e-2},
+        "config": {"workload": WORKLOAD_DESC, "grid": [n, n, n], "sample_of_grid": [256, 256, 256], "nt": 4,
+                   "beta": 1e-2, "gamma": 1.0, "precond": "InvA", "eps_n": 5e-2, "storage": "fp64",
+                   "parallelism": f"host cores ({cores} OpenMP threads)"},
         "cpu_baseline": {"value": round(value, 7), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"full FP64 GN-Krylov solve of the same generator on a "
                                    f"{n}^3 grid ({rep.n_gn} GN, {rep.n_pcg} PCG); voxels/s"},
@@ -523,15 +577,18 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, as_extra=False):
     """The batched form: 16 blob pairs on grids drawn from {64, 96, 128, 160}^3
     solved together (claire_solve_batch: a stream and host thread per pair)
-    against the same 16 solved one by one; one step = all 16 solves."""
+    against the same 16 solved one by one; one step = all 16 solves.  With
+    as_extra the result is returned (a key of the default line) instead of
+    printed."""
     import numpy as np
     import torch
 
     import __graft_entry__
-    torch.cuda.set_device(0)
+    if not as_extra:
+        torch.cuda.set_device(0)
     __graft_entry__.build()
     from paper_2008_12820_gb300 import claire, synth
 
@@ -572,12 +629,13 @@ def run_batch(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.steps, reps
 
-    clocks = ClockSampler(0)
-    clocks.start()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if not as_extra:
+        clocks.start()
     launches0 = sum(r.launch_count() for r in regs)
     ms_b, reps_b = timed(batch_step)
     launches = (sum(r.launch_count() for r in regs) - launches0) // (args.steps + args.warmup)
-    clk = clocks.stop()
+    clk = clocks.stop() if not as_extra else None
     ms_s, reps_s = timed(seq_step)
     same = all(a.n_pcg == b.n_pcg and a.J == b.J for a, b in zip(reps_b, reps_s))
     sizes = sorted({w["shape"][0] for w in ws})
@@ -598,6 +656,8 @@ def run_batch(args):
     }
     for r in regs:
         r.close()
+    if as_extra:
+        return out
     print(json.dumps(out), flush=True)
 
 

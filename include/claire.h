@@ -355,7 +355,9 @@ int claire_set_workspace_limit(size_t bytes);
  * sizes, beta <= 0, gamma < 0 or NULL pointers return CLAIRE_ERR_ARG with a
  * message in claire_last_error(NULL).  r and s are device float[3][N] and
  * may be equal.  The first call on each device looks up the array's device
- * address (so make it before any stream capture).  All calls on a device share
+ * address (so make it before any stream capture) and keeps it for the life of
+ * the process: a device reset (cudaDeviceReset) after that first call is not
+ * supported by this entry point.  All calls on a device share
  * the array: calls that overlap on the GPU race and must be serialized by the
  * caller.  Returns as soon as the work is enqueued. */
 int claire_precond_noalloc(int nx, int ny, int nz, double beta, double gamma, const float *r,

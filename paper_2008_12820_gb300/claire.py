@@ -121,13 +121,19 @@ def load(path: str = LIB_PATH):
     return L
 
 
-def _ptr(t):
+def _ptr(t, shape=None, name="field"):
+    """Device pointer of a contiguous float32 CUDA tensor.  With ``shape``, the
+    tensor's shape must equal it: the C side reads and writes exactly that many
+    floats through the pointer, so a wrong shape is rejected here, before any
+    pointer crosses into the library."""
     if t is None:
         return None
     if not isinstance(t, torch.Tensor):
-        raise TypeError("expected a torch tensor")
+        raise TypeError(f"{name}: expected a torch tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
     if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
-        raise ValueError("fields must be contiguous float32 CUDA tensors")
+        raise ValueError(f"{name}: fields must be contiguous float32 CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -179,10 +185,14 @@ def set_workspace_limit(nbytes):
 def precond_noalloc(r, s, beta, gamma, stream=None):
     """s = (beta*A)^{-1} r through claire_precond_noalloc (no device allocation
     inside the library); r, s: float32 CUDA tensors [3, nx, ny, nz]."""
+    if not isinstance(r, torch.Tensor) or r.dim() != 4 or r.shape[0] != 3:
+        raise ValueError("precond_noalloc: r must be a [3, nx, ny, nz] tensor")
+    shape = tuple(r.shape)
+    pr, ps = _ptr(r, shape, "r"), _ptr(s, shape, "s")
     L = load()
     st = stream if stream is not None else torch.cuda.current_stream()
-    nx, ny, nz = (int(x) for x in r.shape[1:])
-    rc = L.claire_precond_noalloc(nx, ny, nz, float(beta), float(gamma), _ptr(r), _ptr(s),
+    nx, ny, nz = (int(x) for x in shape[1:])
+    rc = L.claire_precond_noalloc(nx, ny, nz, float(beta), float(gamma), pr, ps,
                                   ctypes.c_void_p(st.cuda_stream))
     if rc != CLAIRE_OK:
         raise ClaireError(rc, L.claire_last_error(None).decode())
@@ -200,8 +210,9 @@ def solve_batch(regs, vs, check=True, **opts):
     if isinstance(opts.get("precond"), str):
         opts["precond"] = Registration.PRECOND[opts["precond"]]
     o = Registration.default_opts(**opts)
+    ptrs = [r._vec(v, "v") for r, v in zip(regs, vs)]
     hs = (ctypes.c_void_p * n)(*[r.handle for r in regs])
-    ps = (ctypes.c_void_p * n)(*[ctypes.c_void_p(v.data_ptr()) for v in vs])
+    ps = (ctypes.c_void_p * n)(*ptrs)
     reps = (SolveReport * n)()
     rc = load().claire_solve_batch(hs, ps, n, ctypes.byref(o), reps)
     if check and rc != CLAIRE_OK:
@@ -266,6 +277,14 @@ class Registration:
     def _new(self, *lead):
         return torch.empty(lead + self.shape, device="cuda", dtype=torch.float32)
 
+    def _vec(self, t, name="vector field"):
+        """pointer of a [3, nx, ny, nz] field of this grid (None passes)"""
+        return _ptr(t, (3,) + self.shape, name)
+
+    def _scal(self, t, name="scalar field"):
+        """pointer of an [nx, ny, nz] field of this grid (None passes)"""
+        return _ptr(t, self.shape, name)
+
     # ---- API ----
     def set_params(self, beta, gamma):
         self._c("claire_set_params", float(beta), float(gamma))
@@ -277,79 +296,91 @@ class Registration:
                 1 if deriv == "fd8" else 0)
 
     def set_images(self, m0, m1):
-        self._c("claire_set_images", _ptr(m0), _ptr(m1))
+        self._c("claire_set_images", self._scal(m0, "m0"), self._scal(m1, "m1"))
 
     def forward(self, v, want_mismatch=True):
+        pv = self._vec(v, "v")
         m = self._new()
         mis = ctypes.c_double(0)
-        self._c("claire_forward", _ptr(v), _ptr(m), ctypes.byref(mis) if want_mismatch else None)
+        self._c("claire_forward", pv, self._scal(m, "m"), ctypes.byref(mis) if want_mismatch else None)
         return m, mis.value
 
     def mismatch_forward(self, v, checkpoint_stride=2, m_final=None):
         """(m(1), mismatch) keeping the state every checkpoint_stride steps."""
+        pv = self._vec(v, "v")
         m = m_final if m_final is not None else self._new()
         mis = ctypes.c_double(0)
-        self._c("claire_mismatch_forward", _ptr(v), _ptr(m), ctypes.byref(mis), int(checkpoint_stride))
+        self._c("claire_mismatch_forward", pv, self._scal(m, "m_final"), ctypes.byref(mis),
+                int(checkpoint_stride))
         return m, mis.value
 
     def mismatch_backward(self, grad_mismatch, grad_m_final=None, out=None):
         """Euclidean gradient w.r.t. v of grad_mismatch * mismatch +
         <grad_m_final, m(1)> at the last mismatch_forward."""
+        pg = self._scal(grad_m_final, "grad_m_final")
         g = out if out is not None else self._new(3)
-        self._c("claire_mismatch_backward", float(grad_mismatch), _ptr(grad_m_final), _ptr(g))
+        self._c("claire_mismatch_backward", float(grad_mismatch), pg, self._vec(g, "out"))
         return g
 
     def objective(self, v):
         J, mis = ctypes.c_double(0), ctypes.c_double(0)
-        self._c("claire_objective", _ptr(v), ctypes.byref(J), ctypes.byref(mis))
+        self._c("claire_objective", self._vec(v, "v"), ctypes.byref(J), ctypes.byref(mis))
         return J.value, mis.value
 
     def linearize(self, v):
-        self._c("claire_linearize", _ptr(v))
+        self._c("claire_linearize", self._vec(v, "v"))
 
     def gradient(self, v, out=None, want_objective=True):
+        pv = self._vec(v, "v")
         g = out if out is not None else self._new(3)
         J = ctypes.c_double(0)
-        self._c("claire_gradient", _ptr(v), _ptr(g), ctypes.byref(J) if want_objective else None)
+        self._c("claire_gradient", pv, self._vec(g, "out"), ctypes.byref(J) if want_objective else None)
         return g, J.value
 
     def hess_matvec(self, v, vt, out=None):
+        pv, pvt = self._vec(v, "v"), self._vec(vt, "vt")
         Hv = out if out is not None else self._new(3)
-        self._c("claire_hess_matvec", _ptr(v), _ptr(vt), _ptr(Hv))
+        self._c("claire_hess_matvec", pv, pvt, self._vec(Hv, "out"))
         return Hv
 
     def precond(self, r, out=None):
+        pr = self._vec(r, "r")
         s = out if out is not None else self._new(3)
-        self._c("claire_precond", _ptr(r), _ptr(s))
+        self._c("claire_precond", pr, self._vec(s, "out"))
         return s
 
     def precond_h0(self, r, out=None, tol=1e-3, maxit=500, two_level=False):
         """InvH0 or its two-level variant: (s, inner iterations) with
         s = H0^{-1} r at the cached linearization."""
+        pr = self._vec(r, "r")
         s = out if out is not None else self._new(3)
         it = ctypes.c_int(0)
-        self._c("claire_precond_h0", _ptr(r), _ptr(s), float(tol), int(maxit), int(bool(two_level)),
+        self._c("claire_precond_h0", pr, self._vec(s, "out"), float(tol), int(maxit), int(bool(two_level)),
                 ctypes.byref(it))
         return s, it.value
 
     def grad(self, f):
+        pf = self._scal(f, "f")
         g = self._new(3)
-        self._c("claire_grad", _ptr(f), _ptr(g))
+        self._c("claire_grad", pf, self._vec(g))
         return g
 
     def div(self, v):
+        pv = self._vec(v, "v")
         d = self._new()
-        self._c("claire_div", _ptr(v), _ptr(d))
+        self._c("claire_div", pv, self._scal(d))
         return d
 
     def apply_A(self, v):
+        pv = self._vec(v, "v")
         out = self._new(3)
-        self._c("claire_apply_A", _ptr(v), _ptr(out))
+        self._c("claire_apply_A", pv, self._vec(out))
         return out
 
     def interp(self, f, disp):
+        pf, pd = self._scal(f, "f"), self._vec(disp, "disp")
         out = self._new()
-        self._c("claire_interp", _ptr(f), _ptr(disp), _ptr(out))
+        self._c("claire_interp", pf, pd, self._scal(out))
         return out
 
     def field(self, name, j=0):
@@ -371,11 +402,12 @@ class Registration:
     def solve(self, v_inout, check=True, **opts):
         """opts: max_gn, max_pcg, fixed_pcg, eps_n, armijo_c1, max_ls,
         precond ("invA" | "invH0" | "2LinvH0" or the enum value), eps_h0, max_inner."""
+        pv = self._vec(v_inout, "v")
         if isinstance(opts.get("precond"), str):
             opts["precond"] = self.PRECOND[opts["precond"]]
         o = self.default_opts(**opts)
         rep = SolveReport()
-        rc = load().claire_solve(self._h, _ptr(v_inout), ctypes.byref(o), ctypes.byref(rep))
+        rc = load().claire_solve(self._h, pv, ctypes.byref(o), ctypes.byref(rep))
         if check and rc not in (CLAIRE_OK,):
             _check(self._h, rc)
         return Report(**rep.as_dict())
@@ -384,13 +416,14 @@ class Registration:
         """set_images + solve with host (CPU) tensors, the copies overlapped
         with the computation (pin the tensors for the overlap); the result
         lands in v_out (default: v_in) before the call returns."""
-        if isinstance(opts.get("precond"), str):
-            opts["precond"] = self.PRECOND[opts["precond"]]
         if v_out is None:
             v_out = v_in
-        n = self.shape[0] * self.shape[1] * self.shape[2]
-        if m0.numel() != n or m1.numel() != n or v_in.numel() != 3 * n or v_out.numel() != 3 * n:
-            raise ValueError("solve_host: m0, m1 need N values, v_in and v_out 3N")
+        for t, want, nm in ((m0, self.shape, "m0"), (m1, self.shape, "m1"), (v_in, (3,) + self.shape, "v_in"),
+                            (v_out, (3,) + self.shape, "v_out")):
+            if not isinstance(t, torch.Tensor) or tuple(t.shape) != want:
+                raise ValueError(f"solve_host: {nm} must have shape {want}")
+        if isinstance(opts.get("precond"), str):
+            opts["precond"] = self.PRECOND[opts["precond"]]
         o = self.default_opts(**opts)
         rep = SolveReport()
         rc = load().claire_solve_host(self._h, _host_ptr(m0), _host_ptr(m1), _host_ptr(v_in), _host_ptr(v_out),
@@ -408,7 +441,7 @@ class Registration:
         o = self.default_opts(**opts)
         rep = SolveReport()
         lev = ctypes.c_int(0)
-        rc = load().claire_solve_continuation(self._h, _ptr(v_inout), float(beta_target),
+        rc = load().claire_solve_continuation(self._h, self._vec(v_inout, "v"), float(beta_target),
                                               float(beta_start), float(factor), ctypes.byref(o),
                                               ctypes.byref(rep), ctypes.byref(lev))
         if check and rc != CLAIRE_OK:

@@ -83,6 +83,11 @@ namespace claire {
 // message returned by claire_last_error(NULL) on this thread
 void set_thread_error(const std::string &msg) { g_create_error = msg; }
 
+void attr_failed(const char *kernel, cudaError_t e) {
+    throw Error(CLAIRE_ERR_CUDA, std::string("cudaFuncSetAttribute (dynamic shared memory) of ") + kernel + ": " +
+                                     cudaGetErrorString(e));
+}
+
 int Profiler::begin(int cls, double bytes, cudaStream_t st) {
     if (!on) return -1;
     if (used == recs.size()) {

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include <string>
 #include <vector>
 
@@ -209,6 +211,42 @@ void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, cons
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
                      cudaStream_t st, Profiler *prof);
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
+
+// ------------------------------------------------- kernel attributes ----
+// Reports a failed cudaFuncSetAttribute as a library error with the kernel's
+// name (thrown to the ABI call that launched it; defined in capi.cu).
+[[noreturn]] void attr_failed(const char *kernel, cudaError_t e);
+
+// A kernel's dynamic shared-memory limit above the 48 KB default, raised per
+// device: the attribute belongs to the device's context, so a context on
+// another device needs its own call.  The largest limit set so far is kept
+// per device (kernels with a runtime-sized plan ask for different sizes), so
+// steady-state launches make no runtime call.  Thread-safe; a failure is
+// reported with the kernel's name instead of surfacing later as a failed
+// launch.
+struct SmemAttr {
+    static constexpr int kDevices = 64;
+    std::atomic<int> set[kDevices] = {};  // bytes set so far, per device index
+    template <typename K>
+    void ensure(K kernel, int bytes, const char *name) {
+        if (bytes <= 48 * 1024) return;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) attr_failed(name, e);
+        std::atomic<int> *slot = dev >= 0 && dev < kDevices ? &set[dev] : nullptr;
+        if (slot && slot->load(std::memory_order_acquire) >= bytes) return;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            attr_failed(name, e);
+        }
+        if (slot) {
+            int cur = slot->load(std::memory_order_acquire);
+            while (cur < bytes && !slot->compare_exchange_weak(cur, bytes, std::memory_order_acq_rel)) {
+            }
+        }
+    }
+};
 
 // ------------------------------------------------------------ profiler ----
 // Counts kernel launches and, when on, brackets each launch group with CUDA

@@ -253,7 +253,7 @@ void r2c_l(const Dims &d, const FftPlan &p, const TI *in, float2 *out, long long
            cudaStream_t st) {
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const long long blocks = (nlines + 2 * L - 1) / (2 * L);
-    set_smem(k_r2c_x3<N, L, TI>, smem);
+    set_smem<k_r2c_x3<N, L, TI>>(smem);
     k_r2c_x3<N, L, TI><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3);
 }
 
@@ -287,7 +287,7 @@ template <int N, int TK>
 void c2c_t(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
     const size_t smem = 2 * (size_t)d.n2 * TK * sizeof(float2);
     dim3 grid((d.h3 + TK - 1) / TK, ncomp * d.n1);
-    set_smem(k_c2c_x2<N, TK>, smem);
+    set_smem<k_c2c_x2<N, TK>>(smem);
     k_c2c_x2<N, TK><<<grid, kThreads, smem, st>>>(data, p, d.h3, d.p3, s);
 }
 
@@ -319,7 +319,7 @@ void mul_t(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, 
     const size_t smem = (size_t)(NB + 1) * d.n1 * TK * sizeof(float2);
     const long long cstride = (long long)d.n1 * d.n2 * d.p3;
     dim3 grid((d.h3 + TK - 1) / TK, d.n2);
-    set_smem(k_mul_x1<N, TK, OP>, smem);
+    set_smem<k_mul_x1<N, TK, OP>>(smem);
     k_mul_x1<N, TK, OP><<<grid, kThreads, smem, st>>>(data, p, d.n2, d.n3, d.h3, d.p3, cstride, sp);
 }
 
@@ -354,11 +354,11 @@ void c2r_l(const Dims &d, const FftPlan &p, const float2 *in, TO *out, const flo
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const long long blocks = (nlines + 2 * L - 1) / (2 * L);
     if (add) {
-        set_smem(k_c2r_x3<N, L, EPI_ADD, TO>, smem);
+        set_smem<k_c2r_x3<N, L, EPI_ADD, TO>>(smem);
         k_c2r_x3<N, L, EPI_ADD, TO><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines, p,
                                                                               d.h3, d.p3);
     } else {
-        set_smem(k_c2r_x3<N, L, EPI_STORE, TO>, smem);
+        set_smem<k_c2r_x3<N, L, EPI_STORE, TO>>(smem);
         k_c2r_x3<N, L, EPI_STORE, TO><<<(unsigned)blocks, kThreads, smem, st>>>(in, out, add, nlines,
                                                                                 p, d.h3, d.p3);
     }

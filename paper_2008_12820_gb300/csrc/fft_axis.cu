@@ -128,12 +128,12 @@ void deriv_x3_l(const Dims &d, const FftPlan &p, const float *in, TO *out, const
     const unsigned blocks = (unsigned)((nlines + 2 * L - 1) / (2 * L));
     if constexpr (std::is_same<TO, float>::value) {
         if (add) {
-            set_smem(k_deriv_x3<N, L, EPI_ADD, TO>, smem);
+            set_smem<k_deriv_x3<N, L, EPI_ADD, TO>>(smem);
             k_deriv_x3<N, L, EPI_ADD, TO><<<blocks, kThreads, smem, st>>>(in, out, add, nlines, p);
             return;
         }
     }
-    set_smem(k_deriv_x3<N, L, EPI_STORE, TO>, smem);
+    set_smem<k_deriv_x3<N, L, EPI_STORE, TO>>(smem);
     k_deriv_x3<N, L, EPI_STORE, TO><<<blocks, kThreads, smem, st>>>(in, out, add, nlines, p);
 }
 
@@ -157,12 +157,12 @@ void deriv_strided_t(const Dims &d, const FftPlan &p, int n, const float *in, TO
     const dim3 grid((d.n3 + 2 * TKC - 1) / (2 * TKC), nplanes);
     if constexpr (std::is_same<TO, float>::value) {
         if (add) {
-            set_smem(k_deriv_strided<N, TKC, EPI_ADD, TO>, smem);
+            set_smem<k_deriv_strided<N, TKC, EPI_ADD, TO>>(smem);
             k_deriv_strided<N, TKC, EPI_ADD, TO><<<grid, kThreads, smem, st>>>(in, out, add, d.n3, estride, pstride, p);
             return;
         }
     }
-    set_smem(k_deriv_strided<N, TKC, EPI_STORE, TO>, smem);
+    set_smem<k_deriv_strided<N, TKC, EPI_STORE, TO>>(smem);
     k_deriv_strided<N, TKC, EPI_STORE, TO><<<grid, kThreads, smem, st>>>(in, out, add, d.n3, estride, pstride, p);
 }
 

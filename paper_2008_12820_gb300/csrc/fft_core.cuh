@@ -268,10 +268,12 @@ __device__ __forceinline__ float wavenumber_d1(int i, int n) {
 
 // ------------------------------------------------------- launch helpers --
 
-template <typename K>
-void set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// dynamic shared-memory limit of a transform kernel: one SmemAttr per kernel
+// instantiation (set per device, failures reported with a clear message)
+template <auto K>
+void set_smem(size_t bytes) {
+    static SmemAttr a;
+    a.ensure(K, (int)bytes, "pencil FFT pass");
 }
 
 // lines per block of the x3 passes and column tile of the strided passes,

@@ -13,7 +13,10 @@
 // Host code sees those arrays only through host-side stand-ins; their device
 // addresses come from cudaGetSymbolAddress, looked up once per device with
 // that device current (the first call on a device does it, so that first
-// call should come before any stream capture).  All calls on a device share
+// call should come before any stream capture).  The addresses are kept for
+// the life of the process, so a device reset after that first call is not
+// supported (the module's arrays could then sit elsewhere).  All calls on a
+// device share
 // the arrays: calls whose work overlaps on the GPU (different streams, or
 // several host threads) race on them and must be serialized by the caller.
 // The arrays keep the last call's contents; nothing in them needs to start at
@@ -21,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <exception>
 #include <mutex>
 #include <string>
 
@@ -139,7 +143,11 @@ extern "C" int claire_precond_noalloc(int nx, int ny, int nz, double beta, doubl
         ax[a] = axis_plan(ns[a], tw);
     }
     const SpecParams sp{(float)beta, (float)gamma, (float)(1.0 / (double)d.N)};
-    spectral_apply(d, ax, OP_AINV, sp, r, s, nullptr, sc.spec, st, nullptr);
+    try {
+        spectral_apply(d, ax, OP_AINV, sp, r, s, nullptr, sc.spec, st, nullptr);
+    } catch (const std::exception &ex) {
+        return fail(CLAIRE_ERR_CUDA, std::string("claire_precond_noalloc: ") + ex.what());
+    }
     e = cudaPeekAtLastError();
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -19,15 +19,13 @@
 // number (no loss of precision at large grid indices).
 //
 // The time-step kernels stage the source field in shared-memory halo boxes
-// (k_sl_pipe); the foot-point kernel gathers v from global memory, one
-// thread per voxel, a block covering 32 consecutive x3 points of 8 x2 rows.
-// (A shared-memory box version of the foot points measured no faster: its
-// three 64-tap sums per voxel load the shared-memory pipe as much as the L1
-// gathers do, and the box copies come on top.)
+// (k_sl_pipe).  The cubic foot points (k_footpoints_box) walk the same tiles
+// and stage the three components of v in shared-memory boxes sized by each
+// tile's own predictor floor range; the trilinear foot points
+// (k_footpoints) gather v from global memory, one thread per voxel.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <type_traits>
 
 #include "claire_internal.cuh"
@@ -942,13 +940,9 @@ inline int pipe_blocks(const Dims &d, int per_sm) {
 template <int MODE, int ORDER, typename TS, typename TG, bool FULL>
 void launch_pipe_f(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
-    // the shared-memory limit is set once per instantiation, so that launches
-    // being captured into a CUDA graph make no other runtime call
-    static std::once_flag attr;
-    std::call_once(attr, [] {
-        cudaFuncSetAttribute(k_sl_pipe<MODE, ORDER, TS, TG, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * BOX_FLOATS * sizeof(float)));
-    });
+    // the shared-memory limit is set once per instantiation and device
+    static SmemAttr attr;
+    attr.ensure(k_sl_pipe<MODE, ORDER, TS, TG, FULL>, (int)smem, "k_sl_pipe");
     k_sl_pipe<MODE, ORDER, TS, TG, FULL><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(
         a, d, range, chunk_ok(d, a.src));
 }
@@ -1058,12 +1052,8 @@ void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, floa
         nblocks = (long long)grid.x * grid.y * grid.z;
     } else {
         const size_t smem = 3 * BOX_FLOATS * sizeof(float);
-        // set once, so that launches being captured make no other runtime call
-        static std::once_flag attr;
-        std::call_once(attr, [] {
-            cudaFuncSetAttribute(k_footpoints_box, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(3 * BOX_FLOATS * sizeof(float)));
-        });
+        static SmemAttr attr;  // once per device
+        attr.ensure(k_footpoints_box, (int)smem, "k_footpoints_box");
         const int grid = pipe_blocks(d, FP_OCC);
         k_footpoints_box<<<grid, dim3(PT3, PT2), smem, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, chunk_ok(d, v),
                                                              part);

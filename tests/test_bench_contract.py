@@ -27,6 +27,9 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 0
     assert d["value"] > 0 and d["higher_is_better"] is True and d["unit"] == "Gvoxel/s"
     assert "workload" in d["config"]
+    # the config names the grid the oracle actually solved
+    n = d["config"]["grid"][0]
+    assert d["config"]["grid"] == [n, n, n] and f"{n}^3" in d["cpu_baseline"]["sample"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e = d["e2e"]

@@ -56,6 +56,29 @@ def test_noalloc_matches_precond_on_two_calls_in_a_row(C):
         assert rel(s, ref) < 1e-5, (shape, rel(s, ref))
 
 
+def test_noalloc_in_place_and_allocates_nothing_when_warm(C):
+    """s may equal r (in place), and a call after the first one on the device
+    changes the device's free memory by nothing (no allocation inside)."""
+    beta, gamma = 1e-2, 1.0
+    shape = (40, 36, 30)
+    g = torch.Generator(device="cpu").manual_seed(3)
+    r = torch.randn((3,) + shape, generator=g).cuda()
+    with C.Registration(shape, 4, beta, gamma) as reg:
+        ref = reg.precond(r)
+    t = r.clone()
+    C.precond_noalloc(t, t, beta, gamma)   # warm: the first call on the device sets up
+    torch.cuda.synchronize()
+    assert rel(t, ref) < 1e-5, rel(t, ref)
+    t = r.clone()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    C.precond_noalloc(t, t, beta, gamma)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    assert rel(t, ref) < 1e-5, rel(t, ref)
+
+
 def test_noalloc_rejects_oversized_grid(C):
     r = torch.zeros((3, 128, 128, 128), device="cuda")
     with pytest.raises(C.ClaireError) as e:
