@@ -333,6 +333,8 @@ def run_ours(args):
     # ---- the same solve with the paper's H0-based preconditioners ---------
     if not args.no_extra:
         out["precond_solves"] = precond_solves(reg, v, stream)
+        if args.workload == "blob256":
+            out["large_displacement"] = large_displacement(claire, synth, args, stream)
 
     # ---- end to end through the C ABI with host buffers --------------------
     # claire_solve_host: images and initial v from page-locked host memory,
@@ -403,6 +405,44 @@ def precond_solves(reg, v, stream, reps=3):
                      "grel": rep.grel, "J": rep.J, "t_pc_ms": round(rep.t_pc_ms, 3),
                      "t_hess_ms": round(rep.t_hess_ms, 3)}
     return out
+
+
+def large_displacement(claire, synth, args, stream, reps=3):
+    """The same generator with three times the displacement (12 voxels at
+    most, up to 3 cells per time step): solve time and Hessian matvec at the
+    solution, beside the default workload's."""
+    import torch
+    w = synth.workload("blob256_d12")
+    shape = w["shape"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with claire.Registration(shape, w["nt"], w["beta"], w["gamma"], precision=args.precision) as reg:
+        reg.set_images(torch.from_numpy(w["m0"]).cuda(), torch.from_numpy(w["m1"]).cuda())
+        v = torch.zeros((3,) + shape, device="cuda")
+        reg.solve(v)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            v.zero_()
+            rep = reg.solve(v)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        reg.linearize(v)
+        vt = torch.from_numpy(synth.smooth_direction(shape, 7)).cuda()
+        Hv = torch.empty_like(vt)
+        for _ in range(3):
+            reg.hess_matvec(None, vt, out=Hv)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(20):
+            reg.hess_matvec(None, vt, out=Hv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mv = e0.elapsed_time(e1) / 20
+        vmax = float(torch.linalg.vector_norm(v, dim=0).max()) * shape[0] / (2 * 3.141592653589793)
+    return {"workload": "blob256 generator with max displacement 12 voxels (seed 1001)", "solve_ms": round(ms, 3),
+            "n_gn": rep.n_gn, "n_pcg": rep.n_pcg, "grel": rep.grel, "hess_matvec_ms": round(mv, 4),
+            "max_displacement_vox_of_solution": round(vmax, 2)}
 
 
 def fft_reference(reg, r, beta, gamma, stream, reps=20):

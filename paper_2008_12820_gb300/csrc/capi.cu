@@ -140,15 +140,16 @@ struct claire_ctx {
     float2 *spec = nullptr;
     double *partial = nullptr, *dres = nullptr;
     int *dflag = nullptr;
-    int *fpart = nullptr;  // the foot-point blocks' partial floor ranges
-    // floor ranges of the displacement fields: X-, X+, forward-only X-, interp
-    // (the X- and forward-only slots swap when a line-search trial is adopted)
-    int *rng = nullptr;
-    int off_m = 0, off_f = 12;
-    int *rng_m() { return rng + off_m; }
-    int *rng_p() { return rng + 6; }
-    int *rng_f() { return rng + off_f; }
-    int *rng_i() { return rng + 18; }
+    // box entries (one int4 per transport tile) of the displacement fields:
+    // X-, X+, forward-only X-, interp (the X- and forward-only slots swap when
+    // a line-search trial is adopted)
+    int4 *rng = nullptr;
+    long long ntiles = 0;
+    int off_m = 0, off_f = 2;
+    int4 *rng_m() { return rng + off_m * ntiles; }
+    int4 *rng_p() { return rng + 1 * ntiles; }
+    int4 *rng_f() { return rng + off_f * ntiles; }
+    int4 *rng_i() { return rng + 3 * ntiles; }
     // solver vectors, allocated on the first solve
     float *sv = nullptr;
     // state history of the line search's trial velocity (solver only): an
@@ -398,11 +399,11 @@ struct claire_ctx {
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         if (state_ready) {
-            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), fpart, st, &prof);
+            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), st, &prof);
         } else if (h16) {
             // FP32 transport; FP16 copies of m^j and of grad m^j (taken of the
             // FP32 state); m(1) and grad m(1) also kept in FP32
-            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
+            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
             wait_images();
             launch_f2h(m0, mhist_h, (long long)N, st, &prof);
             if (!gm0_valid) grad_h(m0, hist(gmhist_h, 0, 3));
@@ -418,7 +419,7 @@ struct claire_ctx {
             grad(m1f, gm1f);
             launch_f2h(gm1f, hist(gmhist_h, nt, 3), 3 * (long long)N, st, &prof);
         } else {
-            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
+            launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
             wait_images();
             CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
             for (int j = 0; j < nt; ++j)
@@ -648,7 +649,7 @@ struct claire_ctx {
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
         have_lin = false;  // the full history is not kept on this path
-        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), fpart, st, &prof);
+        launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
         div(vlin, divv);
         launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, st, &prof);
         CK(cudaMemcpyAsync(ck, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -705,7 +706,7 @@ struct claire_ctx {
     // m(1) for v into mout (N); uses fdisp, s1a, s1b; leaves the cache alone
     const float *forward(const float *v) {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
-        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, fpart, st, &prof);
+        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
         const float *src = m0;
         float *a = s1a, *b = s1b;
         for (int j = 0; j < nt; ++j) {
@@ -726,7 +727,7 @@ struct claire_ctx {
     bool keeps_trial() const { return !h16; }
     double trial_mismatch(const float *v) {
         if (h16) return mismatch_of(forward(v));
-        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, fpart, st, &prof);
+        launch_footpoints(d, nt, v, fdisp, nullptr, rng_f(), nullptr, st, &prof);
         if (!mhist_t) mhist_t = alloc_f((size_t)(nt + 1) * d.N);
         const float *src = m0;
         for (int j = 0; j < nt; ++j) {
@@ -884,8 +885,8 @@ int claire_create_ex(int nx, int ny, int nz, int nt, double beta, double gamma, 
         c->partial = (double *)c->alloc_bytes(4 * kReduceBlocks * sizeof(double));
         c->dres = (double *)c->alloc_bytes(16 * sizeof(double));
         c->dflag = (int *)c->alloc_bytes(sizeof(int));
-        c->rng = (int *)c->alloc_bytes(24 * sizeof(int));
-        c->fpart = (int *)c->alloc_bytes((size_t)footpoint_parts(c->d) * sizeof(int));
+        c->ntiles = tile_count(c->d);
+        c->rng = (int4 *)c->alloc_bytes((size_t)4 * c->ntiles * sizeof(int4));
     } catch (const Error &e) {
         g_create_error = e.msg;
         delete c;

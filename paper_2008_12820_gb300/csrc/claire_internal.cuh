@@ -84,38 +84,40 @@ void launch_grad_fd8(const Dims &d, const float *f, float *g, cudaStream_t st, P
 void launch_div_fd8(const Dims &d, const float *v, float *out, cudaStream_t st, Profiler *prof);
 
 // ------------------------------------------------------------ transport ----
-// Foot points and the per-axis [min, max] floor range of each displacement
-// field (6 ints each), which fixes the shared-memory box of the SL kernels.
+// Box entries: the SL kernels work on tiles of 32 (x3) x 8 (x2) x 4 (x1)
+// voxels, ordered x3 fastest; a displacement field comes with one int4 per
+// tile, {lo1, lo2, lo3, ok}: the smallest floor of the tile's displacements
+// per axis, and whether all its floors fit the kernels' shared-memory box.
+long long tile_count(const Dims &d);
+// Foot points and the box entries of each output (tile_count(d) int4 each).
 // Either of dispm (X-) and dispp (X+) may be null; that side is skipped.
-// part: scratch of footpoint_parts(d) ints (the blocks' partial ranges).
-void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
-                       int *range_m, int *range_p, int *part, cudaStream_t st, Profiler *prof);
-long long footpoint_parts(const Dims &d);
-void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream_t st,
-                        Profiler *prof);
-void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int *range,
+void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp, int4 *tiles_m,
+                       int4 *tiles_p, cudaStream_t st, Profiler *prof);
+// box entries of an arbitrary displacement field
+void launch_tile_ranges(const Dims &d, const float *disp, int4 *tiles, cudaStream_t st, Profiler *prof);
+void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int4 *tiles,
                    cudaStream_t st, Profiler *prof, int kclass);
 void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
-                           const int *range_p, float *cfac, cudaStream_t st, Profiler *prof);
+                           const int4 *tiles_p, float *cfac, cudaStream_t st, Profiler *prof);
 // dst_h (optional): an FP16 copy of dst, the stored trajectory of the
 // FP16-storage form
-void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
+void launch_state_step(const Dims &d, const float *src, const float *dispm, const int4 *tiles_m,
                        float *dst, cudaStream_t st, Profiler *prof, __half *dst_h = nullptr);
-void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
+void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p,
                          const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass,
                          __half *dst_h = nullptr);
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const float *gm0, float *u0,
                           cudaStream_t st, Profiler *prof);
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
-                          const int *range_m, const float *vt, const float *gm_next, float *dst,
+                          const int4 *tiles_m, const float *vt, const float *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof);
 // the last incremental-state step fused with the incremental adjoint's final
 // condition: lt_last = -mt(1), mt_out (nullable) = mt(1), b_out (nullable)
 // [3][N] = the body force's first term dt/2 lt(1) grad m(1)
-void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int4 *tiles_m,
                           const float *vt, const float *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof);
-void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int4 *tiles_m,
                           const float *vt, const __half *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof);
 // adjoint step dst = c src(X+) that also adds w dst grad m^{j-1} to the body
@@ -123,11 +125,11 @@ void launch_incstate_last(const Dims &d, float dt, const float *src, const float
 // p . b of the updated b (b . b if p is null): block partials in partial,
 // their sum plus *dot_add (nullable) in *dot_out.  dst_h: optional FP16 copy
 // of dst.
-void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p, const float *cfac,
                         float *dst, const float *gm, float *b, float w, bool want_dot, const float *p,
                         double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
                         int kclass, __half *dst_h = nullptr);
-void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p, const float *cfac,
                         float *dst, const __half *gm, float *b, float w, bool want_dot, const float *p,
                         double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
                         int kclass, __half *dst_h = nullptr);
@@ -150,7 +152,7 @@ void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float 
 void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half *gm0, float *u0,
                           cudaStream_t st, Profiler *prof);
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
-                          const int *range_m, const float *vt, const __half *gm_next, float *dst,
+                          const int4 *tiles_m, const float *vt, const __half *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof);
 // FP16 <-> FP32 copies of n values
 void launch_f2h(const float *in, __half *out, long long n, cudaStream_t st, Profiler *prof);

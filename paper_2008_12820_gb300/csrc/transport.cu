@@ -153,102 +153,41 @@ __device__ __forceinline__ int floor_int(float x) {
     return (int)fminf(fmaxf(floorf(x), -1.0e6f), 1.0e6f);
 }
 
-// The block also reduces the per-axis floor range of what it wrote (the SL
-// steps' box geometry) into part[block][12]: side, axis, {min, max}.
+// One thread per voxel (the trilinear form); the box geometry of its outputs
+// comes from k_tile_ranges.
 template <int ORDER>
 __global__ void __launch_bounds__(BX * BY)
 k_footpoints(const float *__restrict__ v, float *__restrict__ dispm, float *__restrict__ dispp,
-             Dims d, float dt, float ih1, float ih2, float ih3, int *__restrict__ part) {
-    __shared__ int red[BY][12];
+             Dims d, float dt, float ih1, float ih2, float ih3) {
     const Pt p = this_point(d);
+    if (!p.ok) return;
     const long long N = d.N;
-    float v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    if (p.ok) {
-        v1 = v[p.id];
-        v2 = v[N + p.id];
-        v3 = v[2 * N + p.id];
-    }
+    const float v1 = v[p.id], v2 = v[N + p.id], v3 = v[2 * N + p.id];
     // X- (side 0) and X+ (side 1); a side whose output is null is skipped
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         float *out = s == 0 ? dispm : dispp;
         if (!out) continue;
-        int f[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, g[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
-        if (p.ok) {
-            const float sg = s == 0 ? -1.f : 1.f;
-            const float q1 = sg * dt * v1 * ih1, q2 = sg * dt * v2 * ih2, q3 = sg * dt * v3 * ih3;
-            float w1, w2, w3;
-            if (ORDER == 1) {
-                w1 = gather8(v, d, p.i1, p.i2, p.i3, q1, q2, q3);
-                w2 = gather8(v + N, d, p.i1, p.i2, p.i3, q1, q2, q3);
-                w3 = gather8(v + 2 * N, d, p.i1, p.i2, p.i3, q1, q2, q3);
-            } else {
-                Axis4 a1, a2, a3;
-                axis_stencil(p.i1, q1, d.n1, d.n2 * d.n3, a1);
-                axis_stencil(p.i2, q2, d.n2, d.n3, a2);
-                axis_stencil(p.i3, q3, d.n3, 1, a3);
-                w1 = gather64(v, a1, a2, a3);
-                w2 = gather64(v + N, a1, a2, a3);
-                w3 = gather64(v + 2 * N, a1, a2, a3);
-            }
-            const float hs = 0.5f * sg * dt;
-            const float o[3] = {hs * (v1 + w1) * ih1, hs * (v2 + w2) * ih2, hs * (v3 + w3) * ih3};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                out[c * N + p.id] = o[c];
-                f[c] = g[c] = floor_int(o[c]);
-            }
+        const float sg = s == 0 ? -1.f : 1.f;
+        const float q1 = sg * dt * v1 * ih1, q2 = sg * dt * v2 * ih2, q3 = sg * dt * v3 * ih3;
+        float w1, w2, w3;
+        if (ORDER == 1) {
+            w1 = gather8(v, d, p.i1, p.i2, p.i3, q1, q2, q3);
+            w2 = gather8(v + N, d, p.i1, p.i2, p.i3, q1, q2, q3);
+            w3 = gather8(v + 2 * N, d, p.i1, p.i2, p.i3, q1, q2, q3);
+        } else {
+            Axis4 a1, a2, a3;
+            axis_stencil(p.i1, q1, d.n1, d.n2 * d.n3, a1);
+            axis_stencil(p.i2, q2, d.n2, d.n3, a2);
+            axis_stencil(p.i3, q3, d.n3, 1, a3);
+            w1 = gather64(v, a1, a2, a3);
+            w2 = gather64(v + N, a1, a2, a3);
+            w3 = gather64(v + 2 * N, a1, a2, a3);
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int lo = __reduce_min_sync(0xffffffffu, f[c]), hi = __reduce_max_sync(0xffffffffu, g[c]);
-            if (threadIdx.x == 0) {
-                red[threadIdx.y][6 * s + 2 * c] = lo;
-                red[threadIdx.y][6 * s + 2 * c + 1] = hi;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.y == 0 && threadIdx.x < 12) {
-        const int k = threadIdx.x;
-        const bool on = k < 6 ? dispm != nullptr : dispp != nullptr;
-        int r = (k & 1) ? -0x7fffffff : 0x7fffffff;
-        if (on)
-            for (int y = 0; y < BY; ++y) r = (k & 1) ? max(r, red[y][k]) : min(r, red[y][k]);
-        part[(((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x) * 12 + k] = r;
-    }
-}
-
-// per-axis floor ranges of the foot points from the blocks' partials
-__global__ void __launch_bounds__(256) k_range_parts(const int *__restrict__ part, long long nblocks,
-                                                     int *__restrict__ range_m, int *__restrict__ range_p) {
-    __shared__ int red[8][12];
-    int rg[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) rg[k] = (k & 1) ? -0x7fffffff : 0x7fffffff;
-    for (long long b = blockIdx.x * 256LL + threadIdx.x; b < nblocks; b += (long long)gridDim.x * 256) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const int x = part[b * 12 + k];
-            rg[k] = (k & 1) ? max(rg[k], x) : min(rg[k], x);
-        }
-    }
-    const int w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const int r = (k & 1) ? __reduce_max_sync(0xffffffffu, rg[k]) : __reduce_min_sync(0xffffffffu, rg[k]);
-        if ((threadIdx.x & 31) == 0) red[w][k] = r;
-    }
-    __syncthreads();
-    if (threadIdx.x < 12) {
-        const int k = threadIdx.x;
-        int r = red[0][k];
-        for (int y = 1; y < 8; ++y) r = (k & 1) ? max(r, red[y][k]) : min(r, red[y][k]);
-        int *range = k < 6 ? range_m : range_p;
-        if (range) {
-            if (k & 1) atomicMax(&range[k % 6], r);
-            else atomicMin(&range[k % 6], r);
-        }
+        const float hs = 0.5f * sg * dt;
+        out[p.id] = hs * (v1 + w1) * ih1;
+        out[N + p.id] = hs * (v2 + w2) * ih2;
+        out[2 * N + p.id] = hs * (v3 + w3) * ih3;
     }
 }
 
@@ -328,26 +267,28 @@ __device__ __forceinline__ float gather_lean(const T *__restrict__ f, const Dims
 
 // ---------------------------------------------------------------------------
 // Software-pipelined tiled semi-Lagrangian step (the production path).
-// Persistent blocks walk the tiles of 32 x 8 x 4 voxels.  The floor range of
-// the displacement field (per axis, over the whole field, from
-// k_floor_range) fixes the geometry of the source box every tile needs, so
-// while a block computes tile k from one shared-memory buffer, cp.async
-// already copies the box of tile k+1 into the other.  The displacements and
-// epilogue inputs of a tile are loaded when the tile starts, not a tile
-// ahead: that holds half the registers (three blocks per SM for the
+// Persistent blocks walk the tiles of 32 x 8 x 4 voxels.  Every tile has a box
+// entry (written by the foot-point kernel with the displacements, or by
+// k_tile_ranges): the smallest floor of its displacements per axis, which
+// fixes where its shared-memory source box starts, and whether the floors
+// fit the box.  While a block computes tile k from one shared-memory buffer,
+// cp.async already copies the box of tile k+1 into the other.  The
+// displacements and epilogue inputs of a tile are loaded when the tile starts,
+// not a tile ahead: that holds half the registers (three blocks per SM for the
 // incremental state, which has six epilogue inputs a voxel), and the loads
 // still overlap the box wait and the other resident blocks (measured at
 // 256^3: state 199 -> 182 us, adjoint 205 -> 187 us, incremental state
 // 234 -> 207 us, accumulating adjoint 242 -> 230 us).  The 64 taps of
 // a voxel are then shared-memory reads with immediate offsets, the same
 // instruction stream for every lane (the periodic wrap happened once, when
-// the box was fetched).  If the range makes the box larger than a buffer, the
-// kernel gathers from global memory instead (the decision is uniform).
+// the box was fetched).  A tile whose floors span more than the box gathers
+// from global memory instead (the decision is uniform per tile), so a region
+// of large displacements slows only its own tiles.
 // ---------------------------------------------------------------------------
 constexpr int PT3 = 32, PT2 = 8, PT1 = 4;
-// box geometry, fixed at compile time: floors of the displacement may span
-// BOX_SPAN + 1 consecutive integers per axis (per-step displacements of about
-// a cell); wider ranges take the global-memory gather
+// box geometry, fixed at compile time: floors of a tile's displacements may
+// span BOX_SPAN + 1 consecutive integers per axis (per-step displacements that
+// vary by about a cell over a tile); wider ranges take the global-memory gather
 constexpr int BOX_SPAN = 2;
 constexpr int BS1 = PT1 + 3 + BOX_SPAN, BS2 = PT2 + 3 + BOX_SPAN, BS3 = PT3 + 3 + BOX_SPAN;
 constexpr int BOX_PITCH = 64;  // floats per box row: rows start on bank 0
@@ -546,14 +487,43 @@ __device__ __forceinline__ void tile_range(int ntiles, int &tbeg, int &tend) {
 
 // floors inside the clamp of floor_int: a non-finite or huge displacement
 // (clamped to +-1e6 there, while the box path converts floorf directly) sends
-// the block to the gather path, whose stencil clamps
+// the tile to the gather path, whose stencil clamps
 __device__ __forceinline__ bool floor_sane(int lo, int hi) { return lo > -1000000 && hi < 1000000; }
 
-// the box of a displacement field's floor range fits a buffer
-__device__ __forceinline__ bool box_fits(const int *__restrict__ range) {
-    return range[1] - range[0] <= BOX_SPAN && range[3] - range[2] <= BOX_SPAN && range[5] - range[4] <= BOX_SPAN &&
-           range[0] <= range[1] && range[2] <= range[3] && range[4] <= range[5] && floor_sane(range[0], range[1]) &&
-           floor_sane(range[2], range[3]) && floor_sane(range[4], range[5]);
+// Box entry of one tile of a displacement field: {lo1, lo2, lo3, ok}, lo_d =
+// the smallest floor of the tile's displacements along axis d; ok = 1 when on
+// every axis the floors span at most BOX_SPAN + 1 consecutive integers (the
+// tile's stencils then lie inside the box at lo - 1), 0 otherwise (the tile
+// gathers from global memory).  lo, hi: this thread's per-axis floor min and
+// max over its voxels of the tile; red: [PT2][6] shared ints.  Contains one
+// barrier; the entry is written by thread (0, 0) after a second pass over red,
+// so the caller needs a barrier before red is written again.
+__device__ __forceinline__ void tile_box_reduce(const int lo[3], const int hi[3], int (*red)[6], int4 *out) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a = __reduce_min_sync(0xffffffffu, lo[c]), b = __reduce_max_sync(0xffffffffu, hi[c]);
+        if (tx == 0) {
+            red[ty][2 * c] = a;
+            red[ty][2 * c + 1] = b;
+        }
+    }
+    __syncthreads();
+    if (ty == 0) {
+        int x = 0;
+        if (tx < 6) {
+            x = red[0][tx];
+            for (int y = 1; y < PT2; ++y) x = (tx & 1) ? max(x, red[y][tx]) : min(x, red[y][tx]);
+        }
+        const int l0 = __shfl_sync(0xffffffffu, x, 0), h0 = __shfl_sync(0xffffffffu, x, 1);
+        const int l1 = __shfl_sync(0xffffffffu, x, 2), h1 = __shfl_sync(0xffffffffu, x, 3);
+        const int l2 = __shfl_sync(0xffffffffu, x, 4), h2 = __shfl_sync(0xffffffffu, x, 5);
+        if (tx == 0) {
+            const bool ok = h0 - l0 <= BOX_SPAN && h1 - l1 <= BOX_SPAN && h2 - l2 <= BOX_SPAN && floor_sane(l0, h0) &&
+                            floor_sane(l1, h1) && floor_sane(l2, h2);
+            *out = make_int4(l0, l1, l2, ok ? 1 : 0);
+        }
+    }
 }
 
 // block partial of the dot product of the accumulating adjoint step
@@ -565,63 +535,39 @@ __device__ __forceinline__ void sl_dot_store(const Acc2 &dot, double *partial) {
     }
 }
 
-// The same step by global-memory gathers over the block's tiles, for
-// displacement ranges too wide for the box.  Not inlined: its registers then
-// stay out of the box path's allocation, and no second launch is needed.
-template <int MODE, int ORDER, typename TS, typename TG>
-__device__ __noinline__ void sl_gather_tiles(const SlArgsT<TS, TG> &a, const Dims &d, Acc2 &dot) {
-    constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
-    constexpr int NX = EarlyCount<MODE>::v > 0 ? EarlyCount<MODE>::v : 1;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
-    const long long N = d.N, plane = (long long)d.n2 * d.n3;
-    int tbeg, tend;
-    tile_range(nb3 * nb2 * nb1, tbeg, tend);
-    for (int tile = tbeg; tile < tend; ++tile) {
-        const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
-        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
-        if (i3 >= d.n3 || i2 >= d.n2) continue;
-        for (int t = 0; t < PT1; ++t) {
-            const int i1 = t1 * PT1 + t;
-            if (i1 >= d.n1) break;
-            const long long id = i1 * plane + (long long)i2 * d.n3 + i3;
-            const float val = ORDER == 1
-                ? gather8(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id])
-                : gather_lean(a.src, d, i1, i2, i3, a.disp[id], a.disp[N + id], a.disp[2 * N + id]);
-            float e[NE], x[NX];
-            sl_load_epi<MODE>(a, id, N, e);
-            sl_load_early<MODE>(a, id, N, x);
-            sl_epilogue<MODE>(a, id, N, val, e, x, dot);
-        }
-    }
+// One voxel of a step by global-memory gathers, for tiles whose displacement
+// floors span more than the box holds.  Not inlined: its registers then stay
+// out of the box path's allocation.
+template <int ORDER, typename TS>
+__device__ __noinline__ float sl_gather_voxel(const TS *__restrict__ f, const Dims &d, int i1, int i2, int i3,
+                                              float d1, float d2, float d3) {
+    return ORDER == 1 ? gather8(f, d, i1, i2, i3, d1, d2, d3) : gather_lean(f, d, i1, i2, i3, d1, d2, d3);
 }
 
 // FULL: the grid is a whole number of tiles on every axis, so no voxel of a
 // tile needs a bounds check (measured ~5% of the step time at 256^3)
 template <int MODE, int ORDER, typename TS = float, typename TG = float, bool FULL = false>
 __global__ void __launch_bounds__(PT3 * PT2, SlOcc<MODE>::v)
-k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_in) {
+k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int4 *__restrict__ tiles, int chunked_in) {
     static_assert(std::is_same<TS, float>::value, "the box path stages FP32 source fields");
     constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
     constexpr int NX = EarlyCount<MODE>::v > 0 ? EarlyCount<MODE>::v : 1;
     Acc2 dot;
-    if (!box_fits(range)) {
-        sl_gather_tiles<MODE, ORDER>(a, d, dot);
-        sl_dot_store<MODE>(dot, a.partial);
-        return;
-    }
     extern __shared__ float smem[];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool chunked = chunked_in != 0;
-    const int fmn0 = range[0], fmn1 = range[2], fmn2 = range[4];
     const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
     const int ntiles = nb3 * nb2 * nb1;
     const long long N = d.N, plane = (long long)d.n2 * d.n3;
     int tbeg, tend;
     tile_range(ntiles, tbeg, tend);
     if (tbeg < tend) {
-        auto issue_box = [&](int t1, int t2, int t3, float *buf) {
-            box_copy(a.src, d, plane, t1 * PT1 + fmn0 - 1, t2 * PT2 + fmn1 - 1, t3 * PT3 + fmn2 - 1, buf, chunked);
+        // box of a tile at its own floor range g (lo1, lo2, lo3); a tile whose
+        // range does not fit (g.w == 0) copies nothing, but still commits a
+        // (empty) group so that the wait counts stay the same
+        auto issue_box = [&](int t1, int t2, int t3, const int4 &g, float *buf) {
+            if (g.w) box_copy(a.src, d, plane, t1 * PT1 + g.x - 1, t2 * PT2 + g.y - 1, t3 * PT3 + g.z - 1, buf, chunked);
+            else cp_async_commit();
         };
         // displacements and epilogue inputs of the voxels of a tile
         auto load_regs = [&](int t1, int t2, int t3, float *dd, float *ee) {
@@ -639,9 +585,13 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
             }
         };
 
-        // tile counters of the next tile to fetch (x3 fastest)
+        // tile counters of the next tile to fetch (x3 fastest); box entries of
+        // the current tile, the next one and the one after (loaded two tiles
+        // ahead, so the next box can be issued without waiting for its entry)
         int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
-        issue_box(c1, c2, c3, smem);
+        int4 g_cur = tiles[tbeg];
+        int4 g_next = tbeg + 1 < tend ? tiles[tbeg + 1] : make_int4(0, 0, 0, 0);
+        issue_box(c1, c2, c3, g_cur, smem);
         int cur = 0;
         for (int tile = tbeg; tile < tend; ++tile) {
             const int t1 = c1, t2 = c2, t3 = c3;
@@ -661,33 +611,39 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
                 for (int t = 0; t < PT1; ++t)
                     if (FULL || t1 * PT1 + t < d.n1) sl_load_early<MODE>(a, id0 + t * plane, N, cx[t]);
             }
+            const int4 g_after = tile + 2 < tend ? tiles[tile + 2] : make_int4(0, 0, 0, 0);
             if (tile + 1 < tend) {
-                issue_box(c1, c2, c3, smem + (cur ^ 1) * BOX_FLOATS);
+                issue_box(c1, c2, c3, g_next, smem + (cur ^ 1) * BOX_FLOATS);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncthreads();
             const float *bx = smem + cur * BOX_FLOATS;
+            const int fmn0 = g_cur.x, fmn1 = g_cur.y, fmn2 = g_cur.z;
             const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
             if (inplane) {
 #pragma unroll
                 for (int t = 0; t < PT1; ++t) {
                     if (FULL || t1 * PT1 + t < d.n1) {
                         const float *dt3 = cd + 3 * t;
-                        const float fl0 = floorf(dt3[0]), fl1 = floorf(dt3[1]), fl2 = floorf(dt3[2]);
-                        // stencil origin inside the box; every tap is an immediate offset
-                        const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
-                        const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
                         float acc;
-                        if (ORDER == 1) {
-                            acc = box_linear(p, dt3[0] - fl0, dt3[1] - fl1, dt3[2] - fl2);
+                        if (g_cur.w) {
+                            const float fl0 = floorf(dt3[0]), fl1 = floorf(dt3[1]), fl2 = floorf(dt3[2]);
+                            // stencil origin inside the box; every tap is an immediate offset
+                            const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
+                            const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
+                            if (ORDER == 1) {
+                                acc = box_linear(p, dt3[0] - fl0, dt3[1] - fl1, dt3[2] - fl2);
+                            } else {
+                                float w1[4], w2[4], w3[4];
+                                lagrange4(dt3[0] - fl0, w1);
+                                lagrange4(dt3[1] - fl1, w2);
+                                lagrange4(dt3[2] - fl2, w3);
+                                acc = box_cubic(p, w1, w2, w3);
+                            }
                         } else {
-                            float w1[4], w2[4], w3[4];
-                            lagrange4(dt3[0] - fl0, w1);
-                            lagrange4(dt3[1] - fl1, w2);
-                            lagrange4(dt3[2] - fl2, w3);
-                            acc = box_cubic(p, w1, w2, w3);
+                            acc = sl_gather_voxel<ORDER>(a.src, d, t1 * PT1 + t, i2, i3, dt3[0], dt3[1], dt3[2]);
                         }
                         sl_epilogue<MODE>(a, id0 + t * plane, N, acc, ce + NE * t, cx[t], dot);
                     }
@@ -695,9 +651,42 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
             }
             __syncthreads();
             cur ^= 1;
+            g_cur = g_next;
+            g_next = g_after;
         }
     }
     sl_dot_store<MODE>(dot, a.partial);
+}
+
+// Box entries of every tile of a displacement field (for fields that do not
+// come from the foot-point kernel, which writes them itself): persistent
+// blocks over the tiles, 12 bytes read per voxel.
+__global__ void __launch_bounds__(PT3 * PT2)
+k_tile_ranges(const float *__restrict__ disp, Dims d, int4 *__restrict__ tiles) {
+    __shared__ int red[PT2][6];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
+    const long long N = d.N, plane = (long long)d.n2 * d.n3;
+    int tbeg, tend;
+    tile_range(nb3 * nb2 * nb1, tbeg, tend);
+    for (int tile = tbeg; tile < tend; ++tile) {
+        const int t3 = tile % nb3, r = tile / nb3, t2 = r % nb2, t1 = r / nb2;
+        const int i3 = t3 * PT3 + tx, i2 = t2 * PT2 + ty;
+        int lo[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, hi[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+        if (i3 < d.n3 && i2 < d.n2) {
+            for (int t = 0; t < PT1 && t1 * PT1 + t < d.n1; ++t) {
+                const long long id = (long long)(t1 * PT1 + t) * plane + (long long)i2 * d.n3 + i3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int f = floor_int(disp[c * N + id]);
+                    lo[c] = min(lo[c], f);
+                    hi[c] = max(hi[c], f);
+                }
+            }
+        }
+        tile_box_reduce(lo, hi, red, tiles + tile);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -710,8 +699,8 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int *__restrict__ range, int chunked_
 // warp, where the global-memory gather of a misaligned 32-float row costs two
 // L1 wavefronts.  A tile whose predictor floors span more than the box allows
 // gathers from global memory instead (the decision is uniform per block).
-// The block also reduces the floor range of what it wrote (the SL steps' box
-// geometry) into part[block][12], as k_footpoints does.
+// The block also reduces, per tile and side, the floor range of what it wrote:
+// the box entry of that tile for the SL steps.
 // ---------------------------------------------------------------------------
 constexpr int FP_OCC = 2;  // resident blocks per SM: three component boxes each
 
@@ -729,19 +718,17 @@ __device__ __noinline__ float3 fp_gather3(const float *__restrict__ v, const Dim
 
 __global__ void __launch_bounds__(PT3 * PT2, FP_OCC)
 k_footpoints_box(const float *__restrict__ v, float *__restrict__ dispm, float *__restrict__ dispp, Dims d,
-                 float dt, float ih1, float ih2, float ih3, int chunked_in, int *__restrict__ part) {
+                 float dt, float ih1, float ih2, float ih3, int chunked_in, int4 *__restrict__ tiles_m,
+                 int4 *__restrict__ tiles_p) {
     extern __shared__ float smem[];
-    __shared__ int red[PT2][12];
+    __shared__ int red[PT2][6];
+    __shared__ int ored[PT2][6];
     __shared__ int rng[6];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool chunked = chunked_in != 0;
     const int nb3 = (d.n3 + PT3 - 1) / PT3, nb2 = (d.n2 + PT2 - 1) / PT2, nb1 = (d.n1 + PT1 - 1) / PT1;
     const long long N = d.N, plane = (long long)d.n2 * d.n3;
     const float ih[3] = {ih1, ih2, ih3};
-    // floor range of the outputs: [side * 3 + axis]
-    int omn[6], omx[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) { omn[k] = 0x7fffffff; omx[k] = -0x7fffffff; }
     int tbeg, tend;
     tile_range(nb3 * nb2 * nb1, tbeg, tend);
     for (int tile = tbeg; tile < tend; ++tile) {
@@ -801,6 +788,9 @@ k_footpoints_box(const float *__restrict__ v, float *__restrict__ dispm, float *
                 __syncthreads();
             }
             const int sh = box_shift(t3 * PT3 + f2 - 1, chunked);
+            // floor range of this side's output over the tile: the box entry
+            // of the SL steps that use it
+            int omn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, omx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
 #pragma unroll
             for (int t = 0; t < PT1; ++t) {
                 if (!ok[t]) continue;
@@ -828,86 +818,16 @@ k_footpoints_box(const float *__restrict__ v, float *__restrict__ dispm, float *
                     const float o = hs * (vx[t][c] + w[c]) * ih[c];
                     out[c * N + id] = o;
                     const int f = floor_int(o);
-                    omn[3 * s + c] = min(omn[3 * s + c], f);
-                    omx[3 * s + c] = max(omx[3 * s + c], f);
+                    omn[c] = min(omn[c], f);
+                    omx[c] = max(omx[c], f);
                 }
             }
-            // the boxes and rng are rewritten by the next side or tile
+            // the boxes, rng and ored are rewritten by the next side or tile
+            // only after further barriers, which the first warp reaches after
+            // it has read ored
+            tile_box_reduce(omn, omx, ored, (s == 0 ? tiles_m : tiles_p) + tile);
             __syncthreads();
         }
-    }
-    // block partial of the output floor ranges
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const int a = __reduce_min_sync(0xffffffffu, omn[k]), b = __reduce_max_sync(0xffffffffu, omx[k]);
-        if (tx == 0) {
-            red[ty][2 * k] = a;
-            red[ty][2 * k + 1] = b;
-        }
-    }
-    __syncthreads();
-    if (ty == 0 && tx < 12) {
-        const int k = tx;
-        const bool on = k < 6 ? dispm != nullptr : dispp != nullptr;
-        int x = (k & 1) ? -0x7fffffff : 0x7fffffff;
-        if (on)
-            for (int y = 0; y < PT2; ++y) x = (k & 1) ? max(x, red[y][k]) : min(x, red[y][k]);
-        part[(long long)blockIdx.x * 12 + k] = x;
-    }
-}
-
-// per-axis [min, max] of floor(disp) over the field (6 ints: min0, max0, ...)
-__global__ void k_range_init(int *range) {
-    if (threadIdx.x < 3) {
-        range[2 * threadIdx.x] = 0x7fffffff;
-        range[2 * threadIdx.x + 1] = -0x7fffffff;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_floor_range(const float *__restrict__ disp, long long N,
-                                                     int *__restrict__ range) {
-    // all three components in one sweep (float4 loads where the rows allow),
-    // then a block reduction and one atomic per bound and block
-    __shared__ int red[8][6];
-    int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, mx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
-    const long long stride = (long long)gridDim.x * 256;
-    const bool vec = (N & 3) == 0 && (((uintptr_t)disp) & 15) == 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float *dc = disp + c * N;
-        if (vec) {
-            const float4 *d4 = reinterpret_cast<const float4 *>(dc);
-#pragma unroll 4
-            for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N / 4; i += stride) {
-                const float4 q = d4[i];
-                const int f0 = floor_int(q.x), f1 = floor_int(q.y), f2 = floor_int(q.z), f3 = floor_int(q.w);
-                mn[c] = min(mn[c], min(min(f0, f1), min(f2, f3)));
-                mx[c] = max(mx[c], max(max(f0, f1), max(f2, f3)));
-            }
-        } else {
-            for (long long i = blockIdx.x * 256LL + threadIdx.x; i < N; i += stride) {
-                const int f = floor_int(dc[i]);
-                mn[c] = min(mn[c], f);
-                mx[c] = max(mx[c], f);
-            }
-        }
-    }
-    const int w = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int a = __reduce_min_sync(0xffffffffu, mn[c]), b = __reduce_max_sync(0xffffffffu, mx[c]);
-        if ((threadIdx.x & 31) == 0) {
-            red[w][2 * c] = a;
-            red[w][2 * c + 1] = b;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        const int k = threadIdx.x;
-        int r = red[0][k];
-        for (int y = 1; y < 8; ++y) r = (k & 1) ? max(r, red[y][k]) : min(r, red[y][k]);
-        if (k & 1) atomicMax(&range[k], r);
-        else atomicMin(&range[k], r);
     }
 }
 
@@ -938,13 +858,13 @@ inline int pipe_blocks(const Dims &d, int per_sm) {
 }
 
 template <int MODE, int ORDER, typename TS, typename TG, bool FULL>
-void launch_pipe_f(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
+void launch_pipe_f(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
     // the shared-memory limit is set once per instantiation and device
     static SmemAttr attr;
     attr.ensure(k_sl_pipe<MODE, ORDER, TS, TG, FULL>, (int)smem, "k_sl_pipe");
     k_sl_pipe<MODE, ORDER, TS, TG, FULL><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(
-        a, d, range, chunk_ok(d, a.src));
+        a, d, tiles, chunk_ok(d, a.src));
 }
 
 // kernels one SL step launches
@@ -954,20 +874,20 @@ inline bool full_tiles(const Dims &d) { return d.n3 % PT3 == 0 && d.n2 % PT2 == 
 
 // the full-tile form for the cubic steps (the production discretization)
 template <int MODE, int ORDER, typename TS, typename TG>
-void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
+void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
     if constexpr (ORDER == 3) {
         if (full_tiles(d)) {
-            launch_pipe_f<MODE, ORDER, TS, TG, true>(d, a, range, st);
+            launch_pipe_f<MODE, ORDER, TS, TG, true>(d, a, tiles, st);
             return;
         }
     }
-    launch_pipe_f<MODE, ORDER, TS, TG, false>(d, a, range, st);
+    launch_pipe_f<MODE, ORDER, TS, TG, false>(d, a, tiles, st);
 }
 
 template <int MODE, typename TS, typename TG>
-void launch_pipe(const Dims &d, const SlArgsT<TS, TG> &a, const int *range, cudaStream_t st) {
-    if (d.iorder == 1) launch_pipe_o<MODE, 1>(d, a, range, st);
-    else launch_pipe_o<MODE, 3>(d, a, range, st);
+void launch_pipe(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
+    if (d.iorder == 1) launch_pipe_o<MODE, 1>(d, a, tiles, st);
+    else launch_pipe_o<MODE, 3>(d, a, tiles, st);
 }
 
 // ----------------------------------------------------------- pointwise ----
@@ -1031,83 +951,79 @@ inline int grid1(long long N) {
 
 }  // namespace
 
-void launch_floor_range(const Dims &d, const float *disp, int *range, cudaStream_t st,
-                        Profiler *prof) {
-    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 12.0 * d.N, 2);
-    k_range_init<<<1, 32, 0, st>>>(range);
-    k_floor_range<<<8 * num_sms(), 256, 0, st>>>(disp, d.N, range);
+long long tile_count(const Dims &d) {
+    return (long long)((d.n3 + PT3 - 1) / PT3) * ((d.n2 + PT2 - 1) / PT2) * ((d.n1 + PT1 - 1) / PT1);
 }
 
-void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp,
-                       int *range_m, int *range_p, int *part, cudaStream_t st, Profiler *prof) {
+void launch_tile_ranges(const Dims &d, const float *disp, int4 *tiles, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 12.0 * d.N, 1);
+    k_tile_ranges<<<pipe_blocks(d, 4), dim3(PT3, PT2), 0, st>>>(disp, d, tiles);
+}
+
+void launch_footpoints(const Dims &d, int nt, const float *v, float *dispm, float *dispp, int4 *tiles_m,
+                       int4 *tiles_p, cudaStream_t st, Profiler *prof) {
     if (!dispm && !dispp) return;
     const float dt = 1.f / nt;
     const double two_pi = 6.283185307179586476925286766559;
-    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)), 4);
     const float i1 = (float)(d.n1 / two_pi), i2 = (float)(d.n2 / two_pi), i3 = (float)(d.n3 / two_pi);
-    long long nblocks;
     if (d.iorder == 1) {
-        const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
-        k_footpoints<1><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, part);
-        nblocks = (long long)grid.x * grid.y * grid.z;
-    } else {
-        const size_t smem = 3 * BOX_FLOATS * sizeof(float);
-        static SmemAttr attr;  // once per device
-        attr.ensure(k_footpoints_box, (int)smem, "k_footpoints_box");
-        const int grid = pipe_blocks(d, FP_OCC);
-        k_footpoints_box<<<grid, dim3(PT3, PT2), smem, st>>>(v, dispm, dispp, d, dt, i1, i2, i3, chunk_ok(d, v),
-                                                             part);
-        nblocks = grid;
+        {
+            ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)), 1);
+            const dim3 grid((d.n3 + BX - 1) / BX, (d.n2 + BY - 1) / BY, d.n1);
+            k_footpoints<1><<<grid, dim3(BX, BY), 0, st>>>(v, dispm, dispp, d, dt, i1, i2, i3);
+        }
+        if (dispm) launch_tile_ranges(d, dispm, tiles_m, st, prof);
+        if (dispp) launch_tile_ranges(d, dispp, tiles_p, st, prof);
+        return;
     }
-    if (dispm) k_range_init<<<1, 32, 0, st>>>(range_m);
-    if (dispp) k_range_init<<<1, 32, 0, st>>>(range_p);
-    k_range_parts<<<num_sms(), 256, 0, st>>>(part, nblocks, dispm ? range_m : nullptr, dispp ? range_p : nullptr);
+    ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, (double)d.N * (12 + (dispm ? 12 : 0) + (dispp ? 12 : 0)), 1);
+    const size_t smem = 3 * BOX_FLOATS * sizeof(float);
+    static SmemAttr attr;  // once per device
+    attr.ensure(k_footpoints_box, (int)smem, "k_footpoints_box");
+    k_footpoints_box<<<pipe_blocks(d, FP_OCC), dim3(PT3, PT2), smem, st>>>(v, dispm, dispp, d, dt, i1, i2, i3,
+                                                                          chunk_ok(d, v), tiles_m, tiles_p);
 }
 
-long long footpoint_parts(const Dims &d) {
-    return (long long)((d.n3 + BX - 1) / BX) * ((d.n2 + BY - 1) / BY) * d.n1 * 12;
-}
-
-void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int *range,
+void launch_interp(const Dims &d, const float *f, const float *disp, float *out, int4 *tiles,
                    cudaStream_t st, Profiler *prof, int kclass) {
-    launch_floor_range(d, disp, range, st, prof);
+    launch_tile_ranges(d, disp, tiles, st, prof);
     ProfScope ps(prof, kclass, st, 20.0 * d.N, kSlLaunches);
     SlArgs a{f, disp, out, nullptr, nullptr, nullptr, 0.f};
-    launch_pipe<SL_PLAIN>(d, a, range, st);
+    launch_pipe<SL_PLAIN>(d, a, tiles, st);
 }
 
 void launch_adjoint_factor(const Dims &d, int nt, const float *divv, const float *dispp,
-                           const int *range_p, float *cfac, cudaStream_t st, Profiler *prof) {
+                           const int4 *tiles_p, float *cfac, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_FOOTPOINT, st, 20.0 * d.N, kSlLaunches);
     SlArgs a{divv, dispp, cfac, divv, nullptr, nullptr, 1.f / nt};
-    launch_pipe<SL_ADJFAC>(d, a, range_p, st);
+    launch_pipe<SL_ADJFAC>(d, a, tiles_p, st);
 }
 
-void launch_state_step(const Dims &d, const float *src, const float *dispm, const int *range_m,
+void launch_state_step(const Dims &d, const float *src, const float *dispm, const int4 *tiles_m,
                        float *dst, cudaStream_t st, Profiler *prof, __half *dst_h) {
     ProfScope ps(prof, CLAIRE_K_STATE, st, (20.0 + (dst_h ? 2 : 0)) * d.N, kSlLaunches);
     SlArgs a{src, dispm, dst, nullptr, nullptr, nullptr, 0.f, dst_h};
-    launch_pipe<SL_PLAIN>(d, a, range_m, st);
+    launch_pipe<SL_PLAIN>(d, a, tiles_m, st);
 }
 
-void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int *range_p,
+void launch_adjoint_step(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p,
                          const float *cfac, float *dst, cudaStream_t st, Profiler *prof, int kclass,
                          __half *dst_h) {
     ProfScope ps(prof, kclass, st, (24.0 + (dst_h ? 2 : 0)) * d.N, kSlLaunches);
     SlArgs a{src, dispp, dst, cfac, nullptr, nullptr, 0.f, dst_h};
-    launch_pipe<SL_ADJ>(d, a, range_p, st);
+    launch_pipe<SL_ADJ>(d, a, tiles_p, st);
 }
 
 namespace {
 template <typename TG>
-void incstate_step(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+void incstate_step(const Dims &d, float dt, const float *src, const float *dispm, const int4 *tiles_m,
                    const float *vt, const TG *gm_next, float *dst, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_INCSTATE, st, (32.0 + 3 * sizeof(TG)) * d.N, kSlLaunches);
     SlArgsT<float, TG> a{src, dispm, dst, nullptr, vt, gm_next, dt};
-    launch_pipe<SL_INCSTATE>(d, a, range_m, st);
+    launch_pipe<SL_INCSTATE>(d, a, tiles_m, st);
 }
 template <typename TG>
-void incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+void incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int4 *tiles_m,
                    const float *vt, const TG *gm_last, float *lt_last, float *mt_out, float *b_out,
                    cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_INCSTATE, st, (32.0 + 3 * sizeof(TG) + (mt_out ? 4 : 0) + (b_out ? 12 : 0)) * d.N,
@@ -1115,11 +1031,11 @@ void incstate_last(const Dims &d, float dt, const float *src, const float *dispm
     SlArgsT<float, TG> a{src, dispm, lt_last, nullptr, vt, gm_last, dt};
     a.dst2 = mt_out;
     a.acc = b_out;
-    launch_pipe<SL_INCLAST>(d, a, range_m, st);
+    launch_pipe<SL_INCLAST>(d, a, tiles_m, st);
 }
 
 template <typename TG>
-void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p, const float *cfac,
                  float *dst, const TG *gm, float *b, float w, bool want_dot, const float *p, double *partial,
                  const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof, int kclass,
                  __half *dst_h) {
@@ -1132,37 +1048,37 @@ void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int 
     if (want_dot) {
         a.pv = p;
         a.partial = partial;
-        launch_pipe<SL_ADJDOT>(d, a, range_p, st);
+        launch_pipe<SL_ADJDOT>(d, a, tiles_p, st);
         launch_finalize(partial, pipe_blocks(d, SlOcc<SL_ADJDOT>::v), dot_add, dot_out, st);
     } else {
-        launch_pipe<SL_ADJACC>(d, a, range_p, st);
+        launch_pipe<SL_ADJACC>(d, a, tiles_p, st);
     }
 }
 }  // namespace
 
-void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int4 *tiles_m,
                           const float *vt, const float *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof) {
-    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, b_out, st, prof);
+    incstate_last(d, dt, src, dispm, tiles_m, vt, gm_last, lt_last, mt_out, b_out, st, prof);
 }
-void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int *range_m,
+void launch_incstate_last(const Dims &d, float dt, const float *src, const float *dispm, const int4 *tiles_m,
                           const float *vt, const __half *gm_last, float *lt_last, float *mt_out, float *b_out,
                           cudaStream_t st, Profiler *prof) {
-    incstate_last(d, dt, src, dispm, range_m, vt, gm_last, lt_last, mt_out, b_out, st, prof);
+    incstate_last(d, dt, src, dispm, tiles_m, vt, gm_last, lt_last, mt_out, b_out, st, prof);
 }
 
-void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p, const float *cfac,
                         float *dst, const float *gm, float *b, float w, bool want_dot, const float *p,
                         double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
                         int kclass, __half *dst_h) {
-    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, want_dot, p, partial, dot_add, dot_out, st, prof,
+    adjoint_acc(d, src, dispp, tiles_p, cfac, dst, gm, b, w, want_dot, p, partial, dot_add, dot_out, st, prof,
                 kclass, dst_h);
 }
-void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int *range_p, const float *cfac,
+void launch_adjoint_acc(const Dims &d, const float *src, const float *dispp, const int4 *tiles_p, const float *cfac,
                         float *dst, const __half *gm, float *b, float w, bool want_dot, const float *p,
                         double *partial, const double *dot_add, double *dot_out, cudaStream_t st, Profiler *prof,
                         int kclass, __half *dst_h) {
-    adjoint_acc(d, src, dispp, range_p, cfac, dst, gm, b, w, want_dot, p, partial, dot_add, dot_out, st, prof,
+    adjoint_acc(d, src, dispp, tiles_p, cfac, dst, gm, b, w, want_dot, p, partial, dot_add, dot_out, st, prof,
                 kclass, dst_h);
 }
 
@@ -1178,14 +1094,14 @@ void launch_incstate_init(const Dims &d, float dt, const float *vt, const __half
 }
 
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
-                          const int *range_m, const float *vt, const float *gm_next, float *dst,
+                          const int4 *tiles_m, const float *vt, const float *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof) {
-    incstate_step(d, dt, src, dispm, range_m, vt, gm_next, dst, st, prof);
+    incstate_step(d, dt, src, dispm, tiles_m, vt, gm_next, dst, st, prof);
 }
 void launch_incstate_step(const Dims &d, float dt, const float *src, const float *dispm,
-                          const int *range_m, const float *vt, const __half *gm_next, float *dst,
+                          const int4 *tiles_m, const float *vt, const __half *gm_next, float *dst,
                           cudaStream_t st, Profiler *prof) {
-    incstate_step(d, dt, src, dispm, range_m, vt, gm_next, dst, st, prof);
+    incstate_step(d, dt, src, dispm, tiles_m, vt, gm_next, dst, st, prof);
 }
 
 namespace {

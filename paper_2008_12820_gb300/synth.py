@@ -263,6 +263,8 @@ WORKLOADS = {
     "blob128": dict(seed=1001, shape=(128, 128, 128), nt=4, beta=1e-2, gamma=1.0),
     "blob256": dict(seed=1001, shape=(256, 256, 256), nt=4, beta=1e-2, gamma=1.0),
     "blob256_nt8": dict(seed=1002, shape=(256, 256, 256), nt=8, beta=1e-2, gamma=1.0),
+    # the 256^3 pair with three times the displacement (12 voxels at most)
+    "blob256_d12": dict(seed=1001, shape=(256, 256, 256), nt=4, beta=1e-2, gamma=1.0, max_disp_vox=12.0),
     "blob768": dict(seed=1004, shape=(768, 768, 768), nt=8, beta=1e-2, gamma=1.0),
 }
 
@@ -286,7 +288,7 @@ def workload(name, shape=None):
         elif name == "blob768":
             d = blob_pair(w["shape"], w["seed"], n_blobs=60, sigma_vox=3.0)
         else:
-            d = blob_pair(w["shape"], w["seed"])
+            d = blob_pair(w["shape"], w["seed"], max_disp_vox=w.get("max_disp_vox", 4.0))
         if cache:
             os.makedirs(cache, exist_ok=True)
             for k in keys:

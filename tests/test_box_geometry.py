@@ -1,5 +1,6 @@
 """Host-side model of the shared-memory box geometry of the semi-Lagrangian
-steps (k_sl_pipe) and the box foot points (k_footpoints_box): for every voxel
+steps (k_sl_pipe) and the box foot points (k_footpoints_box): both place each
+tile's box at the tile's own floor range (the box entry), and for every voxel
 of every tile whose floor range fits the box, each of the 64 stencil taps the
 kernel reads (box row and column from the voxel's floors, the tile origin and
 the 16-byte chunk shift) lies inside the part of the box the copy writes, and
@@ -55,7 +56,8 @@ def box_contents(lo1, lo2, lo3, shape, chunked):
 
 def check_tiles(shape, disp, per_tile):
     """disp: [3][n1][n2][n3] displacement (index units) of each voxel's stencil
-    origin; per_tile: floor range of the tile (foot points) or of the field (SL)"""
+    origin; per_tile: floor range of the tile (the kernels' box entries) or of
+    the whole field"""
     n1, n2, n3 = shape
     chunked = n3 % 4 == 0
     fl = floor_int(disp)
@@ -69,7 +71,7 @@ def check_tiles(shape, disp, per_tile):
                 f = fl[(slice(None),) + sl]
                 lo, hi = (f.reshape(3, -1).min(1), f.reshape(3, -1).max(1)) if per_tile else (lo_field, hi_field)
                 if np.any(hi - lo > C["SPAN"]) or np.any(lo <= -1000000) or np.any(hi >= 1000000):
-                    continue                                   # the block gathers from global memory
+                    continue                                   # the tile gathers from global memory
                 fits += 1
                 lo1, lo2, lo3 = t1 * C["PT1"] + lo[0] - 1, t2 * C["PT2"] + lo[1] - 1, t3 * C["PT3"] + lo[2] - 1
                 box = box_contents(lo1, lo2, lo3, shape, chunked)
@@ -110,22 +112,33 @@ def test_foot_point_boxes_cover_every_tap(shape, amp, seed):
     assert fits > 0 and checked > 0
 
 
-@pytest.mark.parametrize("shape,amp,seed", [((24, 32, 40), 0.5, 5), ((20, 16, 33), 0.9, 6)])
+@pytest.mark.parametrize("shape,amp,seed", [((24, 32, 40), 0.5, 5), ((20, 16, 33), 0.9, 6), ((32, 64, 64), 3.0, 7),
+                                            ((32, 64, 64), 5.0, 7)])
 def test_sl_step_boxes_cover_every_tap(shape, amp, seed):
-    # k_sl_pipe: the foot-point displacement with the field-wide floor range
+    # k_sl_pipe: the foot-point displacement with each tile's own floor range
     disp = smooth_disp(shape, amp, seed)
-    fits, checked = check_tiles(shape, disp, per_tile=False)
+    fits, checked = check_tiles(shape, disp, per_tile=True)
     assert fits > 0 and checked > 0
+    if amp > 2:
+        # displacements of several cells: a field-wide range would send every
+        # tile to the gather path; per tile, all (amp 3) or some (amp 5) fit
+        assert check_tiles(shape, disp, per_tile=False)[0] == 0
+        ntiles = np.prod([-(-n // c) for n, c in zip(shape, (C["PT1"], C["PT2"], C["PT3"]))])
+        assert (fits == ntiles) if amp < 4 else (0 < fits < ntiles)
 
 
 def test_wide_or_nonfinite_ranges_leave_the_box_path():
-    # a span beyond the box, or a clamped (non-finite) floor, never takes the box path
+    # a span beyond the box, or a clamped (non-finite) floor, never takes the box path,
+    # and only the tile that holds it leaves
     assert np.all(floor_int(np.array([np.inf, -np.inf, 3e9])) == [1e6, -1e6, 1e6])
     shape = (8, 8, 32)
     disp = np.zeros((3,) + shape, np.float32)
     disp[0, 0, 0, 0] = C["SPAN"] + 1.5
     fits, _ = check_tiles(shape, disp, per_tile=False)
     assert fits == 0
+    fits, _ = check_tiles(shape, disp, per_tile=True)
+    ntiles = (8 // C["PT1"]) * (8 // C["PT2"]) * (32 // C["PT3"])
+    assert fits == ntiles - 1
     # every displacement infinite: a span of 0 at the clamp, still not the box
     fits, _ = check_tiles(shape, np.full((3,) + shape, np.inf, np.float32), per_tile=True)
     assert fits == 0

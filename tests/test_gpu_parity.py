@@ -275,6 +275,50 @@ def test_large_displacement_wraps(claire):
         assert rel(host(g), go) < TOL and abs(J - Jo) / abs(Jo) < TOL
 
 
+def tile_spans(disp):
+    """per-tile floor span of a displacement field on the transport tiles
+    (4 x 8 x 32 voxels), max over the three axes"""
+    fl = np.floor(disp).astype(np.int64)
+    n1, n2, n3 = disp.shape[1:]
+    t = fl.reshape(3, n1 // 4, 4, n2 // 8, 8, n3 // 32, 32)
+    return (t.max(axis=(2, 4, 6)) - t.min(axis=(2, 4, 6))).max(axis=0)
+
+
+def test_mixed_box_and_gather_tiles(claire):
+    """a velocity with a steep local bump: the tiles it covers span more
+    floors than the shared-memory box holds and gather from global memory,
+    the others use the box; gradient, adjoint and matvec at 1e-5"""
+    shape, nt = (32, 48, 64), 2
+    m0, m1, v = make_problem(shape, nt, scale=0.5)
+    x = np.meshgrid(*synth.grid_axes(shape), indexing="ij")
+    bump = np.exp(-((x[0] - 3.0) ** 2 + (x[1] - 2.5) ** 2 + (x[2] - 3.5) ** 2) / 0.15)
+    v = v.copy()
+    v[2] += (4.0 * bump).astype(np.float32)
+    v[1] -= (3.0 * bump).astype(np.float32)
+    vt = synth.smooth_direction(shape, 11)
+    P = O.Problem(m0, m1, nt, 1e-2, 1.0)
+    go, Jo, lh = P.gradient(v, want_adjoint=True)
+    Ho = P.matvec(vt)
+    for disp in (P.dispm(), P.dispp()):
+        sp = tile_spans(disp)
+        assert (sp > 2).any() and (sp <= 2).any(), np.bincount(sp.ravel())
+    with claire.Registration(shape, nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(m0), dev(m1))
+        g, J = reg.gradient(dev(v))
+        assert rel(host(g), go) < TOL and abs(J - Jo) / abs(Jo) < TOL
+        for j in range(nt + 1):
+            assert rel(host(reg.field("adj", j)), lh[j]) < TOL, j
+        assert rel(host(reg.field("state", nt)), P.state_history()[nt]) < TOL
+        assert rel(host(reg.hess_matvec(None, dev(vt))), Ho) < TOL
+        # an interpolation with the same displacement through claire_interp
+        # (box entries from k_tile_ranges instead of the foot-point kernel)
+        f = m0.astype(np.float32)
+        I = np.stack(np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij"))
+        dm = P.dispm()
+        ref = O.interp(f, (I + dm).reshape(3, -1)).reshape(shape)
+        assert rel(host(reg.interp(dev(f), dev(dm))), ref) < TOL
+
+
 # -------------------------------------------- full size (256^3) properties --
 
 @pytest.fixture(scope="module")
@@ -395,10 +439,10 @@ def test_solve_with_invh0_matches_oracle(claire):
         v = torch.zeros((3,) + shape, device="cuda")
         rep = reg.solve(v, precond="invH0", eps_h0=1e-3)
         assert rep.status == 0 and rep.grel <= 5e-2
-        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg
+        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg and rep.n_inner == ro.n_inner
         assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
-        assert abs(rep.grel - ro.grel) / ro.grel < 1e-3
-        assert rel(host(v), vo) < 1e-3
+        assert abs(rep.grel - ro.grel) / ro.grel < TOL_SOLVE
+        assert rel(host(v), vo) < TOL_SOLVE
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 32), (48, 40, 36)])
@@ -434,9 +478,10 @@ def test_solve_with_two_level_invh0(claire):
         v = torch.zeros((3,) + shape, device="cuda")
         rep = reg.solve(v, precond="2LinvH0", eps_h0=1e-3)
         assert rep.status == 0 and rep.grel <= 5e-2
-        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg
+        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg and rep.n_inner == ro.n_inner
         assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
-        assert rel(host(v), vo) < 1e-3
+        assert abs(rep.grel - ro.grel) / ro.grel < TOL_SOLVE
+        assert rel(host(v), vo) < TOL_SOLVE
 
 
 def test_beta_continuation_matches_oracle(claire):
@@ -453,9 +498,10 @@ def test_beta_continuation_matches_oracle(claire):
         rep, lev = reg.solve_continuation(v, 1e-2, beta_start=1.0, factor=0.1, precond="invH0")
         assert lev == lev_o == 3
         assert rep.status == 0 and rep.grel <= 5e-2
-        assert rep.n_gn == ro.n_gn
-        assert abs(rep.J - ro.J) / abs(ro.J) < 1e-3
-        assert rel(host(v), vo) < 1e-2
+        assert rep.n_gn == ro.n_gn and rep.n_pcg == ro.n_pcg
+        assert abs(rep.J - ro.J) / abs(ro.J) < TOL_SOLVE
+        assert abs(rep.grel - ro.grel) / ro.grel < TOL_SOLVE
+        assert rel(host(v), vo) < TOL_SOLVE
 
 
 # ------------------------------- the paper's GPU discretization (FD8, linear) ---
