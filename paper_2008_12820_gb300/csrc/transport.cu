@@ -535,14 +535,35 @@ __device__ __forceinline__ void sl_dot_store(const Acc2 &dot, double *partial) {
     }
 }
 
-// One voxel of a step by global-memory gathers, for tiles whose displacement
-// floors span more than the box holds.  Not inlined: its registers then stay
-// out of the box path's allocation.
-template <int ORDER, typename TS>
-__device__ __noinline__ float sl_gather_voxel(const TS *__restrict__ f, const Dims &d, int i1, int i2, int i3,
-                                              float d1, float d2, float d3) {
-    return ORDER == 1 ? gather8(f, d, i1, i2, i3, d1, d2, d3) : gather_lean(f, d, i1, i2, i3, d1, d2, d3);
+// One tile of a step by global-memory gathers, for tiles whose displacement
+// floors span more than the box holds.  It loads the tile's inputs itself and
+// returns its part of the epilogue's dot product.  Not inlined, and called
+// outside the box path's voxel loop, so that its registers and call frame
+// stay out of the box path.
+template <int MODE, int ORDER, typename TS, typename TG>
+__device__ __noinline__ Acc2 sl_gather_tile(const SlArgsT<TS, TG> &a, const Dims &d, int t1, int t2, int t3) {
+    constexpr int NE = EpiCount<MODE>::v > 0 ? EpiCount<MODE>::v : 1;
+    constexpr int NX = EarlyCount<MODE>::v > 0 ? EarlyCount<MODE>::v : 1;
+    Acc2 dot;
+    const int i3 = t3 * PT3 + threadIdx.x, i2 = t2 * PT2 + threadIdx.y;
+    if (i3 >= d.n3 || i2 >= d.n2) return dot;
+    const long long N = d.N, plane = (long long)d.n2 * d.n3;
+    for (int t = 0; t < PT1; ++t) {
+        const int i1 = t1 * PT1 + t;
+        if (i1 >= d.n1) break;
+        const long long id = i1 * plane + (long long)i2 * d.n3 + i3;
+        const float d1 = a.disp[id], d2 = a.disp[N + id], d3 = a.disp[2 * N + id];
+        const float val = ORDER == 1 ? gather8(a.src, d, i1, i2, i3, d1, d2, d3)
+                                     : gather_lean(a.src, d, i1, i2, i3, d1, d2, d3);
+        float e[NE], x[NX];
+        sl_load_epi<MODE>(a, id, N, e);
+        sl_load_early<MODE>(a, id, N, x);
+        sl_epilogue<MODE>(a, id, N, val, e, x, dot);
+    }
+    return dot;
 }
+
+constexpr int GTAB = 64;  // box entries a block stages in shared memory at a time
 
 // FULL: the grid is a whole number of tiles on every axis, so no voxel of a
 // tile needs a bounds check (measured ~5% of the step time at 256^3)
@@ -585,12 +606,18 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int4 *__restrict__ tiles, int chunked
             }
         };
 
-        // tile counters of the next tile to fetch (x3 fastest); box entries of
-        // the current tile, the next one and the one after (loaded two tiles
-        // ahead, so the next box can be issued without waiting for its entry)
+        // the block's box entries are staged in shared memory, GTAB at a time
+        // (a register copy of a pending global load would stall each tile)
+        __shared__ int4 gtab[GTAB];
+        auto stage_entries = [&](int first) {
+            for (int k = ty * PT3 + tx; k < GTAB && first + k < tend; k += PT3 * PT2) gtab[k] = tiles[first + k];
+        };
+        int gbase = tbeg;
+        stage_entries(gbase);
+        __syncthreads();
+        // tile counters of the next tile to fetch (x3 fastest)
         int c3 = tbeg % nb3, c2 = (tbeg / nb3) % nb2, c1 = tbeg / (nb3 * nb2);
-        int4 g_cur = tiles[tbeg];
-        int4 g_next = tbeg + 1 < tend ? tiles[tbeg + 1] : make_int4(0, 0, 0, 0);
+        int4 g_cur = gtab[0];
         issue_box(c1, c2, c3, g_cur, smem);
         int cur = 0;
         for (int tile = tbeg; tile < tend; ++tile) {
@@ -611,9 +638,19 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int4 *__restrict__ tiles, int chunked
                 for (int t = 0; t < PT1; ++t)
                     if (FULL || t1 * PT1 + t < d.n1) sl_load_early<MODE>(a, id0 + t * plane, N, cx[t]);
             }
-            const int4 g_after = tile + 2 < tend ? tiles[tile + 2] : make_int4(0, 0, 0, 0);
+            // entry of the next tile (the table is refilled behind the barrier
+            // that follows this tile when the next tile starts a new batch)
+            const int4 g_next = tile + 1 < tend && tile + 1 - gbase < GTAB ? gtab[tile + 1 - gbase] : g_cur;
+            const bool refill = tile + 1 < tend && tile + 1 - gbase == GTAB;
             if (tile + 1 < tend) {
-                issue_box(c1, c2, c3, g_next, smem + (cur ^ 1) * BOX_FLOATS);
+                if (refill) {
+                    // the next batch of entries: its first one is read here
+                    // from global memory, the rest after the end barrier
+                    const int4 gn = tiles[tile + 1];
+                    issue_box(c1, c2, c3, gn, smem + (cur ^ 1) * BOX_FLOATS);
+                } else {
+                    issue_box(c1, c2, c3, g_next, smem + (cur ^ 1) * BOX_FLOATS);
+                }
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -622,28 +659,27 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int4 *__restrict__ tiles, int chunked
             const float *bx = smem + cur * BOX_FLOATS;
             const int fmn0 = g_cur.x, fmn1 = g_cur.y, fmn2 = g_cur.z;
             const int sh = box_shift(t3 * PT3 + fmn2 - 1, chunked);
-            if (inplane) {
+            if (!g_cur.w) {
+                const Acc2 td = sl_gather_tile<MODE, ORDER>(a, d, t1, t2, t3);
+                if (MODE == SL_ADJDOT) dot.add(td.s, td.c);
+            } else if (inplane) {
 #pragma unroll
                 for (int t = 0; t < PT1; ++t) {
                     if (FULL || t1 * PT1 + t < d.n1) {
                         const float *dt3 = cd + 3 * t;
+                        const float fl0 = floorf(dt3[0]), fl1 = floorf(dt3[1]), fl2 = floorf(dt3[2]);
+                        // stencil origin inside the box; every tap is an immediate offset
+                        const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
+                        const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
                         float acc;
-                        if (g_cur.w) {
-                            const float fl0 = floorf(dt3[0]), fl1 = floorf(dt3[1]), fl2 = floorf(dt3[2]);
-                            // stencil origin inside the box; every tap is an immediate offset
-                            const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
-                            const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
-                            if (ORDER == 1) {
-                                acc = box_linear(p, dt3[0] - fl0, dt3[1] - fl1, dt3[2] - fl2);
-                            } else {
-                                float w1[4], w2[4], w3[4];
-                                lagrange4(dt3[0] - fl0, w1);
-                                lagrange4(dt3[1] - fl1, w2);
-                                lagrange4(dt3[2] - fl2, w3);
-                                acc = box_cubic(p, w1, w2, w3);
-                            }
+                        if (ORDER == 1) {
+                            acc = box_linear(p, dt3[0] - fl0, dt3[1] - fl1, dt3[2] - fl2);
                         } else {
-                            acc = sl_gather_voxel<ORDER>(a.src, d, t1 * PT1 + t, i2, i3, dt3[0], dt3[1], dt3[2]);
+                            float w1[4], w2[4], w3[4];
+                            lagrange4(dt3[0] - fl0, w1);
+                            lagrange4(dt3[1] - fl1, w2);
+                            lagrange4(dt3[2] - fl2, w3);
+                            acc = box_cubic(p, w1, w2, w3);
                         }
                         sl_epilogue<MODE>(a, id0 + t * plane, N, acc, ce + NE * t, cx[t], dot);
                     }
@@ -651,8 +687,12 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int4 *__restrict__ tiles, int chunked
             }
             __syncthreads();
             cur ^= 1;
-            g_cur = g_next;
-            g_next = g_after;
+            if (refill) {
+                gbase = tile + 1;
+                stage_entries(gbase);
+                __syncthreads();
+            }
+            g_cur = gtab[tile + 1 - gbase < GTAB ? tile + 1 - gbase : 0];
         }
     }
     sl_dot_store<MODE>(dot, a.partial);
