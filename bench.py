@@ -701,12 +701,56 @@ def run_batch(args, as_extra=False):
     print(json.dumps(out), flush=True)
 
 
+def run_pcstudy(args):
+    """The preconditioner study of Section 3 ("Preconditioning", Algorithm 2)
+    on the synthetic blob pairs: PCG iterations, inner iterations and solve
+    time of InvA, InvH0 and two-level InvH0 for beta in {5e-1, 1e-1, 5e-2} at
+    128^3 and 256^3 (N_t = 4, gamma = 1, from v = 0 to 5e-2 gradient
+    reduction; inner tolerance 1e-3 times the forcing term).  One untimed and
+    one timed solve per case."""
+    import torch
+
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    from paper_2008_12820_gb300 import claire, synth
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for n in (128, 256):
+        w = synth.workload("blob256", shape=(n, n, n))
+        shape = w["shape"]
+        m0, m1 = torch.from_numpy(w["m0"]).cuda(), torch.from_numpy(w["m1"]).cuda()
+        v = torch.zeros((3,) + shape, device="cuda")
+        for beta in (5e-1, 1e-1, 5e-2):
+            with claire.Registration(shape, w["nt"], beta, w["gamma"]) as reg:
+                reg.set_images(m0, m1)
+                for pc in ("invA", "invH0", "2LinvH0"):
+                    v.zero_()
+                    reg.solve(v, precond=pc)
+                    torch.cuda.synchronize()
+                    v.zero_()
+                    e0.record(stream)
+                    rep = reg.solve(v, precond=pc)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    rows.append({"n": n, "beta": beta, "precond": pc, "n_gn": rep.n_gn, "n_pcg": rep.n_pcg,
+                                 "n_inner": rep.n_inner, "solve_ms": round(e0.elapsed_time(e1), 3),
+                                 "t_pc_ms": round(rep.t_pc_ms, 3), "t_hess_ms": round(rep.t_hess_ms, 3),
+                                 "grel": rep.grel, "status": rep.status})
+    print(json.dumps({"study": "preconditioners (InvA, InvH0, 2LInvH0) on the synthetic blob pairs",
+                      "nt": 4, "gamma": 1.0, "eps_n": 5e-2, "eps_h0": 1e-3, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch16":
         run_batch(args)
+    elif args.workload == "pcstudy":
+        run_pcstudy(args)
     else:
         run_ours(args)
 

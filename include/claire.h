@@ -118,10 +118,20 @@ int claire_forward(claire_ctx *ctx, const float *v, float *m_final, double *mism
 /* Differentiable forward (Eq. 2.1b): m(1) from m0 along the characteristics
  * of v, keeping the state only every checkpoint_stride time steps (and at
  * t = 1); *mismatch = 1/2 ||m(1) - m1||^2_{L2} (nullable; synchronizes).
- * m_final: float[N] (nullable).  The first call fixes the stride of ctx.
- * Leaves the Gauss-Newton linearization invalid. */
+ * m_final: float[N] (nullable).  checkpoint_stride in [1, nt], or 0: chosen
+ * from the memory left on the device (and under claire_set_workspace_limit)
+ * -- every state kept (stride 1: the backward recomputes nothing) when that
+ * fits, else the stride that needs the least memory (CLAIRE_ERR_OOM if none
+ * fits).  The first call fixes the stride of ctx (see
+ * claire_checkpoint_stride).  Leaves the Gauss-Newton linearization
+ * invalid.  The memory model follows the paper's Section 5 (the state history
+ * dominates; keep it when it fits, recompute otherwise). */
 int claire_mismatch_forward(claire_ctx *ctx, const float *v, float *m_final, double *mismatch,
                             int checkpoint_stride);
+
+/* Checkpoint stride the differentiable form of ctx uses (0 before its first
+ * claire_mismatch_forward). */
+int claire_checkpoint_stride(const claire_ctx *ctx, int *stride);
 
 /* Backward of the last claire_mismatch_forward (same v): the adjoint of
  * Eq. 3.2 from lambda(1) = grad_mismatch * (m1 - m(1)) - grad_m_final / h^3

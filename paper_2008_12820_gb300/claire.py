@@ -38,6 +38,7 @@ EXPORTED = [
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
     "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization", "claire_solve_batch",
     "claire_mismatch_forward", "claire_mismatch_backward", "claire_solve_host", "claire_set_workspace_limit",
+    "claire_checkpoint_stride",
 ]
 
 
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
         "claire_set_discretization": [P, I, I],
         "claire_mismatch_forward": [P, V, V, pd, I],
         "claire_mismatch_backward": [P, D, V, V],
+        "claire_checkpoint_stride": [P, ctypes.POINTER(ctypes.c_int)],
         "claire_solve_continuation": [P, V, D, D, D, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveReport), ctypes.POINTER(ctypes.c_int)],
     }
@@ -306,7 +308,8 @@ class Registration:
         return m, mis.value
 
     def mismatch_forward(self, v, checkpoint_stride=2, m_final=None):
-        """(m(1), mismatch) keeping the state every checkpoint_stride steps."""
+        """(m(1), mismatch) keeping the state every checkpoint_stride steps
+        (0: chosen from the free device memory, see checkpoint_stride())."""
         pv = self._vec(v, "v")
         m = m_final if m_final is not None else self._new()
         mis = ctypes.c_double(0)
@@ -321,6 +324,12 @@ class Registration:
         g = out if out is not None else self._new(3)
         self._c("claire_mismatch_backward", float(grad_mismatch), pg, self._vec(g, "out"))
         return g
+
+    def checkpoint_stride(self):
+        """stride of the differentiable form (0 before its first forward)"""
+        k = ctypes.c_int(0)
+        self._c("claire_checkpoint_stride", ctypes.byref(k))
+        return k.value
 
     def objective(self, v):
         J, mis = ctypes.c_double(0), ctypes.c_double(0)

@@ -609,13 +609,38 @@ struct claire_ctx {
     }
 
     // ---- differentiable transport with state checkpointing -----------------
-    // checkpoints m^j at j = 0, k, 2k, ... and nt; segment buffers for the
-    // recomputation in the backward pass
-    float *ck = nullptr, *seg_m = nullptr, *seg_g = nullptr, *bacc = nullptr, *lam2 = nullptr;
+    // checkpoints m^j at j = 0, k, 2k, ... and nt; a buffer for the states of
+    // one segment (recomputed in the backward pass; none when k = 1, where
+    // every state is a checkpoint); one gradient buffer (each grad m^j is
+    // taken once, right before its body-force term)
+    float *ck = nullptr, *seg_m = nullptr, *gbuf = nullptr, *bacc = nullptr, *lam2 = nullptr;
     int ck_stride = 0;
     bool ck_valid = false;
     int n_ck() const { return (nt + ck_stride - 1) / ck_stride + 1; }
     int ck_slot(int j) const { return j == nt ? n_ck() - 1 : j / ck_stride; }
+    // floats of N the differentiable form holds for stride k
+    long long ck_fields(int k) const { return (nt + k - 1) / k + 1 + (k > 1 ? k + 1 : 0) + 3 + 3 + 2; }
+
+    // stride for checkpoint_stride = 0: keep every state (no recomputation)
+    // when that fits the memory left (the device's free memory less a reserve,
+    // and the workspace cap if one is set); otherwise the stride that needs
+    // the least memory; CLAIRE_ERR_OOM if even that does not fit
+    int auto_stride() const {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const size_t reserve = 256ull << 20;
+        double budget = free_b > reserve ? (double)(free_b - reserve) : 0.0;
+        const size_t cap = g_workspace_limit.load();
+        if (cap) budget = std::min(budget, cap > bytes ? (double)(cap - bytes) : 0.0);
+        const double fb = 4.0 * (double)d.N;
+        if ((double)ck_fields(1) * fb <= budget) return 1;
+        int best = 1;
+        for (int k = 2; k <= nt; ++k)
+            if (ck_fields(k) < ck_fields(best)) best = k;
+        if ((double)ck_fields(best) * fb > budget)
+            throw Error(CLAIRE_ERR_OOM, "differentiable form: no checkpoint stride fits the free device memory");
+        return best;
+    }
 
     void ensure_ck(int stride) {
         if (stride != ck_stride) {
@@ -624,13 +649,13 @@ struct claire_ctx {
             const size_t mark = allocs.size(), bytes0 = bytes;
             try {
                 float *c0 = alloc_f((size_t)((nt + stride - 1) / stride + 1) * d.N);
-                float *c1 = alloc_f((size_t)(stride + 1) * d.N);
-                float *c2 = alloc_f((size_t)(stride + 1) * 3 * d.N);
+                float *c1 = stride > 1 ? alloc_f((size_t)(stride + 1) * d.N) : nullptr;
+                float *c2 = alloc_f(3 * (size_t)d.N);
                 float *c3 = alloc_f(3 * (size_t)d.N);
                 float *c4 = alloc_f(2 * (size_t)d.N);
                 ck = c0;
                 seg_m = c1;
-                seg_g = c2;
+                gbuf = c2;
                 bacc = c3;
                 lam2 = c4;
                 ck_stride = stride;
@@ -642,9 +667,11 @@ struct claire_ctx {
     }
 
     // forward transport keeping only checkpoints; X-, X+ and c at v kept for
-    // the backward; returns the mismatch 1/2 ||m(1) - m1||^2
+    // the backward; returns the mismatch 1/2 ||m(1) - m1||^2.  stride 0: the
+    // stride is chosen from the free memory (auto_stride) at the first call
     double diff_forward(const float *v, float *m_final, int stride) {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
+        if (stride == 0) stride = ck_stride ? ck_stride : auto_stride();
         ensure_ck(stride);
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -670,8 +697,10 @@ struct claire_ctx {
     }
 
     // backward of (mismatch, m(1)) -> v: adjoint from l(1) = gmis (m1 - m(1))
-    // - gm_final / h^3, segments recomputed from the checkpoints, body force
-    // accumulated by the trapezoidal rule; grad_v = h^3 b (Euclidean)
+    // - gm_final / h^3, segments recomputed from the checkpoints (none when
+    // every state is a checkpoint), body force accumulated by the trapezoidal
+    // rule level by level from t = 1 down to 0, each grad m^j taken once;
+    // grad_v = h^3 b (Euclidean)
     void diff_backward(double gmis, const float *gm_final, float *grad_v) {
         if (!ck_valid) throw Error(CLAIRE_ERR_STATE, "no differentiable forward at this point");
         const size_t N = d.N;
@@ -684,20 +713,32 @@ struct claire_ctx {
         const int nseg = (nt + ck_stride - 1) / ck_stride;
         for (int sgi = nseg - 1; sgi >= 0; --sgi) {
             const int j0 = sgi * ck_stride, j1 = std::min(j0 + ck_stride, nt);
-            // recompute m^j, j0..j1, and their gradients
-            CK(cudaMemcpyAsync(seg_m, ck + (size_t)ck_slot(j0) * N, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
-            for (int j = j0; j < j1; ++j)
-                launch_state_step(d, seg_m + (size_t)(j - j0) * N, dispm, rng_m(), seg_m + (size_t)(j + 1 - j0) * N,
-                                  st, &prof);
-            for (int j = j0; j <= j1; ++j) grad(seg_m + (size_t)(j - j0) * N, seg_g + (size_t)(j - j0) * 3 * N);
-            // adjoint steps j1 -> j0, body force of levels j1 .. j0+1 (and j0 = 0)
+            // the states m^j, j0..j1, of the segment: the checkpoints
+            // themselves for stride 1, else recomputed from m^{j0}
+            auto state = [&](int j) -> const float * {
+                if (ck_stride == 1) return ck + (size_t)ck_slot(j) * N;
+                return seg_m + (size_t)(j - j0) * N;
+            };
+            if (ck_stride > 1) {
+                CK(cudaMemcpyAsync(seg_m, ck + (size_t)ck_slot(j0) * N, N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   st));
+                for (int j = j0; j < j1; ++j)
+                    launch_state_step(d, seg_m + (size_t)(j - j0) * N, dispm, rng_m(), seg_m + (size_t)(j + 1 - j0) * N,
+                                      st, &prof);
+            }
+            // body-force terms of levels j1 .. j0+1 with the adjoint steps
+            // j1 -> j0 (and the level j0 = 0 term at the very end)
             for (int j = j1; j > j0; --j) {
                 const float w = (j == nt ? 0.5f : 1.f) * dt;
-                launch_bodyforce_acc(d, bacc, lam, seg_g + (size_t)(j - j0) * 3 * N, w, st, &prof);
+                grad(state(j), gbuf);
+                launch_bodyforce_acc(d, bacc, lam, gbuf, w, st, &prof);
                 launch_adjoint_step(d, lam, dispp, rng_p(), cfac, lam_next, st, &prof, CLAIRE_K_ADJOINT);
                 float *t = lam; lam = lam_next; lam_next = t;
             }
-            if (j0 == 0) launch_bodyforce_acc(d, bacc, lam, seg_g, 0.5f * dt, st, &prof);
+            if (j0 == 0) {
+                grad(state(0), gbuf);
+                launch_bodyforce_acc(d, bacc, lam, gbuf, 0.5f * dt, st, &prof);
+            }
         }
         launch_axpby(grad_v, (float)H3, bacc, 0.f, nullptr, 3 * (long long)N, st, &prof);
         check_launch("mismatch_backward");
@@ -1000,13 +1041,18 @@ int claire_mismatch_forward(claire_ctx *ctx, const float *v, float *m_final, dou
                             int checkpoint_stride) {
     API_BEGIN(ctx)
     need(v, "v");
-    if (checkpoint_stride < 1 || checkpoint_stride > ctx->nt)
-        throw Error(CLAIRE_ERR_ARG, "checkpoint_stride must be in [1, nt]");
+    if (checkpoint_stride < 0 || checkpoint_stride > ctx->nt)
+        throw Error(CLAIRE_ERR_ARG, "checkpoint_stride must be in [0, nt] (0: chosen from the free memory)");
     const double mis = ctx->diff_forward(v, m_final, checkpoint_stride);
     if (mismatch) *mismatch = mis;
     API_END(ctx)
 }
 
+int claire_checkpoint_stride(const claire_ctx *ctx, int *stride) {
+    if (!ctx || !stride) return CLAIRE_ERR_ARG;
+    *stride = ctx->ck_stride;
+    return CLAIRE_OK;
+}
 int claire_mismatch_backward(claire_ctx *ctx, double grad_mismatch, const float *grad_m_final,
                              float *grad_v) {
     API_BEGIN(ctx)

@@ -84,6 +84,45 @@ def test_checkpoint_stride_does_not_change_the_gradient(C):
         assert np.array_equal(gv, out[0][1])
 
 
+def test_checkpoint_stride_chosen_from_free_memory(C):
+    """stride 0: every state kept (stride 1, nothing recomputed) when the
+    memory allows; under a workspace cap that leaves room only for a sparser
+    set of checkpoints, the stride that needs the least memory; the gradient
+    is the same bit for bit either way."""
+    claire, ag = C
+    n, nt = 48, 8
+    w, v = setup(n)
+    out = []
+    with claire.Registration((n, n, n), nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        out.append(gpu_grad(C, reg, v, 0))
+        assert reg.checkpoint_stride() == 1
+    # the differentiable form needs (ceil(nt/k) + 1 + (k + 1 if k > 1) + 8) N
+    # floats: 17 N for k = 1, 16 N for k = 2, 3, 4; a cap between the two
+    # leaves k = 2 (the first stride of least memory)
+    N = n ** 3
+    with claire.Registration((n, n, n), nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        held = reg.workspace_bytes()
+        try:
+            claire.set_workspace_limit(held + int(16.5 * 4 * N))
+            out.append(gpu_grad(C, reg, v, 0))
+            assert reg.checkpoint_stride() == 2
+        finally:
+            claire.set_workspace_limit(0)
+    with claire.Registration((n, n, n), nt, 1e-2, 1.0) as reg:
+        reg.set_images(dev(w["m0"]), dev(w["m1"]))
+        held = reg.workspace_bytes()
+        try:
+            claire.set_workspace_limit(held + int(15.5 * 4 * N))
+            with pytest.raises(claire.ClaireError) as e:
+                gpu_grad(C, reg, v, 0)
+            assert e.value.code == 2
+        finally:
+            claire.set_workspace_limit(0)
+    assert out[1][0] == out[0][0] and np.array_equal(out[1][1], out[0][1])
+
+
 def test_upstream_gradient_on_m1(C):
     """loss = mismatch + <w, m(1)>: the adjoint starts from m1 - m(1) - w/h^3."""
     claire, ag = C
