@@ -373,6 +373,14 @@ int claire_set_workspace_limit(size_t bytes);
 int claire_precond_noalloc(int nx, int ny, int nz, double beta, double gamma, const float *r,
                            float *s, void *stream);
 
+/* Debug build only (compiled with -DCLAIRE_CHECKS, libclaire_gb_checks.so):
+ * the number of shared-memory box stencils the transport kernels found
+ * outside the part of the box their copy wrote since the last reset (each is
+ * counted and not read).  Synchronizes the device; reset != 0 clears the
+ * count.  The release build returns CLAIRE_ERR_STATE with *count = 0.  No
+ * counterpart in the paper (its kernels are checked on the CPU here too). */
+int claire_check_count(unsigned long long *count, int reset);
+
 /* Message of the last error on ctx (or of the last failed claire_create when
  * ctx is NULL); never NULL. */
 const char *claire_last_error(const claire_ctx *ctx);

@@ -38,7 +38,7 @@ EXPORTED = [
     "claire_workspace_bytes", "claire_last_error", "claire_precond_noalloc",
     "claire_precond_h0", "claire_solve_continuation", "claire_set_discretization", "claire_solve_batch",
     "claire_mismatch_forward", "claire_mismatch_backward", "claire_solve_host", "claire_set_workspace_limit",
-    "claire_checkpoint_stride",
+    "claire_checkpoint_stride", "claire_check_count",
 ]
 
 
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "claire_mismatch_forward": [P, V, V, pd, I],
         "claire_mismatch_backward": [P, D, V, V],
         "claire_checkpoint_stride": [P, ctypes.POINTER(ctypes.c_int)],
+        "claire_check_count": [ctypes.POINTER(ctypes.c_ulonglong), I],
         "claire_solve_continuation": [P, V, D, D, D, ctypes.POINTER(SolveOpts),
                                       ctypes.POINTER(SolveReport), ctypes.POINTER(ctypes.c_int)],
     }
@@ -182,6 +183,16 @@ def set_workspace_limit(nbytes):
     rc = load().claire_set_workspace_limit(int(nbytes))
     if rc != CLAIRE_OK:
         raise ClaireError(rc, "claire_set_workspace_limit")
+
+
+def check_count(reset=False):
+    """Box-stencil violations counted by the debug build (claire_check_count);
+    raises in the release build, which has no counter."""
+    n = ctypes.c_ulonglong(0)
+    rc = load().claire_check_count(ctypes.byref(n), 1 if reset else 0)
+    if rc != CLAIRE_OK:
+        raise ClaireError(rc, "claire_check_count: the loaded library is not the checks build")
+    return n.value
 
 
 def precond_noalloc(r, s, beta, gamma, stream=None):

@@ -208,6 +208,7 @@ struct claire_ctx {
     }
     ~claire_ctx() {
         if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
+        drop_inner_graphs();
         if (aux) {
             cudaStreamSynchronize(aux);
             cudaStreamDestroy(aux);
@@ -311,8 +312,153 @@ struct claire_ctx {
     // iterations if fixed); H0 = beta0 A + gm (x) gm.  beta0 A p is carried by
     // the same recurrence as in the outer PCG.  work: 5 vectors of g.  Uses
     // result slots dres[4..7] so the caller's residual sums survive.
+    // The inner PCG as one CUDA graph: the setup (s = 0, r, ||r0||, the first
+    // preconditioned direction) and a conditional WHILE node whose body is one
+    // PCG iteration.  Step length, direction ratio and the stopping test are
+    // evaluated on the device in the same FP64 arithmetic as the host-driven
+    // loop below (same iterates and counts), so an inner solve costs one graph
+    // launch and one host read instead of three round trips per iteration.
+    // The executable graph is cached per grid and buffer set; the tolerance
+    // goes through device memory.  Used on streams that can be captured and
+    // when the profiler is off; a runtime that refuses conditional nodes turns
+    // it off for the context (the host-driven loop then runs).
+    struct InnerGraph {
+        cudaGraphExec_t exec = nullptr;
+        const float *gm = nullptr, *r = nullptr;
+        float *s = nullptr, *work = nullptr;
+        long long N = 0;
+        int maxit = 0;
+        bool fixed = false;
+        double beta0 = 0, gamma = 0;  // baked into the captured transforms
+        long k_init = 0, k_body = 0;  // kernels of the setup and of one body
+    } igr[2];
+    double *ictl = nullptr;  // device scalars of the inner solve (16 doubles)
+    bool inner_graphs = true;
+
+    void drop_inner_graphs() {
+        for (auto &e : igr)
+            if (e.exec) {
+                cudaGraphExecDestroy(e.exec);
+                e.exec = nullptr;
+            }
+    }
+
+    // the launches of one inner solve's setup and loop body (captured)
+    void inner_setup(const Grid &g, const float *r, float *s, float *work) {
+        const long long N = g.d.N, n3 = 3 * N;
+        float *ir = work, *iz = ir + n3, *ip = iz + n3, *iAp = ip + n3 + n3;
+        const double b0 = beta_h0();
+        const SpecParams spb{(float)b0, (float)gamma, (float)(1.0 / (double)N)};
+        CK(cudaMemsetAsync(s, 0, n3 * sizeof(float), st));
+        CK(cudaMemcpyAsync(ir, r, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        launch_stats(ir, N, partial, ictl + 6, st, &prof);
+        launch_inner_init(ictl, st, &prof);
+        spectral_apply(g.d, g.ax, OP_AINV, spb, ir, iz, nullptr, g.spec, st, &prof);
+        launch_pcg_dir(ip, iAp, iz, ir, ictl + 7, nullptr, 0.f, N, true, st, &prof);
+        launch_dot(ir, iz, n3, partial, ictl + 3, st, &prof);
+    }
+    void inner_body(const Grid &g, const float *gm, float *s, float *work, cudaGraphConditionalHandle h, int maxit,
+                    bool fixed) {
+        const long long N = g.d.N, n3 = 3 * N;
+        float *ir = work, *iz = ir + n3, *ip = iz + n3, *iq = ip + n3, *iAp = iq + n3;
+        const double b0 = beta_h0();
+        const SpecParams spb{(float)b0, (float)gamma, (float)(1.0 / (double)N)};
+        launch_h0_apply(iq, iAp, gm, ip, N, st, &prof);
+        launch_dot(ip, iq, n3, partial, ictl + 2, st, &prof);
+        launch_pcg_update(s, nullptr, ir, ip, iAp, iq, 0.f, N, partial, ictl + 6, st, &prof, false, ictl + 2,
+                          ictl + 3, nullptr);
+        launch_inner_ctl(ictl, h, maxit, fixed, st, &prof);
+        // the next direction (also after the last step, where it is unused)
+        spectral_apply(g.d, g.ax, OP_AINV, spb, ir, iz, nullptr, g.spec, st, &prof);
+        launch_dot(ir, iz, n3, partial, ictl + 4, st, &prof);
+        launch_pcg_dir(ip, iAp, iz, ir, ictl + 7, nullptr, 0.f, N, false, st, &prof, ictl + 4, ictl + 3);
+        launch_scalar_copy(ictl + 3, ictl + 4, st, &prof);
+    }
+
+    // builds (or reuses) the graph of grid slot `which` and runs it; false if
+    // the runtime refused (nothing has run then)
+    bool invh0_graph(const Grid &g, const float *gm, const float *r, float *s, double tol, int maxit, bool fixed,
+                     float *work, int which, int &iters) {
+        if (!ictl) ictl = (double *)alloc_bytes(16 * sizeof(double));
+        InnerGraph &e = igr[which];
+        const bool same = e.exec && e.gm == gm && e.r == r && e.s == s && e.work == work && e.N == g.d.N &&
+                          e.maxit == maxit && e.fixed == fixed && e.beta0 == beta_h0() && e.gamma == gamma;
+        if (!same) {
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+            e.exec = nullptr;
+            cudaGraph_t G = nullptr, gi = nullptr;
+            cudaGraphNode_t ni = nullptr, nc = nullptr;
+            cudaGraphConditionalHandle h = 0;
+            bool ok = cudaGraphCreate(&G, 0) == cudaSuccess &&
+                      cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+            const long k0 = prof.launches;
+            long k1 = k0, k2 = k0;
+            auto capture_into = [&](cudaGraph_t *dst, cudaGraph_t into, auto &&launches) -> bool {
+                cudaError_t st0 = into ? cudaStreamBeginCaptureToGraph(st, into, nullptr, nullptr, 0,
+                                                                       cudaStreamCaptureModeThreadLocal)
+                                       : cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (st0 != cudaSuccess) return false;
+                try {
+                    launches();
+                } catch (...) {
+                    cudaGraph_t tmp = nullptr;
+                    cudaStreamEndCapture(st, &tmp);
+                    if (tmp && !into) cudaGraphDestroy(tmp);
+                    throw;
+                }
+                cudaGraph_t out = nullptr;
+                if (cudaStreamEndCapture(st, &out) != cudaSuccess || !out) return false;
+                if (dst) *dst = out;
+                return true;
+            };
+            if (ok) ok = capture_into(&gi, nullptr, [&] { inner_setup(g, r, s, work); });
+            k1 = prof.launches;
+            if (ok) ok = cudaGraphAddChildGraphNode(&ni, G, nullptr, 0, gi) == cudaSuccess;
+            if (gi) cudaGraphDestroy(gi);
+            cudaGraphNodeParams cp = {};
+            if (ok) {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                ok = cudaGraphAddNode(&nc, G, &ni, nullptr, 1, &cp) == cudaSuccess;
+            }
+            if (ok)
+                ok = capture_into(nullptr, cp.conditional.phGraph_out[0],
+                                  [&] { inner_body(g, gm, s, work, h, maxit, fixed); });
+            k2 = prof.launches;
+            if (ok) ok = cudaGraphInstantiate(&e.exec, G, 0) == cudaSuccess;
+            if (G) cudaGraphDestroy(G);
+            prof.launches = k0;
+            if (!ok) {
+                cudaGetLastError();
+                e.exec = nullptr;
+                inner_graphs = false;
+                return false;
+            }
+            e.gm = gm; e.r = r; e.s = s; e.work = work; e.N = g.d.N; e.maxit = maxit; e.fixed = fixed;
+            e.beta0 = beta_h0();
+            e.gamma = gamma;
+            e.k_init = k1 - k0;
+            e.k_body = k2 - k1;
+        }
+        launch_scalar_set(ictl, tol, st, &prof);
+        CK(cudaGraphLaunch(e.exec, st));
+        check_launch("invh0 graph");
+        double h[11];
+        CK(cudaMemcpyAsync(h, ictl, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        iters = (int)h[5];
+        prof.launches += e.k_init + (long)h[10] * e.k_body;
+        return true;
+    }
+
     int invh0_on(const Grid &g, const float *gm, const float *r, float *s, double tol, int maxit,
-                 bool fixed, float *work) {
+                 bool fixed, float *work, int which = 0) {
+        if (inner_graphs && use_graphs && capturable(st) && !prof.on) {
+            int it = 0;
+            if (invh0_graph(g, gm, r, s, tol, maxit, fixed, work, which, it)) return it;
+        }
         const long long N = g.d.N, n3 = 3 * N;
         float *ir = work, *iz = ir + n3, *ip = iz + n3, *iq = ip + n3, *iAp = iq + n3;
         const double b0 = beta_h0();
@@ -370,7 +516,7 @@ struct claire_ctx {
         spectral_forward3(d, ax, r, spec, st, &prof);
         launch_spec_restrict(d, spec, co.d, co.spec, f2c, st, &prof);
         spectral_inverse3(co.d, co.ax, co.spec, co.r, (float)(1.0 / (double)co.d.N), st, &prof);
-        const int it = invh0_on(cg, co.gm, co.r, co.s, tol, maxit, fixed, co.work);
+        const int it = invh0_on(cg, co.gm, co.r, co.s, tol, maxit, fixed, co.work, 1);
         spectral_forward3(co.d, co.ax, co.s, co.spec, st, &prof);
         launch_spec_twolevel(d, spec, co.d, co.spec, c2f, (float)beta_h0(), (float)gamma, st, &prof);
         spectral_inverse3(d, ax, spec, s, (float)(1.0 / (double)d.N), st, &prof);

@@ -197,7 +197,16 @@ void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const floa
 // with Az given (beta*A z), Ap = Az + b Ap instead.  x += a p skips Ax if NULL.
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
                     const float *Az, float b, long long N, bool init, cudaStream_t st,
-                    Profiler *prof);
+                    Profiler *prof, const double *dbn = nullptr, const double *dbd = nullptr);
+// device-side control of the inner PCG of the H0 preconditioners (a CUDA
+// graph with a conditional while node); c: the loop's device scalars,
+// c[0] tolerance, c[1] ||r0||, c[2] p.q, c[3] r.z (current direction),
+// c[4] r.z (new residual), c[5] iterations, c[6..9] stats of r, c[10] bodies
+void launch_inner_init(double *c, cudaStream_t st, Profiler *prof);
+void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
+                      Profiler *prof);
+void launch_scalar_copy(double *dst, const double *src, cudaStream_t st, Profiler *prof);
+void launch_scalar_set(double *dst, double v, cudaStream_t st, Profiler *prof);
 // launch_pcg_dir that also writes u0 = dt/2 * (-p . gm0) (N floats), the
 // first incremental-state field of the next matvec (hdt = dt/2), and, with
 // pap_out non-null, p . Ap of the new direction into *pap_out

@@ -295,6 +295,22 @@ constexpr int BOX_PITCH = 64;  // floats per box row: rows start on bank 0
 constexpr int BOX_FLOATS = BS1 * BS2 * BOX_PITCH;
 static_assert(BS3 <= BOX_PITCH && BS3 > PT3, "box row must fit one pitch and exceed a warp");
 
+// Debug build (-DCLAIRE_CHECKS): every box stencil origin is checked before
+// its 64 taps are read -- inside the buffer and inside the columns the box
+// copy wrote -- and a violation is counted in g_check_count and its taps are
+// not read (the value becomes 0).  The release build compiles the check away.
+// The host model of the same geometry is tests/test_box_geometry.py.
+#ifdef CLAIRE_CHECKS
+__device__ unsigned long long g_check_count;
+__device__ __forceinline__ bool box_origin_ok(int b1, int b2, int b3, int ncols) {
+    const bool ok = b1 >= 0 && b1 + 3 < BS1 && b2 >= 0 && b2 + 3 < BS2 && b3 >= 0 && b3 + 3 < ncols;
+    if (!ok) atomicAdd(&g_check_count, 1ull);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool box_origin_ok(int, int, int, int) { return true; }
+#endif
+
 __device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -394,6 +410,8 @@ __device__ __forceinline__ void cp_async16(float *smem, const float *gmem) {
 }
 
 __device__ __forceinline__ int box_shift(int lo3, bool chunked) { return chunked ? lo3 - (lo3 & ~3) : 0; }
+// columns of a box row that the copy writes
+__device__ __forceinline__ int box_cols(bool chunked) { return chunked ? 4 * BOX_CH : BS3; }
 
 __device__ __forceinline__ void box_copy(const float *__restrict__ src, const Dims &d, long long plane, int lo1,
                                          int lo2, int lo3, float *buf, bool chunked) {
@@ -671,8 +689,9 @@ k_sl_pipe(SlArgsT<TS, TG> a, Dims d, const int4 *__restrict__ tiles, int chunked
                         // stencil origin inside the box; every tap is an immediate offset
                         const int b1 = t + (int)fl0 - fmn0, b2 = ty + (int)fl1 - fmn1, b3 = tx + (int)fl2 - fmn2 + sh;
                         const float *p = bx + (b1 * BS2 + b2) * BOX_PITCH + b3;
-                        float acc;
-                        if (ORDER == 1) {
+                        float acc = 0.f;
+                        if (!box_origin_ok(b1, b2, b3, box_cols(chunked))) {
+                        } else if (ORDER == 1) {
                             acc = box_linear(p, dt3[0] - fl0, dt3[1] - fl1, dt3[2] - fl2);
                         } else {
                             float w1[4], w2[4], w3[4];
@@ -844,8 +863,12 @@ k_footpoints_box(const float *__restrict__ v, float *__restrict__ dispm, float *
                     lagrange4(q1 - fl1, w1);
                     lagrange4(q2 - fl2, w2);
                     lagrange4(q3 - fl3, w3);
+                    if (box_origin_ok(b1, b2, b3, box_cols(chunked))) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) w[c] = box_cubic(p + c * BOX_FLOATS, w1, w2, w3);
+                        for (int c = 0; c < 3; ++c) w[c] = box_cubic(p + c * BOX_FLOATS, w1, w2, w3);
+                    } else {
+                        w[0] = w[1] = w[2] = 0.f;
+                    }
                 } else {
                     const float3 g = fp_gather3(v, d, t1 * PT1 + t, i2, i3, q1, q2, q3);
                     w[0] = g.x;
@@ -1176,3 +1199,22 @@ void launch_adjoint_final(const Dims &d, float *l, const float *m1, const float 
 }
 
 }  // namespace claire
+
+// Violations counted by the debug build's box checks since the last reset
+// (CLAIRE_ERR_STATE in the release build, which has no counter).
+extern "C" int claire_check_count(unsigned long long *count, int reset) {
+    if (!count) return CLAIRE_ERR_ARG;
+#ifdef CLAIRE_CHECKS
+    if (cudaDeviceSynchronize() != cudaSuccess) return CLAIRE_ERR_CUDA;
+    if (cudaMemcpyFromSymbol(count, claire::g_check_count, sizeof(*count)) != cudaSuccess) return CLAIRE_ERR_CUDA;
+    if (reset) {
+        const unsigned long long z = 0;
+        if (cudaMemcpyToSymbol(claire::g_check_count, &z, sizeof(z)) != cudaSuccess) return CLAIRE_ERR_CUDA;
+    }
+    return CLAIRE_OK;
+#else
+    (void)reset;
+    *count = 0;
+    return CLAIRE_ERR_STATE;
+#endif
+}

@@ -293,8 +293,11 @@ __global__ void __launch_bounds__(RT) k_finalize4(const double *__restrict__ par
 __global__ void __launch_bounds__(RT) k_pcg_dir(float *__restrict__ p, float *__restrict__ Ap,
                                                 const float *__restrict__ z, const float *__restrict__ r,
                                                 const double *__restrict__ rsum, const float *__restrict__ Az,
-                                                float b, long long N, int init) {
+                                                float b, long long N, int init, const double *__restrict__ dbn,
+                                                const double *__restrict__ dbd) {
     const long long stride = (long long)gridDim.x * RT;
+    // dbn, dbd (optional): b = num / den from device memory
+    if (dbn) b = (float)(*dbn / *dbd);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float mean = Az ? 0.f : (float)(rsum[c] / (double)N);
@@ -538,9 +541,67 @@ void launch_pcg_update(float *x, float *Ax, float *r, const float *p, const floa
 
 void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const double *rsum,
                     const float *Az, float b, long long N, bool init, cudaStream_t st,
-                    Profiler *prof) {
+                    Profiler *prof, const double *dbn, const double *dbd) {
     ProfScope ps(prof, CLAIRE_K_VECTOR, st, 3.0 * N * (init ? 16 : 24));
-    k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0);
+    k_pcg_dir<<<blocks_for(3 * N), RT, 0, st>>>(p, Ap, z, r, rsum, Az, b, N, init ? 1 : 0, dbn, dbd);
+}
+
+// ---- device-side control of the inner PCG of the H0 preconditioners -----
+// c: the inner solve's device scalars (see launch_inner_*): c[0] tolerance,
+// c[1] ||r0||, c[2] p.q, c[3] r.z of the current direction, c[4] r.z of the
+// new residual, c[5] iterations, c[6..9] ||r||^2 and the component sums of r,
+// c[10] loop bodies run.
+namespace {
+__global__ void k_inner_init(double *c) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c[1] = sqrt(c[6]);
+        c[5] = 0.0;
+        c[10] = 0.0;
+    }
+}
+// after the PCG update of one loop body: the same decisions, in the same
+// FP64 arithmetic, as the host-driven loop (stop on p.q <= 0 without counting
+// the step; otherwise count it and stop when ||r|| <= tol ||r0|| -- unless
+// the iteration count is fixed -- or at maxit), and the while condition
+__global__ void k_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, int fixed) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c[10] += 1.0;
+        unsigned int cont = 0;
+        const double pq = c[2];
+        if (pq > 0.0) {
+            const double it = c[5] + 1.0;
+            c[5] = it;
+            const double rn = sqrt(c[6]);
+            const bool conv = !fixed && rn <= c[0] * c[1];
+            cont = (!conv && it < (double)maxit) ? 1u : 0u;
+        }
+        cudaGraphSetConditional(h, cont);
+    }
+}
+__global__ void k_scalar_copy(double *dst, const double *src) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
+}
+__global__ void k_scalar_set(double *dst, double v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+}  // namespace
+
+void launch_inner_init(double *c, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st);
+    k_inner_init<<<1, 32, 0, st>>>(c);
+}
+void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
+                      Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st);
+    k_inner_ctl<<<1, 32, 0, st>>>(c, h, maxit, fixed ? 1 : 0);
+}
+void launch_scalar_copy(double *dst, const double *src, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st);
+    k_scalar_copy<<<1, 32, 0, st>>>(dst, src);
+}
+void launch_scalar_set(double *dst, double v, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st);
+    k_scalar_set<<<1, 32, 0, st>>>(dst, v);
 }
 
 template <typename TG>

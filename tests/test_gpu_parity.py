@@ -484,6 +484,40 @@ def test_solve_with_two_level_invh0(claire):
         assert rel(host(v), vo) < TOL_SOLVE
 
 
+def test_h0_inner_graph_matches_host_loop(claire):
+    """On a stream that can be captured, the inner PCG of InvH0 and 2LInvH0
+    runs as one CUDA graph with a conditional while node (step length,
+    direction ratio and stopping test on the device); on the legacy default
+    stream it runs host-driven.  Both give the same iterates bit for bit and
+    the same inner iteration counts, in fixed-count and tolerance mode."""
+    w = synth.workload("sin32")
+    shape, nt, beta, gamma = w["shape"], w["nt"], w["beta"], w["gamma"]
+    rng = np.random.default_rng(6)
+    r = dev(synth.smooth_direction(shape, 8, kmax=8) + 0.1 * rng.standard_normal((3,) + shape).astype(np.float32))
+    m0, m1, v = make_problem(shape, nt)
+    out = {}
+    for mode in ("host", "graph"):
+        stream = torch.cuda.Stream() if mode == "graph" else None
+        with torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(torch.cuda.default_stream()):
+            with claire.Registration(shape, nt, beta, gamma, stream=stream) as reg:
+                reg.set_images(dev(w["m0"]), dev(w["m1"]))
+                res = []
+                for pc in ("invH0", "2LinvH0"):
+                    vv = torch.zeros((3,) + shape, device="cuda")
+                    rep = reg.solve(vv, precond=pc, eps_h0=1e-3)
+                    res.append((host(vv), rep.n_gn, rep.n_pcg, rep.n_inner, rep.J))
+                reg.linearize(dev(v))
+                for two in (False, True):
+                    for tol, maxit in ((0.0, 8), (1e-3, 500)):
+                        sres, it = reg.precond_h0(r, tol=tol, maxit=maxit, two_level=two)
+                        res.append((host(sres), it))
+                torch.cuda.synchronize()
+        out[mode] = res
+    for a, b in zip(out["host"], out["graph"]):
+        assert np.array_equal(a[0], b[0])
+        assert a[1:] == b[1:], (a[1:], b[1:])
+
+
 def test_beta_continuation_matches_oracle(claire):
     """beta-continuation 1 -> 0.1 -> 0.01 with InvA above 0.5 and InvH0 below
     (Section 3 "Preconditioning", last paragraph)."""
