@@ -209,6 +209,7 @@ struct claire_ctx {
     ~claire_ctx() {
         if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
         drop_inner_graphs();
+        drop_pcg_graphs();
         if (aux) {
             cudaStreamSynchronize(aux);
             cudaStreamDestroy(aux);
@@ -334,6 +335,34 @@ struct claire_ctx {
     } igr[2];
     double *ictl = nullptr;  // device scalars of the inner solve (16 doubles)
     bool inner_graphs = true;
+
+    // The outer PCG loop of the solver with the InvA preconditioner as one
+    // CUDA graph: a conditional WHILE node whose body is one PCG iteration
+    // (matvec, update, the device-side stopping test, the preconditioner and
+    // the next direction).  Cached per buffer set; the line search alternates
+    // the X- buffers, so two variants live at once.
+    struct PcgGraph {
+        cudaGraphExec_t exec = nullptr;
+        const float *dispm = nullptr;
+        const int4 *rng = nullptr;
+        const float *sv = nullptr;
+        int maxit = 0, iorder = 0;
+        bool fixed = false;
+        double beta = 0, gamma = 0;
+        long k_body = 0;
+        unsigned long long used = 0;
+    } pgr[2];
+    unsigned long long pgr_clock = 0;
+    double *octl = nullptr;  // device scalars of the outer loop (16 doubles)
+    bool pcg_graphs = true;
+
+    void drop_pcg_graphs() {
+        for (auto &e : pgr)
+            if (e.exec) {
+                cudaGraphExecDestroy(e.exec);
+                e.exec = nullptr;
+            }
+    }
 
     void drop_inner_graphs() {
         for (auto &e : igr)
@@ -1457,12 +1486,104 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
             // the direction update beta = rz_new / rz from there.  One host
             // read per iteration (r . r for the stopping test, p . Hp kept in
             // dres[12] for the curvature test) instead of three.
+            // the loop as a graph (InvA, a stream that can be captured, the
+            // profiler off): one launch and one host read per GN step
+            auto pcg_graph = [&](int &iters) -> bool {
+                claire_ctx &c = *ctx;
+                if (!c.octl) c.octl = (double *)c.alloc_bytes(16 * sizeof(double));
+                const bool fixed = o.fixed_pcg > 0;
+                int slot = -1;
+                for (int i = 0; i < 2; ++i) {
+                    const auto &e = c.pgr[i];
+                    if (e.exec && e.dispm == c.dispm && e.rng == c.rng_m() && e.sv == c.sv && e.maxit == maxit &&
+                        e.fixed == fixed && e.beta == c.beta && e.gamma == c.gamma && e.iorder == c.d.iorder)
+                        slot = i;
+                }
+                if (slot < 0) {
+                    // replace the least recently used variant
+                    slot = c.pgr[0].used <= c.pgr[1].used ? 0 : 1;
+                    auto &e = c.pgr[slot];
+                    if (e.exec) cudaGraphExecDestroy(e.exec);
+                    e.exec = nullptr;
+                    cudaGraph_t G = nullptr;
+                    cudaGraphNode_t nc = nullptr;
+                    cudaGraphConditionalHandle h = 0;
+                    bool ok = cudaGraphCreate(&G, 0) == cudaSuccess &&
+                              cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+                    cudaGraphNodeParams cp = {};
+                    if (ok) {
+                        cp.type = cudaGraphNodeTypeConditional;
+                        cp.conditional.handle = h;
+                        cp.conditional.type = cudaGraphCondTypeWhile;
+                        cp.conditional.size = 1;
+                        ok = cudaGraphAddNode(&nc, G, nullptr, nullptr, 0, &cp) == cudaSuccess;
+                    }
+                    const long k0 = c.prof.launches;
+                    if (ok)
+                        ok = cudaStreamBeginCaptureToGraph(st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                    if (ok) {
+                        try {
+                            c.matvec_launches(p, q, true);
+                            launch_pcg_update(x, Ax, r, p, Ap, q, 0.f, N, c.partial, c.dres, st, &c.prof, true,
+                                              c.dres, c.dres + 10, c.dres + 12);
+                            launch_pcg_ctl(c.dres, c.octl, h, maxit, fixed, st, &c.prof);
+                            launch_pcg_negcopy(c.octl, x, Ax, z, Ap, n3, st, &c.prof);
+                            c.spectral(OP_AINV, r, z, nullptr);
+                            launch_dot(r, z, n3, c.partial, c.dres + 11, st, &c.prof);
+                            pcg_dir(nullptr, false, 11, 10);
+                            launch_scalar_copy(c.dres + 10, c.dres + 11, st, &c.prof);
+                        } catch (...) {
+                            cudaGraph_t tmp = nullptr;
+                            cudaStreamEndCapture(st, &tmp);
+                            cudaGraphDestroy(G);
+                            c.prof.launches = k0;
+                            throw;
+                        }
+                        cudaGraph_t out = nullptr;
+                        ok = cudaStreamEndCapture(st, &out) == cudaSuccess && out;
+                    }
+                    const long kb = c.prof.launches - k0;
+                    c.prof.launches = k0;
+                    if (ok) ok = cudaGraphInstantiate(&e.exec, G, 0) == cudaSuccess;
+                    if (G) cudaGraphDestroy(G);
+                    if (!ok) {
+                        cudaGetLastError();
+                        e.exec = nullptr;
+                        c.pcg_graphs = false;
+                        return false;
+                    }
+                    e.dispm = c.dispm; e.rng = c.rng_m(); e.sv = c.sv; e.maxit = maxit; e.fixed = fixed;
+                    e.beta = c.beta; e.gamma = c.gamma; e.iorder = c.d.iorder; e.k_body = kb;
+                }
+                auto &e = c.pgr[slot];
+                e.used = ++c.pgr_clock;
+                launch_pcg_ctl_init(c.octl, epsk * r0, st, &c.prof);
+                CK(cudaGraphLaunch(e.exec, st));
+                check_launch("pcg graph");
+                double hc[4];
+                CK(cudaMemcpyAsync(hc, c.octl, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                c.prof.launches += (long)hc[3] * e.k_body;
+                if (hc[2] == 1.0) throw Error(CLAIRE_ERR_NONFINITE, "non-finite p.Hp in PCG");
+                iters = (int)hc[1];
+                return true;
+            };
             if (r0 > 0) {
                 const float *Az = apply_pc();
                 pcg_dir(Az, true, 0, 0);
                 int rz = 10;
                 launch_dot(r, z, n3, ctx->partial, ctx->dres + rz, st, &ctx->prof);
-                while (it < maxit) {
+                const bool use_graph = o.precond == CLAIRE_PC_INVA && ctx->pcg_graphs && ctx->use_graphs &&
+                                       claire_ctx::capturable(st) && !ctx->prof.on;
+                int git = 0;
+                const bool by_graph = use_graph && pcg_graph(git);
+                if (by_graph) {
+                    it = git;
+                    rep.n_matvec += it;
+                    rep.n_precond += it - 1;  // the first one is counted above
+                }
+                while (!by_graph && it < maxit) {
                     {
                         Nvtx nv("hess_matvec");
                         EvTimer t(st, &rep.t_hess_ms);

@@ -206,6 +206,14 @@ void launch_inner_init(double *c, cudaStream_t st, Profiler *prof);
 void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
                       Profiler *prof);
 void launch_scalar_copy(double *dst, const double *src, cudaStream_t st, Profiler *prof);
+// device-side control of the outer PCG loop (InvA) as a graph: k_pcg_ctl
+// reads d[0] (||r||^2) and d[12] (p.Hp) of the solver's result slots and
+// keeps c[0] threshold, c[1] iterations, c[2] flags, c[3] bodies
+void launch_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
+                    Profiler *prof);
+void launch_pcg_negcopy(const double *c, float *x, float *Ax, const float *z, const float *Ap, long long n,
+                        cudaStream_t st, Profiler *prof);
+void launch_pcg_ctl_init(double *c, double thr, cudaStream_t st, Profiler *prof);
 void launch_scalar_set(double *dst, double v, cudaStream_t st, Profiler *prof);
 // launch_pcg_dir that also writes u0 = dt/2 * (-p . gm0) (N floats), the
 // first incremental-state field of the next matvec (hdt = dt/2), and, with

@@ -578,6 +578,51 @@ __global__ void k_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, 
         cudaGraphSetConditional(h, cont);
     }
 }
+// after the PCG update of one outer loop body: the decisions of the
+// host-driven loop in the same FP64 arithmetic.  d: the solver's result
+// slots (d[0] ||r||^2 after the update, d[12] p.Hp); c: the loop's scalars
+// (c[0] stopping threshold eps_K ||r0||, c[1] iterations, c[2] flags: 1
+// non-finite p.Hp, 2 non-positive curvature in the first iteration, c[3]
+// bodies run).  Non-finite p.Hp stops the loop; p.Hp <= 0 counts the step and
+// stops (the update changed nothing); otherwise count and test.
+__global__ void k_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, int maxit, int fixed) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c[3] += 1.0;
+        const double pq = d[12];
+        unsigned int cont = 0;
+        if (!(pq >= -1.7976931348623157e308 && pq <= 1.7976931348623157e308)) {
+            c[2] = 1.0;
+        } else if (!(pq > 0.0)) {
+            if (c[1] == 0.0) c[2] = 2.0;
+            c[1] += 1.0;
+        } else {
+            const double it = c[1] + 1.0;
+            c[1] = it;
+            const double rn = sqrt(d[0]);
+            const bool conv = !fixed && rn <= c[0];
+            cont = (!conv && it < (double)maxit) ? 1u : 0u;
+        }
+        cudaGraphSetConditional(h, cont);
+    }
+}
+// negative curvature in the first PCG iteration keeps the preconditioned
+// residual: x = z, Ax = Ap (flag c[2] == 2, set by k_pcg_ctl); otherwise a
+// no-op
+__global__ void k_pcg_negcopy(const double *c, float *__restrict__ x, float *__restrict__ Ax,
+                              const float *__restrict__ z, const float *__restrict__ Ap, long long n) {
+    if (c[2] != 2.0) return;
+    for (long long i = blockIdx.x * (long long)RT + threadIdx.x; i < n; i += (long long)gridDim.x * RT) {
+        x[i] = z[i];
+        Ax[i] = Ap[i];
+    }
+}
+__global__ void k_pcg_ctl_init(double *c, double thr) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c[0] = thr;
+        c[1] = c[2] = c[3] = 0.0;
+    }
+}
+
 __global__ void k_scalar_copy(double *dst, const double *src) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
 }
@@ -594,6 +639,20 @@ void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, bool f
                       Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st);
     k_inner_ctl<<<1, 32, 0, st>>>(c, h, maxit, fixed ? 1 : 0);
+}
+void launch_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
+                    Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st);
+    k_pcg_ctl<<<1, 32, 0, st>>>(d, c, h, maxit, fixed ? 1 : 0);
+}
+void launch_pcg_negcopy(const double *c, float *x, float *Ax, const float *z, const float *Ap, long long n,
+                        cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_VECTOR, st);
+    k_pcg_negcopy<<<blocks_for(n), RT, 0, st>>>(c, x, Ax, z, Ap, n);
+}
+void launch_pcg_ctl_init(double *c, double thr, cudaStream_t st, Profiler *prof) {
+    ProfScope ps(prof, CLAIRE_K_REDUCE, st);
+    k_pcg_ctl_init<<<1, 32, 0, st>>>(c, thr);
 }
 void launch_scalar_copy(double *dst, const double *src, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st);
