@@ -62,14 +62,15 @@ KCLASS = ["footpoint", "state", "adjoint", "incstate", "incadj", "bodyforce", "f
 # argument of k_sl_pipe is the step kind: 0 plain, 1 adjoint, 2 incremental
 # state, 3 adjoint factor, 4 last incremental-state step, 5 adjoint step that
 # adds its body-force term, 6 the same with the curvature dot
-KNAMES = {"footpoint": "k_footpoints, k_range_init, k_floor_range, k_sl_pipe<3, *>",
+KNAMES = {"footpoint": "k_footpoints_box, k_footpoints, k_tile_ranges, k_sl_pipe<3, *>",
           "state": "k_sl_pipe<0, *>", "adjoint": "k_sl_pipe<5, *>", "incstate": "k_sl_pipe<2, *>, k_sl_pipe<4, *>",
-          "incadj": "k_sl_pipe<5, *>, k_sl_pipe<6, *>", "bodyforce": "k_adjfinal_acc", "fft_r2c": "k_r2c_x3",
-          "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1", "fft_c2r": "k_c2r_x3",
+          "incadj": "k_sl_pipe<5, *>, k_sl_pipe<6, *>", "bodyforce": "k_adjfinal_acc",
+          "fft_r2c": "k_r2c_x3_p (k_r2c_x3 for unaligned rows)", "fft_c2c": "k_c2c_x2", "fft_mul": "k_mul_x1",
+          "fft_c2r": "k_c2r_x3_p (k_c2r_x3 for unaligned spectra)",
           "reduce": "k_reduce2, k_stats, k_finalize, k_finalize4",
           "vector": "k_pcg_update, k_pcg_dir_u0, k_axpby, k_incstate_init, k_f2h, k_h2f",
           "interp": "k_sl_pipe<0, *>", "fd": "k_grad_fd8, k_div_fd8",
-          "deriv": "k_deriv_x3, k_deriv_strided"}
+          "deriv": "k_deriv_x3_p, k_deriv_strided_p (k_deriv_x3, k_deriv_strided for unaligned rows)"}
 
 
 # the transport and transform classes (every one of them is asked to reach

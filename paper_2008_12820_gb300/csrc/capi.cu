@@ -313,6 +313,110 @@ struct claire_ctx {
     // iterations if fixed); H0 = beta0 A + gm (x) gm.  beta0 A p is carried by
     // the same recurrence as in the outer PCG.  work: 5 vectors of g.  Uses
     // result slots dres[4..7] so the caller's residual sums survive.
+    // ---- loops as CUDA graphs ---------------------------------------------
+    // Builds [setup] -> WHILE(hw) { head ; IF(hif) { tail } } and instantiates
+    // it.  head ends with a control kernel that sets both conditions (the
+    // loop's and the tail's) to "continue": the tail -- preconditioner and next
+    // direction -- runs only when another iteration follows.  setup, head and
+    // tail launch onto the context's stream, which is being captured.  The
+    // kernels each part launches are returned (k_setup, k_head, k_tail).
+    // false if the runtime refused (nothing has run).
+    template <typename FS, typename FH, typename FT>
+    bool build_loop_graph(cudaGraphExec_t *exec, FS &&setup, bool has_setup, FH &&head, FT &&tail, long &k_setup,
+                          long &k_head, long &k_tail) {
+        *exec = nullptr;
+        const long k0 = prof.launches;
+        k_setup = k_head = k_tail = 0;
+        cudaGraph_t G = nullptr;
+        cudaGraphConditionalHandle hw = 0, hif = 0;
+        bool ok = cudaGraphCreate(&G, 0) == cudaSuccess &&
+                  cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+        // captures fn into graph `into` (a fresh graph if null); returns it
+        auto capture = [&](cudaGraph_t into, auto &&fn, cudaGraph_t *fresh) -> bool {
+            const cudaError_t e0 = into ? cudaStreamBeginCaptureToGraph(st, into, nullptr, nullptr, 0,
+                                                                        cudaStreamCaptureModeThreadLocal)
+                                        : cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e0 != cudaSuccess) return false;
+            try {
+                fn();
+            } catch (...) {
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(st, &tmp);
+                if (tmp && !into) cudaGraphDestroy(tmp);
+                if (G) cudaGraphDestroy(G);
+                prof.launches = k0;
+                throw;
+            }
+            cudaGraph_t out = nullptr;
+            if (cudaStreamEndCapture(st, &out) != cudaSuccess || !out) return false;
+            if (fresh) *fresh = out;
+            return true;
+        };
+        cudaGraphNode_t nsetup = nullptr;
+        if (ok && has_setup) {
+            cudaGraph_t gi = nullptr;
+            long ka = prof.launches;
+            ok = capture(nullptr, setup, &gi);
+            k_setup = prof.launches - ka;
+            if (ok) ok = cudaGraphAddChildGraphNode(&nsetup, G, nullptr, 0, gi) == cudaSuccess;
+            if (gi) cudaGraphDestroy(gi);
+        }
+        cudaGraphNodeParams cw = {};
+        cudaGraphNode_t nw = nullptr;
+        if (ok) {
+            cw.type = cudaGraphNodeTypeConditional;
+            cw.conditional.handle = hw;
+            cw.conditional.type = cudaGraphCondTypeWhile;
+            cw.conditional.size = 1;
+            ok = cudaGraphAddNode(&nw, G, nsetup ? &nsetup : nullptr, nullptr, nsetup ? 1 : 0, &cw) == cudaSuccess;
+        }
+        cudaGraph_t body = ok ? cw.conditional.phGraph_out[0] : nullptr;
+        if (ok) ok = cudaGraphConditionalHandleCreate(&hif, body, 0, 0) == cudaSuccess;
+        cudaGraph_t tailg = nullptr;
+        if (ok) {
+            // the head, then the IF node behind its last node (added to the
+            // graph being captured, the capture continuing from it)
+            long ka = prof.launches;
+            ok = capture(body, [&] {
+                head(hw, hif);
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                const cudaGraphNode_t *deps = nullptr;
+                size_t nd = 0;
+                cudaGraph_t cg = nullptr;
+                bool ok2 = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess &&
+                           cs == cudaStreamCaptureStatusActive;
+                cudaGraphNodeParams ci = {};
+                cudaGraphNode_t nif = nullptr;
+                if (ok2) {
+                    ci.type = cudaGraphNodeTypeConditional;
+                    ci.conditional.handle = hif;
+                    ci.conditional.type = cudaGraphCondTypeIf;
+                    ci.conditional.size = 1;
+                    ok2 = cudaGraphAddNode(&nif, cg, deps, nullptr, nd, &ci) == cudaSuccess;
+                }
+                if (ok2)
+                    ok2 = cudaStreamUpdateCaptureDependencies(st, &nif, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                          cudaSuccess;
+                if (ok2) tailg = ci.conditional.phGraph_out[0];
+            }, nullptr);
+            k_head = prof.launches - ka;
+            ok = ok && tailg;
+        }
+        if (ok) {
+            long ka = prof.launches;
+            ok = capture(tailg, tail, nullptr);
+            k_tail = prof.launches - ka;
+        }
+        prof.launches = k0;
+        if (ok) ok = cudaGraphInstantiate(exec, G, 0) == cudaSuccess;
+        if (G) cudaGraphDestroy(G);
+        if (!ok) {
+            cudaGetLastError();
+            *exec = nullptr;
+        }
+        return ok;
+    }
+
     // The inner PCG as one CUDA graph: the setup (s = 0, r, ||r0||, the first
     // preconditioned direction) and a conditional WHILE node whose body is one
     // PCG iteration.  Step length, direction ratio and the stopping test are
@@ -331,7 +435,7 @@ struct claire_ctx {
         int maxit = 0;
         bool fixed = false;
         double beta0 = 0, gamma = 0;  // baked into the captured transforms
-        long k_init = 0, k_body = 0;  // kernels of the setup and of one body
+        long k_init = 0, k_head = 0, k_tail = 0;  // kernels of the setup, loop head and tail
     } igr[2];
     double *ictl = nullptr;  // device scalars of the inner solve (16 doubles)
     bool inner_graphs = true;
@@ -349,7 +453,7 @@ struct claire_ctx {
         int maxit = 0, iorder = 0;
         bool fixed = false;
         double beta = 0, gamma = 0;
-        long k_body = 0;
+        long k_head = 0, k_tail = 0;  // kernels of the loop head and tail
         unsigned long long used = 0;
     } pgr[2];
     unsigned long long pgr_clock = 0;
@@ -386,18 +490,22 @@ struct claire_ctx {
         launch_pcg_dir(ip, iAp, iz, ir, ictl + 7, nullptr, 0.f, N, true, st, &prof);
         launch_dot(ir, iz, n3, partial, ictl + 3, st, &prof);
     }
-    void inner_body(const Grid &g, const float *gm, float *s, float *work, cudaGraphConditionalHandle h, int maxit,
-                    bool fixed) {
+    void inner_head(const Grid &g, const float *gm, float *s, float *work, cudaGraphConditionalHandle h,
+                    cudaGraphConditionalHandle h_tail, int maxit, bool fixed) {
         const long long N = g.d.N, n3 = 3 * N;
         float *ir = work, *iz = ir + n3, *ip = iz + n3, *iq = ip + n3, *iAp = iq + n3;
-        const double b0 = beta_h0();
-        const SpecParams spb{(float)b0, (float)gamma, (float)(1.0 / (double)N)};
         launch_h0_apply(iq, iAp, gm, ip, N, st, &prof);
         launch_dot(ip, iq, n3, partial, ictl + 2, st, &prof);
         launch_pcg_update(s, nullptr, ir, ip, iAp, iq, 0.f, N, partial, ictl + 6, st, &prof, false, ictl + 2,
                           ictl + 3, nullptr);
-        launch_inner_ctl(ictl, h, maxit, fixed, st, &prof);
-        // the next direction (also after the last step, where it is unused)
+        launch_inner_ctl(ictl, h, h_tail, maxit, fixed, st, &prof);
+    }
+    // the next direction, run only when another iteration follows
+    void inner_tail(const Grid &g, float *work) {
+        const long long N = g.d.N, n3 = 3 * N;
+        float *ir = work, *iz = ir + n3, *ip = iz + n3, *iq = ip + n3, *iAp = iq + n3;
+        const double b0 = beta_h0();
+        const SpecParams spb{(float)b0, (float)gamma, (float)(1.0 / (double)N)};
         spectral_apply(g.d, g.ax, OP_AINV, spb, ir, iz, nullptr, g.spec, st, &prof);
         launch_dot(ir, iz, n3, partial, ictl + 4, st, &prof);
         launch_pcg_dir(ip, iAp, iz, ir, ictl + 7, nullptr, 0.f, N, false, st, &prof, ictl + 4, ictl + 3);
@@ -415,61 +523,19 @@ struct claire_ctx {
         if (!same) {
             if (e.exec) cudaGraphExecDestroy(e.exec);
             e.exec = nullptr;
-            cudaGraph_t G = nullptr, gi = nullptr;
-            cudaGraphNode_t ni = nullptr, nc = nullptr;
-            cudaGraphConditionalHandle h = 0;
-            bool ok = cudaGraphCreate(&G, 0) == cudaSuccess &&
-                      cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault) == cudaSuccess;
-            const long k0 = prof.launches;
-            long k1 = k0, k2 = k0;
-            auto capture_into = [&](cudaGraph_t *dst, cudaGraph_t into, auto &&launches) -> bool {
-                cudaError_t st0 = into ? cudaStreamBeginCaptureToGraph(st, into, nullptr, nullptr, 0,
-                                                                       cudaStreamCaptureModeThreadLocal)
-                                       : cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-                if (st0 != cudaSuccess) return false;
-                try {
-                    launches();
-                } catch (...) {
-                    cudaGraph_t tmp = nullptr;
-                    cudaStreamEndCapture(st, &tmp);
-                    if (tmp && !into) cudaGraphDestroy(tmp);
-                    throw;
-                }
-                cudaGraph_t out = nullptr;
-                if (cudaStreamEndCapture(st, &out) != cudaSuccess || !out) return false;
-                if (dst) *dst = out;
-                return true;
-            };
-            if (ok) ok = capture_into(&gi, nullptr, [&] { inner_setup(g, r, s, work); });
-            k1 = prof.launches;
-            if (ok) ok = cudaGraphAddChildGraphNode(&ni, G, nullptr, 0, gi) == cudaSuccess;
-            if (gi) cudaGraphDestroy(gi);
-            cudaGraphNodeParams cp = {};
-            if (ok) {
-                cp.type = cudaGraphNodeTypeConditional;
-                cp.conditional.handle = h;
-                cp.conditional.type = cudaGraphCondTypeWhile;
-                cp.conditional.size = 1;
-                ok = cudaGraphAddNode(&nc, G, &ni, nullptr, 1, &cp) == cudaSuccess;
-            }
-            if (ok)
-                ok = capture_into(nullptr, cp.conditional.phGraph_out[0],
-                                  [&] { inner_body(g, gm, s, work, h, maxit, fixed); });
-            k2 = prof.launches;
-            if (ok) ok = cudaGraphInstantiate(&e.exec, G, 0) == cudaSuccess;
-            if (G) cudaGraphDestroy(G);
-            prof.launches = k0;
+            const bool ok = build_loop_graph(
+                &e.exec, [&] { inner_setup(g, r, s, work); }, true,
+                [&](cudaGraphConditionalHandle h, cudaGraphConditionalHandle ht) {
+                    inner_head(g, gm, s, work, h, ht, maxit, fixed);
+                },
+                [&] { inner_tail(g, work); }, e.k_init, e.k_head, e.k_tail);
             if (!ok) {
-                cudaGetLastError();
-                e.exec = nullptr;
                 inner_graphs = false;
                 return false;
             }
             e.gm = gm; e.r = r; e.s = s; e.work = work; e.N = g.d.N; e.maxit = maxit; e.fixed = fixed;
             e.beta0 = beta_h0();
             e.gamma = gamma;
-            e.k_init = k1 - k0;
-            e.k_body = k2 - k1;
         }
         launch_scalar_set(ictl, tol, st, &prof);
         CK(cudaGraphLaunch(e.exec, st));
@@ -478,7 +544,8 @@ struct claire_ctx {
         CK(cudaMemcpyAsync(h, ictl, 11 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         iters = (int)h[5];
-        prof.launches += e.k_init + (long)h[10] * e.k_body;
+        // every loop body runs the head, all but the last one the tail
+        prof.launches += e.k_init + (long)h[10] * e.k_head + std::max(0L, (long)h[10] - 1) * e.k_tail;
         return true;
     }
 
@@ -1505,56 +1572,29 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                     auto &e = c.pgr[slot];
                     if (e.exec) cudaGraphExecDestroy(e.exec);
                     e.exec = nullptr;
-                    cudaGraph_t G = nullptr;
-                    cudaGraphNode_t nc = nullptr;
-                    cudaGraphConditionalHandle h = 0;
-                    bool ok = cudaGraphCreate(&G, 0) == cudaSuccess &&
-                              cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault) == cudaSuccess;
-                    cudaGraphNodeParams cp = {};
-                    if (ok) {
-                        cp.type = cudaGraphNodeTypeConditional;
-                        cp.conditional.handle = h;
-                        cp.conditional.type = cudaGraphCondTypeWhile;
-                        cp.conditional.size = 1;
-                        ok = cudaGraphAddNode(&nc, G, nullptr, nullptr, 0, &cp) == cudaSuccess;
-                    }
-                    const long k0 = c.prof.launches;
-                    if (ok)
-                        ok = cudaStreamBeginCaptureToGraph(st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-                    if (ok) {
-                        try {
+                    long ks = 0;
+                    const bool ok = c.build_loop_graph(
+                        &e.exec, [] {}, false,
+                        [&](cudaGraphConditionalHandle h, cudaGraphConditionalHandle ht) {
                             c.matvec_launches(p, q, true);
                             launch_pcg_update(x, Ax, r, p, Ap, q, 0.f, N, c.partial, c.dres, st, &c.prof, true,
                                               c.dres, c.dres + 10, c.dres + 12);
-                            launch_pcg_ctl(c.dres, c.octl, h, maxit, fixed, st, &c.prof);
+                            launch_pcg_ctl(c.dres, c.octl, h, ht, maxit, fixed, st, &c.prof);
                             launch_pcg_negcopy(c.octl, x, Ax, z, Ap, n3, st, &c.prof);
+                        },
+                        [&] {
                             c.spectral(OP_AINV, r, z, nullptr);
                             launch_dot(r, z, n3, c.partial, c.dres + 11, st, &c.prof);
                             pcg_dir(nullptr, false, 11, 10);
                             launch_scalar_copy(c.dres + 10, c.dres + 11, st, &c.prof);
-                        } catch (...) {
-                            cudaGraph_t tmp = nullptr;
-                            cudaStreamEndCapture(st, &tmp);
-                            cudaGraphDestroy(G);
-                            c.prof.launches = k0;
-                            throw;
-                        }
-                        cudaGraph_t out = nullptr;
-                        ok = cudaStreamEndCapture(st, &out) == cudaSuccess && out;
-                    }
-                    const long kb = c.prof.launches - k0;
-                    c.prof.launches = k0;
-                    if (ok) ok = cudaGraphInstantiate(&e.exec, G, 0) == cudaSuccess;
-                    if (G) cudaGraphDestroy(G);
+                        },
+                        ks, e.k_head, e.k_tail);
                     if (!ok) {
-                        cudaGetLastError();
-                        e.exec = nullptr;
                         c.pcg_graphs = false;
                         return false;
                     }
                     e.dispm = c.dispm; e.rng = c.rng_m(); e.sv = c.sv; e.maxit = maxit; e.fixed = fixed;
-                    e.beta = c.beta; e.gamma = c.gamma; e.iorder = c.d.iorder; e.k_body = kb;
+                    e.beta = c.beta; e.gamma = c.gamma; e.iorder = c.d.iorder;
                 }
                 auto &e = c.pgr[slot];
                 e.used = ++c.pgr_clock;
@@ -1564,7 +1604,8 @@ static int do_solve(claire_ctx *ctx, float *v, const claire_solve_opts &o, clair
                 double hc[4];
                 CK(cudaMemcpyAsync(hc, c.octl, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
-                c.prof.launches += (long)hc[3] * e.k_body;
+                // every loop body runs the head, all but the last one the tail
+                c.prof.launches += (long)hc[3] * e.k_head + std::max(0L, (long)hc[3] - 1) * e.k_tail;
                 if (hc[2] == 1.0) throw Error(CLAIRE_ERR_NONFINITE, "non-finite p.Hp in PCG");
                 iters = (int)hc[1];
                 return true;

@@ -199,18 +199,20 @@ void launch_pcg_dir(float *p, float *Ap, const float *z, const float *r, const d
                     const float *Az, float b, long long N, bool init, cudaStream_t st,
                     Profiler *prof, const double *dbn = nullptr, const double *dbd = nullptr);
 // device-side control of the inner PCG of the H0 preconditioners (a CUDA
-// graph with a conditional while node); c: the loop's device scalars,
+// graph with a conditional while node; the control kernel sets the loop's
+// condition and that of the IF node around the rest of the body, h_tail);
+// c: the loop's device scalars,
 // c[0] tolerance, c[1] ||r0||, c[2] p.q, c[3] r.z (current direction),
 // c[4] r.z (new residual), c[5] iterations, c[6..9] stats of r, c[10] bodies
 void launch_inner_init(double *c, cudaStream_t st, Profiler *prof);
-void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
-                      Profiler *prof);
+void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_tail, int maxit,
+                      bool fixed, cudaStream_t st, Profiler *prof);
 void launch_scalar_copy(double *dst, const double *src, cudaStream_t st, Profiler *prof);
 // device-side control of the outer PCG loop (InvA) as a graph: k_pcg_ctl
 // reads d[0] (||r||^2) and d[12] (p.Hp) of the solver's result slots and
 // keeps c[0] threshold, c[1] iterations, c[2] flags, c[3] bodies
-void launch_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
-                    Profiler *prof);
+void launch_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_tail,
+                    int maxit, bool fixed, cudaStream_t st, Profiler *prof);
 void launch_pcg_negcopy(const double *c, float *x, float *Ax, const float *z, const float *Ap, long long n,
                         cudaStream_t st, Profiler *prof);
 void launch_pcg_ctl_init(double *c, double thr, cudaStream_t st, Profiler *prof);
@@ -230,6 +232,11 @@ void launch_pcg_dir_u0(float *p, float *Ap, const float *z, const float *r, cons
 void launch_h0_apply(float *q, const float *Ap, const float *gm, const float *p, long long N,
                      cudaStream_t st, Profiler *prof);
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8
+
+// grid of a persistent transform pass: as many blocks as fit the SMs at this
+// shared memory per block (227 KB per SM, 1 KB reserved per block, at most 8
+// per SM), at most nitems
+int persistent_grid(long long nitems, size_t smem);
 
 // ------------------------------------------------- kernel attributes ----
 // Reports a failed cudaFuncSetAttribute as a library error with the kernel's

@@ -21,6 +21,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 
 #include "claire_internal.cuh"
@@ -63,136 +64,223 @@ k_r2c_x3(const TI *__restrict__ in, float2 *__restrict__ out, long long nlines, 
     }
 }
 
+// Pass 1 with persistent blocks: the 2L real lines of the next tile (one
+// contiguous chunk) are fetched by 16-byte cp.async into a staging buffer
+// while the current tile is transformed, then transposed into the transform
+// layout.  FP32 input, n a multiple of 4, 16-byte aligned (the launcher
+// checks; otherwise the one-tile-per-block form above runs).
+template <int N, int L>
+__global__ void __launch_bounds__(kThreads)
+k_r2c_x3_p(const float *__restrict__ in, float2 *__restrict__ out, long long nlines, FftPlan p, int h3, int p3,
+           int nitems) {
+    extern __shared__ float2 sm[];
+    const int n = Fft<N>::size(p), ls = L + 1;
+    float2 *A = sm, *B = sm + n * ls;
+    float *S = reinterpret_cast<float *>(sm + 2 * n * ls);
+    auto load = [&](int item) {
+        const long long line0 = (long long)item * 2 * L;
+        const float *base = in + line0 * n;
+        const int nch = (2 * L * n) / 4;
+        for (int t = threadIdx.x; t < nch; t += blockDim.x) {
+            const long long line = line0 + (4 * t) / n;
+            const int bytes = line < nlines ? 16 : 0;
+            cp_async16z(S + 4 * t, base + (bytes ? 4 * t : 0), bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0);
+    if (N > 0) h3 = N / 2 + 1;
+    for (int item = i0; item < nitems; item += stride) {
+        cp_async_wait_n<0>();
+        __syncthreads();
+        // real lines 2l and 2l+1 become the real and imaginary part of line l
+        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+            const int l = t / n, e = t - l * n;
+            A[e * ls + l] = make_float2(S[(2 * l) * n + e], S[(2 * l + 1) * n + e]);
+        }
+        __syncthreads();
+        if (item + stride < nitems) load(item + stride);
+        float2 *Rz = Fft<N>::template run<L>(A, B, p, ls, -1.f);
+        const long long line0 = (long long)item * 2 * L;
+        for (int t = threadIdx.x; t < L * h3; t += blockDim.x) {
+            const int l = t / h3, k = t - l * h3;
+            const float2 z = Rz[k * ls + l];
+            const float2 zn = Rz[((k == 0) ? 0 : (n - k)) * ls + l];
+            const float2 a = make_float2(0.5f * (z.x + zn.x), 0.5f * (z.y - zn.y));
+            const float2 b = make_float2(0.5f * (z.y + zn.y), -0.5f * (z.x - zn.x));
+            const long long la = line0 + 2 * l;
+            if (la < nlines) out[la * p3 + k] = a;
+            if (la + 1 < nlines) out[(la + 1) * p3 + k] = b;
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- pass 2 ---
-// x2 complex transform in place.  Block: (k3 tile of TK, one (c, i1) plane).
+// x2 complex transform in place.  Persistent blocks walk the tiles (TK k3
+// columns of one (c, i1) plane) and double-buffer them: cp.async fetches the
+// next tile while the current one is transformed (measured at 256^3: the x2
+// passes of a solve 3.09 -> 2.44 ms against one tile per block).
 template <int N, int TK>
 __global__ void __launch_bounds__(kThreads)
-k_c2c_x2(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s) {
+k_c2c_x2(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s, int ntk, int nitems) {
     extern __shared__ float2 sm[];
     const int n = Fft<N>::size(p);
-    float2 *A = sm, *B = sm + n * TK;
-    float2 *base = data + (long long)blockIdx.y * n * p3;
-    const int k0 = blockIdx.x * TK;
+    float2 *A0 = sm, *A1 = sm + n * TK, *B = sm + 2 * n * TK;
+    auto load = [&](int item, float2 *dst) {
+        const int plane = item / ntk, k0 = (item - plane * ntk) * TK;
+        const float2 *base = data + (long long)plane * n * p3 + k0;
+        for (int t = threadIdx.x; t < n * (TK / 2); t += blockDim.x) {
+            const int e = t / (TK / 2), ch = t - e * (TK / 2);
+            const int col = k0 + 2 * ch;
+            const int bytes = col + 2 <= h3 ? 16 : (col < h3 ? 8 : 0);
+            const float2 *src = base + (long long)e * p3 + (bytes ? 2 * ch : 0);
+            cp_async16z(dst + e * TK + 2 * ch, src, bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0, A0);
+    bool cur0 = true;
+    for (int item = i0; item < nitems; item += stride) {
+        float2 *Acur = cur0 ? A0 : A1, *Anext = cur0 ? A1 : A0;
+        if (item + stride < nitems) {
+            load(item + stride, Anext);
+            cp_async_wait_n<1>();
+        } else {
+            cp_async_wait_n<0>();
+        }
+        __syncthreads();
+        float2 *R = Fft<N>::template run<TK>(Acur, B, p, TK, s);
+        const int plane = item / ntk, k0 = (item - plane * ntk) * TK;
+        float2 *base = data + (long long)plane * n * p3 + k0;
         for (int t = threadIdx.x; t < n * TK; t += blockDim.x) {
-        const int e = t / TK, l = t - e * TK;
-        A[e * TK + l] = (k0 + l < h3) ? base[(long long)e * p3 + k0 + l] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2 *R = Fft<N>::template run<TK>(A, B, p, TK, s);
-    for (int t = threadIdx.x; t < n * TK; t += blockDim.x) {
-        const int e = t / TK, l = t - e * TK;
-        if (k0 + l < h3) base[(long long)e * p3 + k0 + l] = R[e * TK + l];
+            const int e = t / TK, l = t - e * TK;
+            if (k0 + l < h3) base[(long long)e * p3 + l] = R[e * TK + l];
+        }
+        __syncthreads();
+        cur0 = !cur0;
     }
 }
 
 // ---------------------------------------------------------------- pass 3 ---
-// x1 forward, multiplier, x1 inverse, in place.  Block: (k3 tile, k2 index).
-// Buffers: three component tiles of n1*TK plus one scratch.
+// x1 forward, multiplier, x1 inverse, in place; all three components at once
+// (the divergence penalty couples them).  Persistent blocks walk the items
+// (TK k3 columns at one k2 index); the three component tiles of the next item
+// are fetched by 16-byte cp.async (zero-filled past h3) while the current
+// item is transformed, multiplied and transformed back.  Seven tiles of n1*TK:
+// three current, three next, one scratch.
 template <int N, int TK, int OP>
 __global__ void __launch_bounds__(kThreads)
-k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3,
-         long long cstride, SpecParams sp) {
-    constexpr int NIN = 3, NOUT = 3, NB = 3;  // A, A^-1 and the x1-only passes couple all components
+k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3, long long cstride, SpecParams sp,
+           int ntk, int nitems) {
     constexpr bool FWD = OP != OP_X1INV, INV = OP != OP_X1FWD;
     extern __shared__ float2 sm[];
     const int n1 = Fft<N>::size(p1);
     const int tile = n1 * TK;
-    float2 *buf[NB];
-    float2 *scratch = sm + NB * tile;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) buf[c] = sm + c * tile;
-    const int i2 = blockIdx.y;
-    const int k0 = blockIdx.x * TK;
+    float2 *cur[3] = {sm, sm + tile, sm + 2 * tile};
+    float2 *scratch = sm + 3 * tile;
+    float2 *nxt[3] = {sm + 4 * tile, sm + 5 * tile, sm + 6 * tile};
     const long long rowstride = (long long)n2 * p3;  // between consecutive i1
-    float2 *base = data + (long long)i2 * p3 + k0;
-    if constexpr (N >= 256) {
-        // long lines: fully unrolled (the stride known at compile time), all
-        // loads of the three tiles in flight at once; measured 11% faster at
-        // 256^3 than the loop below
-#pragma unroll
-        for (int c = 0; c < NIN; ++c) {
-#pragma unroll
-            for (int t = threadIdx.x; t < tile; t += kThreads) {
-                const int e = t / TK, l = t - e * TK;
-                buf[c][e * TK + l] = (k0 + l < h3) ? base[c * cstride + e * rowstride + l]
-                                                   : make_float2(0.f, 0.f);
-            }
+    constexpr int CH = TK / 2;                        // 16-byte chunks per row
+    auto load = [&](int item, float2 *const *dst) {
+        const int i2 = item / ntk, k0 = (item - i2 * ntk) * TK;
+        const float2 *base = data + (long long)i2 * p3 + k0;
+        for (int t = threadIdx.x; t < 3 * n1 * CH; t += blockDim.x) {
+            const int c = t / (n1 * CH), r = t - c * n1 * CH;
+            const int e = r / CH, ch = r - e * CH;
+            const int col = k0 + 2 * ch;
+            const int bytes = col + 2 <= h3 ? 16 : (col < h3 ? 8 : 0);
+            cp_async16z(dst[c] + e * TK + 2 * ch, base + c * cstride + e * rowstride + (bytes ? 2 * ch : 0), bytes);
         }
-    } else {
-        for (int c = 0; c < NIN; ++c) {
-            for (int t = threadIdx.x; t < tile; t += blockDim.x) {
-                const int e = t / TK, l = t - e * TK;
-                buf[c][e * TK + l] = (k0 + l < h3) ? base[c * cstride + e * rowstride + l]
-                                                   : make_float2(0.f, 0.f);
-            }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0, cur);
+    for (int item = i0; item < nitems; item += stride) {
+        if (item + stride < nitems) {
+            load(item + stride, nxt);
+            cp_async_wait_n<1>();
+        } else {
+            cp_async_wait_n<0>();
         }
-    }
-    __syncthreads();
-    if (FWD) {
-#pragma unroll
-        for (int c = 0; c < NIN; ++c) {
-            float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, -1.f);
-            if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
-        }
-    }
-    // multiplier at (k1, k2, k3)
-    const float k2 = wavenumber(i2, n2), k2d = wavenumber_d1(i2, n2);
-    for (int t = threadIdx.x; t < tile; t += blockDim.x) {
-        const int e = t / TK, l = t - e * TK;
-        const int i3 = k0 + l;
-        const float k1 = wavenumber(e, n1), k1d = wavenumber_d1(e, n1);
-        const float k3 = (float)i3, k3d = ((n3 & 1) == 0 && 2 * i3 == n3) ? 0.f : k3;
-        const int id = e * TK + l;
-        if (OP == OP_X1FWD) {
-            // forward only: no multiplier
-        } else if (OP == OP_X1INV) {
+        __syncthreads();
+        if (FWD) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float2 f = buf[c][id];
-                buf[c][id] = make_float2(f.x * sp.scale, f.y * sp.scale);
+                float2 *r = Fft<N>::template run<TK>(cur[c], scratch, p1, TK, -1.f);
+                if (r != cur[c]) { scratch = cur[c]; cur[c] = r; }
             }
-        } else {
-            const float2 a = buf[0][id], b = buf[1][id], c = buf[2][id];
-            const float kk = k1 * k1 + k2 * k2 + k3 * k3;
-            const float kd2 = k1d * k1d + k2d * k2d + k3d * k3d;
-            // khat . v
-            const float2 kv = make_float2(k1d * a.x + k2d * b.x + k3d * c.x,
-                                          k1d * a.y + k2d * b.y + k3d * c.y);
-            float diag, coup;
-            if (OP == OP_A) {
-                // (beta |k|^2 I + gamma khat khat^T) v
-                diag = sp.beta * kk;
-                coup = sp.gamma;
-            } else {
-                // (beta |k|^2)^-1 (I - gamma khat khat^T / (beta |k|^2 + gamma |khat|^2)) v,
-                // identity at k = 0 (Sherman-Morrison)
-                if (kk == 0.f) {
-                    diag = 1.f;
-                    coup = 0.f;
-                } else {
-                    const float bk = sp.beta * kk;
-                    diag = 1.f / bk;
-                    coup = -sp.gamma * diag / (bk + sp.gamma * kd2);
-                }
-            }
-            const float s = sp.scale;
-            buf[0][id] = make_float2((diag * a.x + coup * k1d * kv.x) * s, (diag * a.y + coup * k1d * kv.y) * s);
-            buf[1][id] = make_float2((diag * b.x + coup * k2d * kv.x) * s, (diag * b.y + coup * k2d * kv.y) * s);
-            buf[2][id] = make_float2((diag * c.x + coup * k3d * kv.x) * s, (diag * c.y + coup * k3d * kv.y) * s);
         }
-    }
-    __syncthreads();
-    if (INV) {
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c) {
-            float2 *r = Fft<N>::template run<TK>(buf[c], scratch, p1, TK, +1.f);
-            if (r != buf[c]) { scratch = buf[c]; buf[c] = r; }
-        }
-    }
-    for (int c = 0; c < NOUT; ++c) {
+        const int i2 = item / ntk, k0 = (item - i2 * ntk) * TK;
+        // multiplier at (k1, k2, k3)
+        const float k2 = wavenumber(i2, n2), k2d = wavenumber_d1(i2, n2);
         for (int t = threadIdx.x; t < tile; t += blockDim.x) {
             const int e = t / TK, l = t - e * TK;
-            if (k0 + l < h3) base[c * cstride + e * rowstride + l] = buf[c][e * TK + l];
+            const int i3 = k0 + l;
+            const float k1 = wavenumber(e, n1), k1d = wavenumber_d1(e, n1);
+            const float k3 = (float)i3, k3d = ((n3 & 1) == 0 && 2 * i3 == n3) ? 0.f : k3;
+            const int id = e * TK + l;
+            if (OP == OP_X1FWD) {
+            } else if (OP == OP_X1INV) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float2 f = cur[c][id];
+                    cur[c][id] = make_float2(f.x * sp.scale, f.y * sp.scale);
+                }
+            } else {
+                const float2 a = cur[0][id], b = cur[1][id], c = cur[2][id];
+                const float kk = k1 * k1 + k2 * k2 + k3 * k3;
+                const float kd2 = k1d * k1d + k2d * k2d + k3d * k3d;
+                const float2 kv = make_float2(k1d * a.x + k2d * b.x + k3d * c.x,
+                                              k1d * a.y + k2d * b.y + k3d * c.y);
+                float diag, coup;
+                if (OP == OP_A) {
+                    diag = sp.beta * kk;
+                    coup = sp.gamma;
+                } else {
+                    if (kk == 0.f) {
+                        diag = 1.f;
+                        coup = 0.f;
+                    } else {
+                        const float bk = sp.beta * kk;
+                        diag = 1.f / bk;
+                        coup = -sp.gamma * diag / (bk + sp.gamma * kd2);
+                    }
+                }
+                const float s = sp.scale;
+                cur[0][id] = make_float2((diag * a.x + coup * k1d * kv.x) * s, (diag * a.y + coup * k1d * kv.y) * s);
+                cur[1][id] = make_float2((diag * b.x + coup * k2d * kv.x) * s, (diag * b.y + coup * k2d * kv.y) * s);
+                cur[2][id] = make_float2((diag * c.x + coup * k3d * kv.x) * s, (diag * c.y + coup * k3d * kv.y) * s);
+            }
+        }
+        __syncthreads();
+        if (INV) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float2 *r = Fft<N>::template run<TK>(cur[c], scratch, p1, TK, +1.f);
+                if (r != cur[c]) { scratch = cur[c]; cur[c] = r; }
+            }
+        }
+        float2 *base = data + (long long)i2 * p3 + k0;
+        for (int c = 0; c < 3; ++c) {
+            for (int t = threadIdx.x; t < tile; t += blockDim.x) {
+                const int e = t / TK, l = t - e * TK;
+                if (k0 + l < h3) base[c * cstride + e * rowstride + l] = cur[c][e * TK + l];
+            }
+        }
+        __syncthreads();
+        // the next item's tiles become the current ones; the current tiles
+        // (and the scratch the transforms left) are free again
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float2 *t = cur[c];
+            cur[c] = nxt[c];
+            nxt[c] = t;
         }
     }
 }
@@ -246,11 +334,109 @@ k_c2r_x3(const float2 *__restrict__ in, TO *__restrict__ out, const float *__res
     }
 }
 
+// Pass 5 with persistent blocks: the 2L half-spectrum lines of the next tile
+// (one contiguous chunk of 2L*p3 complex values) are fetched by 16-byte
+// cp.async into a staging buffer while the current tile is transformed.
+template <int N, int L, int EPI, typename TO = float>
+__global__ void __launch_bounds__(kThreads)
+k_c2r_x3_p(const float2 *__restrict__ in, TO *__restrict__ out, const float *__restrict__ add, long long nlines,
+           FftPlan p, int h3, int p3, int nitems) {
+    extern __shared__ float2 sm[];
+    const int n = Fft<N>::size(p), ls = L + 1;
+    float2 *A = sm, *B = sm + n * ls;
+    float2 *S = sm + 2 * n * ls;  // staging: 2L lines of p3 complex values
+    const bool even = (n & 1) == 0;
+    auto load = [&](int item) {
+        const long long line0 = (long long)item * 2 * L;
+        const float2 *base = in + line0 * p3;
+        const int nch = L * p3;  // 2L * p3 complex values, two per chunk
+        for (int t = threadIdx.x; t < nch; t += blockDim.x) {
+            const long long line = line0 + (2 * t) / p3;
+            const int bytes = line < nlines ? 16 : 0;
+            cp_async16z(S + 2 * t, base + (bytes ? 2 * t : 0), bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0);
+    for (int item = i0; item < nitems; item += stride) {
+        cp_async_wait_n<0>();
+        __syncthreads();
+        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+            const int l = t / n, k = t - l * n;
+            const bool lo = k < h3;
+            const int kk = lo ? k : n - k;
+            float2 a = S[(2 * l) * p3 + kk];
+            float2 b = S[(2 * l + 1) * p3 + kk];
+            if (k == 0 || (even && 2 * k == n)) {
+                a.y = 0.f;
+                b.y = 0.f;
+            }
+            if (!lo) {
+                a.y = -a.y;
+                b.y = -b.y;
+            }
+            // Z = A + i B
+            A[k * ls + l] = make_float2(a.x - b.y, a.y + b.x);
+        }
+        __syncthreads();
+        if (item + stride < nitems) load(item + stride);
+        float2 *R = Fft<N>::template run<L>(A, B, p, ls, +1.f);
+        const long long line0 = (long long)item * 2 * L;
+        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+            const int l = t / n, e = t - l * n;
+            const long long la = line0 + 2 * l;
+            const float2 z = R[e * ls + l];
+            if (la < nlines) {
+                float val = z.x;
+                if (EPI == EPI_ADD) val += add[la * n + e];
+                str(out + la * n + e, val);
+            }
+            if (la + 1 < nlines) {
+                float val = z.y;
+                if (EPI == EPI_ADD) val += add[(la + 1) * n + e];
+                str(out + (la + 1) * n + e, val);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // -------------------------------------------------------------- launchers --
+}  // namespace
+
+int persistent_grid(long long nitems, size_t smem) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!sms[dev]) {
+        int c = 0;
+        if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) c = 152;
+        sms[dev] = c;
+    }
+    long long per_sm = (long long)(227 * 1024) / (long long)(smem + 1024);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    const long long g = per_sm * sms[dev];
+    return (int)(nitems < g ? nitems : g);
+}
+
+namespace {
 
 template <int N, int L, typename TI>
 void r2c_l(const Dims &d, const FftPlan &p, const TI *in, float2 *out, long long nlines,
            cudaStream_t st) {
+    if constexpr (std::is_same<TI, float>::value) {
+        if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
+            const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2) + (size_t)2 * L * d.n3 * sizeof(float);
+            const int nitems = (int)((nlines + 2 * L - 1) / (2 * L));
+            set_smem<k_r2c_x3_p<N, L>>(smem);
+            k_r2c_x3_p<N, L><<<persistent_grid(nitems, smem), kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3,
+                                                                                    nitems);
+            return;
+        }
+    }
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const long long blocks = (nlines + 2 * L - 1) / (2 * L);
     set_smem<k_r2c_x3<N, L, TI>>(smem);
@@ -285,18 +471,19 @@ void r2c_x3(const Dims &d, const FftPlan &p, const TI *in, float2 *out, int ncom
 
 template <int N, int TK>
 void c2c_t(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
-    const size_t smem = 2 * (size_t)d.n2 * TK * sizeof(float2);
-    dim3 grid((d.h3 + TK - 1) / TK, ncomp * d.n1);
+    const size_t smem = 3 * (size_t)d.n2 * TK * sizeof(float2);
+    const int ntk = (d.h3 + TK - 1) / TK, nitems = ntk * ncomp * d.n1;
+    const int grid = persistent_grid(nitems, smem);
     set_smem<k_c2c_x2<N, TK>>(smem);
-    k_c2c_x2<N, TK><<<grid, kThreads, smem, st>>>(data, p, d.h3, d.p3, s);
+    k_c2c_x2<N, TK><<<grid, kThreads, smem, st>>>(data, p, d.h3, d.p3, s, ntk, nitems);
 }
 
 template <int N>
 void c2c_n(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
     if constexpr (N > 0) {
-        c2c_t<N, tile_cols(N, 1)>(d, p, data, ncomp, s, st);
+        c2c_t<N, tile_cols(N, 2)>(d, p, data, ncomp, s, st);
     } else {
-        switch (tile_cols(d.n2, 1)) {
+        switch (tile_cols(d.n2, 2)) {
             case 16: c2c_t<N, 16>(d, p, data, ncomp, s, st); break;
             case 8: c2c_t<N, 8>(d, p, data, ncomp, s, st); break;
             default: c2c_t<N, 4>(d, p, data, ncomp, s, st); break;
@@ -315,17 +502,17 @@ void c2c_x2(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, c
 
 template <int N, int TK, int OP>
 void mul_t(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
-    constexpr int NB = 3;
-    const size_t smem = (size_t)(NB + 1) * d.n1 * TK * sizeof(float2);
+    const size_t smem = (size_t)7 * d.n1 * TK * sizeof(float2);
     const long long cstride = (long long)d.n1 * d.n2 * d.p3;
-    dim3 grid((d.h3 + TK - 1) / TK, d.n2);
+    const int ntk = (d.h3 + TK - 1) / TK, nitems = ntk * d.n2;
     set_smem<k_mul_x1<N, TK, OP>>(smem);
-    k_mul_x1<N, TK, OP><<<grid, kThreads, smem, st>>>(data, p, d.n2, d.n3, d.h3, d.p3, cstride, sp);
+    k_mul_x1<N, TK, OP><<<persistent_grid(nitems, smem), kThreads, smem, st>>>(data, p, d.n2, d.n3, d.h3, d.p3,
+                                                                                cstride, sp, ntk, nitems);
 }
 
 template <int N, int OP>
 void mul_n(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
-    constexpr int NB = 3;  // every operator keeps three component tiles
+    constexpr int NB = 6;  // three component tiles for the current item, three for the next
     if constexpr (N > 0) {
         mul_t<N, tile_cols(N, NB), OP>(d, p, data, sp, st);
     } else {
@@ -351,6 +538,21 @@ void mul_x1_op(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &
 template <int N, int L, typename TO>
 void c2r_l(const Dims &d, const FftPlan &p, const float2 *in, TO *out, const float *add,
            long long nlines, cudaStream_t st) {
+    if (((uintptr_t)in & 15) == 0) {
+        // the persistent form with the next tile staged by cp.async
+        const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2) + (size_t)2 * L * d.p3 * sizeof(float2);
+        const int nitems = (int)((nlines + 2 * L - 1) / (2 * L));
+        const int grid = persistent_grid(nitems, smem);
+        if (add) {
+            set_smem<k_c2r_x3_p<N, L, EPI_ADD, TO>>(smem);
+            k_c2r_x3_p<N, L, EPI_ADD, TO><<<grid, kThreads, smem, st>>>(in, out, add, nlines, p, d.h3, d.p3, nitems);
+        } else {
+            set_smem<k_c2r_x3_p<N, L, EPI_STORE, TO>>(smem);
+            k_c2r_x3_p<N, L, EPI_STORE, TO><<<grid, kThreads, smem, st>>>(in, out, add, nlines, p, d.h3, d.p3,
+                                                                          nitems);
+        }
+        return;
+    }
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const long long blocks = (nlines + 2 * L - 1) / (2 * L);
     if (add) {

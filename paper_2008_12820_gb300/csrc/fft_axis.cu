@@ -3,6 +3,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 
 #include "claire_internal.cuh"
@@ -66,6 +67,71 @@ k_deriv_x3(const float *__restrict__ in, TO *out, const float *add, long long nl
     }
 }
 
+// The same pass with persistent blocks: the 2L real lines of the next tile
+// (one contiguous chunk of 2L*n floats) are fetched by 16-byte cp.async into a
+// staging buffer while the current tile is transformed; the tile is then
+// transposed from the staging buffer into the transform layout.  Needs n a
+// multiple of 4 and 16-byte aligned fields (the launcher checks).
+template <int N, int L, int EPI, typename TO>
+__global__ void __launch_bounds__(kThreads)
+k_deriv_x3_p(const float *__restrict__ in, TO *out, const float *add, long long nlines, FftPlan p, int nitems) {
+    extern __shared__ float2 sm[];
+    const int n = Fft<N>::size(p), ls = L + 1;
+    float2 *A = sm, *B = sm + n * ls;
+    float *S = reinterpret_cast<float *>(sm + 2 * n * ls);  // staging: 2L lines of n floats
+    auto load = [&](int item) {
+        const long long line0 = (long long)item * 2 * L;
+        const float *base = in + line0 * n;
+        const int nch = (2 * L * n) / 4;
+        for (int t = threadIdx.x; t < nch; t += blockDim.x) {
+            const long long line = line0 + (4 * t) / n;
+            const int bytes = line < nlines ? 16 : 0;
+            cp_async16z(S + 4 * t, base + (bytes ? 4 * t : 0), bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0);
+    const float sc = 1.f / (float)n;
+    for (int item = i0; item < nitems; item += stride) {
+        cp_async_wait_n<0>();
+        __syncthreads();
+        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+            const int l = t / n, e = t - l * n;
+            A[e * ls + l] = make_float2(S[(2 * l) * n + e], S[(2 * l + 1) * n + e]);
+        }
+        __syncthreads();
+        if (item + stride < nitems) load(item + stride);
+        float2 *R = Fft<N>::template run<L>(A, B, p, ls, -1.f);
+        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+            const int e = t / L, l = t - e * L;
+            const float k = wavenumber_d1(e, n) * sc;
+            const float2 z = R[e * ls + l];
+            R[e * ls + l] = make_float2(-k * z.y, k * z.x);
+        }
+        __syncthreads();
+        float2 *Q = Fft<N>::template run<L>(R, R == A ? B : A, p, ls, +1.f);
+        const long long line0 = (long long)item * 2 * L;
+        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+            const int l = t / n, e = t - l * n;
+            const long long la = line0 + 2 * l;
+            const float2 z = Q[e * ls + l];
+            if (la < nlines) {
+                float val = z.x;
+                if (EPI == EPI_ADD) val += add[la * n + e];
+                str(out + la * n + e, val);
+            }
+            if (la + 1 < nlines) {
+                float val = z.y;
+                if (EPI == EPI_ADD) val += add[(la + 1) * n + e];
+                str(out + (la + 1) * n + e, val);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // lines along a strided axis (x2: element stride n3, planes i1; x1: element
 // stride n2*n3, planes i2); a tile is 2*TKC consecutive x3 columns of one
 // plane, adjacent columns paired into one complex column
@@ -115,6 +181,74 @@ k_deriv_strided(const float *__restrict__ in, TO *out, const float *add, int n3,
     }
 }
 
+// The same pass with persistent blocks that double-buffer their tiles: cp.async
+// fetches the next tile (2*TKC x3 columns of one plane, 16-byte chunks,
+// zero-filled past n3) while the current one is transformed.  Needs n3 a
+// multiple of 4 and 16-byte aligned fields (the launcher checks).
+template <int N, int TKC, int EPI, typename TO>
+__global__ void __launch_bounds__(kThreads)
+k_deriv_strided_p(const float *__restrict__ in, TO *out, const float *add, int n3, long long estride,
+                  long long pstride, FftPlan p, int ntk, int nitems) {
+    extern __shared__ float2 sm[];
+    const int n = Fft<N>::size(p);
+    float2 *A0 = sm, *A1 = sm + n * TKC, *B = sm + 2 * n * TKC;
+    constexpr int CH = TKC / 2;  // 16-byte chunks per row
+    auto load = [&](int item, float2 *dst) {
+        const int plane = item / ntk, k0 = (item - plane * ntk) * 2 * TKC;
+        const float *base = in + (long long)plane * pstride + k0;
+        for (int t = threadIdx.x; t < n * CH; t += blockDim.x) {
+            const int e = t / CH, ch = t - e * CH;
+            const int i3 = k0 + 4 * ch;
+            const int bytes = i3 + 4 <= n3 ? 16 : 0;
+            cp_async16z(dst + e * TKC + 2 * ch, base + e * estride + (bytes ? 4 * ch : 0), bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0, A0);
+    bool cur0 = true;
+    const float sc = 1.f / (float)n;
+    for (int item = i0; item < nitems; item += stride) {
+        float2 *Acur = cur0 ? A0 : A1, *Anext = cur0 ? A1 : A0;
+        if (item + stride < nitems) {
+            load(item + stride, Anext);
+            cp_async_wait_n<1>();
+        } else {
+            cp_async_wait_n<0>();
+        }
+        __syncthreads();
+        float2 *R = Fft<N>::template run<TKC>(Acur, B, p, TKC, -1.f);
+        for (int t = threadIdx.x; t < n * TKC; t += blockDim.x) {
+            const int e = t / TKC;
+            const float k = wavenumber_d1(e, n) * sc;
+            const float2 z = R[t];
+            R[t] = make_float2(-k * z.y, k * z.x);
+        }
+        __syncthreads();
+        float2 *S = Fft<N>::template run<TKC>(R, R == Acur ? B : Acur, p, TKC, +1.f);
+        const int plane = item / ntk, k0 = (item - plane * ntk) * 2 * TKC;
+        const long long base = (long long)plane * pstride;
+        for (int t = threadIdx.x; t < n * TKC; t += blockDim.x) {
+            const int e = t / TKC, c = t - e * TKC;
+            const int i3 = k0 + 2 * c;
+            const long long o = base + e * estride + i3;
+            const float2 z = S[t];
+            if (i3 < n3) {
+                float val = z.x;
+                if (EPI == EPI_ADD) val += add[o];
+                str(out + o, val);
+            }
+            if (i3 + 1 < n3) {
+                float val = z.y;
+                if (EPI == EPI_ADD) val += add[o + 1];
+                str(out + o + 1, val);
+            }
+        }
+        __syncthreads();
+        cur0 = !cur0;
+    }
+}
 
 // ---- axis derivatives: launchers ------------------------------------------
 constexpr int deriv_cols(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
@@ -124,6 +258,22 @@ constexpr int deriv_cols(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
 template <int N, int L, typename TO>
 void deriv_x3_l(const Dims &d, const FftPlan &p, const float *in, TO *out, const float *add, cudaStream_t st) {
     const long long nlines = (long long)d.n1 * d.n2;
+    if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
+        // the persistent form with the next tile staged by cp.async
+        const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2) + (size_t)2 * L * d.n3 * sizeof(float);
+        const int nitems = (int)((nlines + 2 * L - 1) / (2 * L));
+        const int grid = persistent_grid(nitems, smem);
+        if constexpr (std::is_same<TO, float>::value) {
+            if (add) {
+                set_smem<k_deriv_x3_p<N, L, EPI_ADD, TO>>(smem);
+                k_deriv_x3_p<N, L, EPI_ADD, TO><<<grid, kThreads, smem, st>>>(in, out, add, nlines, p, nitems);
+                return;
+            }
+        }
+        set_smem<k_deriv_x3_p<N, L, EPI_STORE, TO>>(smem);
+        k_deriv_x3_p<N, L, EPI_STORE, TO><<<grid, kThreads, smem, st>>>(in, out, add, nlines, p, nitems);
+        return;
+    }
     const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2);
     const unsigned blocks = (unsigned)((nlines + 2 * L - 1) / (2 * L));
     if constexpr (std::is_same<TO, float>::value) {
@@ -153,6 +303,24 @@ void deriv_x3_n(const Dims &d, const FftPlan &p, const float *in, TO *out, const
 template <int N, int TKC, typename TO>
 void deriv_strided_t(const Dims &d, const FftPlan &p, int n, const float *in, TO *out, const float *add,
                      long long estride, long long pstride, int nplanes, cudaStream_t st) {
+    if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
+        // the double-buffered persistent form
+        const size_t smem = 3 * (size_t)n * TKC * sizeof(float2);
+        const int ntk = (d.n3 + 2 * TKC - 1) / (2 * TKC), nitems = ntk * nplanes;
+        const int grid = persistent_grid(nitems, smem);
+        if constexpr (std::is_same<TO, float>::value) {
+            if (add) {
+                set_smem<k_deriv_strided_p<N, TKC, EPI_ADD, TO>>(smem);
+                k_deriv_strided_p<N, TKC, EPI_ADD, TO><<<grid, kThreads, smem, st>>>(in, out, add, d.n3, estride,
+                                                                                   pstride, p, ntk, nitems);
+                return;
+            }
+        }
+        set_smem<k_deriv_strided_p<N, TKC, EPI_STORE, TO>>(smem);
+        k_deriv_strided_p<N, TKC, EPI_STORE, TO><<<grid, kThreads, smem, st>>>(in, out, add, d.n3, estride, pstride,
+                                                                             p, ntk, nitems);
+        return;
+    }
     const size_t smem = 2 * (size_t)n * TKC * sizeof(float2);
     const dim3 grid((d.n3 + 2 * TKC - 1) / (2 * TKC), nplanes);
     if constexpr (std::is_same<TO, float>::value) {

@@ -276,6 +276,17 @@ void set_smem(size_t bytes) {
     a.ensure(K, (int)bytes, "pencil FFT pass");
 }
 
+// 16-byte cp.async of `bytes` (0, 8 or 16) valid bytes, the rest zero-filled
+__device__ __forceinline__ void cp_async16z(void *smem, const void *gmem, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait_n() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
+
 // lines per block of the x3 passes and column tile of the strided passes,
 // chosen so that a block's shared memory stays near or below ~112 KB
 constexpr int lines_x3(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }

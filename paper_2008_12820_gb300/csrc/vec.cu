@@ -563,7 +563,8 @@ __global__ void k_inner_init(double *c) {
 // FP64 arithmetic, as the host-driven loop (stop on p.q <= 0 without counting
 // the step; otherwise count it and stop when ||r|| <= tol ||r0|| -- unless
 // the iteration count is fixed -- or at maxit), and the while condition
-__global__ void k_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, int fixed) {
+__global__ void k_inner_ctl(double *c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_tail, int maxit,
+                            int fixed) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         c[10] += 1.0;
         unsigned int cont = 0;
@@ -576,6 +577,7 @@ __global__ void k_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, 
             cont = (!conv && it < (double)maxit) ? 1u : 0u;
         }
         cudaGraphSetConditional(h, cont);
+        cudaGraphSetConditional(h_tail, cont);
     }
 }
 // after the PCG update of one outer loop body: the decisions of the
@@ -585,7 +587,8 @@ __global__ void k_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, 
 // non-finite p.Hp, 2 non-positive curvature in the first iteration, c[3]
 // bodies run).  Non-finite p.Hp stops the loop; p.Hp <= 0 counts the step and
 // stops (the update changed nothing); otherwise count and test.
-__global__ void k_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, int maxit, int fixed) {
+__global__ void k_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_tail,
+                          int maxit, int fixed) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         c[3] += 1.0;
         const double pq = d[12];
@@ -603,6 +606,7 @@ __global__ void k_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle
             cont = (!conv && it < (double)maxit) ? 1u : 0u;
         }
         cudaGraphSetConditional(h, cont);
+        cudaGraphSetConditional(h_tail, cont);
     }
 }
 // negative curvature in the first PCG iteration keeps the preconditioned
@@ -635,15 +639,15 @@ void launch_inner_init(double *c, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st);
     k_inner_init<<<1, 32, 0, st>>>(c);
 }
-void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
-                      Profiler *prof) {
+void launch_inner_ctl(double *c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_tail, int maxit,
+                      bool fixed, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st);
-    k_inner_ctl<<<1, 32, 0, st>>>(c, h, maxit, fixed ? 1 : 0);
+    k_inner_ctl<<<1, 32, 0, st>>>(c, h, h_tail, maxit, fixed ? 1 : 0);
 }
-void launch_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, int maxit, bool fixed, cudaStream_t st,
-                    Profiler *prof) {
+void launch_pcg_ctl(const double *d, double *c, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h_tail,
+                    int maxit, bool fixed, cudaStream_t st, Profiler *prof) {
     ProfScope ps(prof, CLAIRE_K_REDUCE, st);
-    k_pcg_ctl<<<1, 32, 0, st>>>(d, c, h, maxit, fixed ? 1 : 0);
+    k_pcg_ctl<<<1, 32, 0, st>>>(d, c, h, h_tail, maxit, fixed ? 1 : 0);
 }
 void launch_pcg_negcopy(const double *c, float *x, float *Ax, const float *z, const float *Ap, long long n,
                         cudaStream_t st, Profiler *prof) {
