@@ -210,6 +210,12 @@ struct claire_ctx {
         if (mvg.exec) cudaGraphExecDestroy(mvg.exec);
         drop_inner_graphs();
         drop_pcg_graphs();
+        if (side) {
+            cudaStreamSynchronize(side);
+            cudaStreamDestroy(side);
+            cudaEventDestroy(ev_fork);
+            cudaEventDestroy(ev_join);
+        }
         if (aux) {
             cudaStreamSynchronize(aux);
             cudaStreamDestroy(aux);
@@ -629,9 +635,21 @@ struct claire_ctx {
         if (deriv_fd8) launch_grad_fd8(d, f, g, st, &prof);
         else spectral_grad_1d(d, ax, f, g, st, &prof);
     }
-    void div(const float *v, float *out) {
-        if (deriv_fd8) launch_div_fd8(d, v, out, st, &prof);
-        else spectral_div_1d(d, ax, v, out, st, &prof);
+    void div(const float *v, float *out) { div_on(v, out, st); }
+    void div_on(const float *v, float *out, cudaStream_t s) {
+        if (deriv_fd8) launch_div_fd8(d, v, out, s, &prof);
+        else spectral_div_1d(d, ax, v, out, s, &prof);
+    }
+
+    // a second stream for work that runs beside the main one (created on
+    // first use, with its fork and join events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    void ensure_side() {
+        if (side) return;
+        CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
     }
 
     // With state_ready, mhist and dispm already hold the state and the X- foot
@@ -640,6 +658,28 @@ struct claire_ctx {
         if (!have_images) throw Error(CLAIRE_ERR_STATE, "images not set (claire_set_images)");
         const size_t N = d.N;
         if (v != vlin) CK(cudaMemcpyAsync(vlin, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        // After an adopted trial only X+, div v and c remain besides grad m^j,
+        // and they do not depend on it: they run on a second stream while the
+        // gradients run on the context's (joined before returning).  Not while
+        // the profiler times launches one by one.
+        const bool fork = state_ready && !h16 && !prof.on;
+        if (fork) {
+            ensure_side();
+            CK(cudaEventRecord(ev_fork, st));
+            CK(cudaStreamWaitEvent(side, ev_fork, 0));
+            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), side, &prof);
+            div_on(vlin, divv, side);
+            launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, side, &prof);
+            CK(cudaEventRecord(ev_join, side));
+            for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
+            gm0_valid = true;
+            CK(cudaStreamWaitEvent(st, ev_join, 0));
+            check_launch("linearize");
+            ++lin_epoch;
+            have_lin = true;
+            co.gm_valid = false;
+            return;
+        }
         if (state_ready) {
             launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), st, &prof);
         } else if (h16) {

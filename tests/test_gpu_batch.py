@@ -128,3 +128,26 @@ def test_graph_replayed_matvec_equals_direct_launches(claire):
         # device-side loop-control kernels (and one unused preconditioner
         # application at the end of each loop)
         assert n2 > n1 > 0, (prec, pc, n1, n2)
+
+
+def test_side_stream_linearization_equals_serial(claire):
+    """After an accepted line-search step the solver computes X+, div v and
+    the adjoint factor on a second stream beside grad m^j; with the profiler
+    on (launches timed one by one) it runs them in order on one stream.  The
+    solves must agree bit for bit."""
+    w = pairs()[3]
+    out = []
+    for prof in (False, True):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            reg = claire.Registration(w["shape"], w["nt"], w["beta"], w["gamma"])
+            reg.set_images(dev(w["m0"]), dev(w["m1"]))
+            reg.profile_enable(prof)
+            v = torch.zeros((3,) + w["shape"], device="cuda")
+            rep = reg.solve(v)
+            torch.cuda.synchronize()
+            out.append((rep.n_gn, rep.n_pcg, rep.J, v.clone()))
+            reg.close()
+    assert out[0][0] == out[1][0] and out[0][0] >= 2
+    assert out[0][1:3] == out[1][1:3]
+    assert torch.equal(out[0][3], out[1][3])
