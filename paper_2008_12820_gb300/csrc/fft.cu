@@ -70,13 +70,14 @@ k_r2c_x3(const TI *__restrict__ in, float2 *__restrict__ out, long long nlines, 
 // layout.  FP32 input, n a multiple of 4, 16-byte aligned (the launcher
 // checks; otherwise the one-tile-per-block form above runs).
 template <int N, int L>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, fft_in_place(N) ? 3 : 1)
 k_r2c_x3_p(const float *__restrict__ in, float2 *__restrict__ out, long long nlines, FftPlan p, int h3, int p3,
            int nitems) {
     extern __shared__ float2 sm[];
+    constexpr bool IP = fft_in_place(N);  // in-place transform: no scratch tile
     const int n = Fft<N>::size(p), ls = L + 1;
     float2 *A = sm, *B = sm + n * ls;
-    float *S = reinterpret_cast<float *>(sm + 2 * n * ls);
+    float *S = reinterpret_cast<float *>(sm + (IP ? 1 : 2) * n * ls);
     auto load = [&](int item) {
         const long long line0 = (long long)item * 2 * L;
         const float *base = in + line0 * n;
@@ -102,7 +103,9 @@ k_r2c_x3_p(const float *__restrict__ in, float2 *__restrict__ out, long long nli
         }
         __syncthreads();
         if (item + stride < nitems) load(item + stride);
-        float2 *Rz = Fft<N>::template run<L>(A, B, p, ls, -1.f);
+        float2 *Rz = A;
+        if constexpr (IP) fft_ip<N, L, kThreads, L + 1>(A, p.tw, -1.f);
+        else Rz = Fft<N>::template run<L>(A, B, p, ls, -1.f);
         const long long line0 = (long long)item * 2 * L;
         for (int t = threadIdx.x; t < L * h3; t += blockDim.x) {
             const int l = t / h3, k = t - l * h3;
@@ -166,7 +169,100 @@ k_c2c_x2(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s, int ntk,
     }
 }
 
+// Pass 2 for lengths with an in-place compile-time plan (stage_ip): the
+// transform needs no scratch tile, so a block holds only the current and the
+// next tile (three blocks per SM at n2 = 256), and stores two columns
+// (16 bytes) at a time.
+template <int N, int TK, int MT, int MINB>
+__global__ void __launch_bounds__(MT, MINB)
+k_c2c_x2_ip(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s, int ntk, int nitems) {
+    extern __shared__ float2 sm[];
+    constexpr int CH = TK / 2;  // 16-byte chunks per row
+    float2 *cur = sm, *nxt = sm + N * TK;
+    const float2 *__restrict__ tw = p.tw;
+    auto load = [&](int item, float2 *dst) {
+        const int plane = item / ntk, k0 = (item - plane * ntk) * TK;
+        const float2 *base = data + (long long)plane * N * p3 + k0;
+        for (int t = threadIdx.x; t < N * CH; t += MT) {
+            const int e = t / CH, ch = t - e * CH;
+            const int col = k0 + 2 * ch;
+            const int bytes = col + 2 <= h3 ? 16 : (col < h3 ? 8 : 0);
+            cp_async16z(dst + e * TK + 2 * ch, base + (long long)e * p3 + (bytes ? 2 * ch : 0), bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0, cur);
+    for (int item = i0; item < nitems; item += stride) {
+        if (item + stride < nitems) {
+            load(item + stride, nxt);
+            cp_async_wait_n<1>();
+        } else {
+            cp_async_wait_n<0>();
+        }
+        __syncthreads();
+        fft_ip<N, TK, MT>(cur, tw, s);
+        const int plane = item / ntk, k0 = (item - plane * ntk) * TK;
+        float2 *base = data + (long long)plane * N * p3 + k0;
+        for (int t = threadIdx.x; t < N * CH; t += MT) {
+            const int e = t / CH, ch = t - e * CH;
+            const int col = k0 + 2 * ch;
+            const float2 *q = cur + e * TK + 2 * ch;
+            float2 *g = base + (long long)e * p3 + 2 * ch;
+            if (col + 2 <= h3) *reinterpret_cast<float4 *>(g) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+            else if (col < h3) *g = q[0];
+        }
+        __syncthreads();
+        float2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+}
+
 // ---------------------------------------------------------------- pass 3 ---
+// The x1 pass's pointwise step at wavenumber (k1, k2, k3) for the three
+// components a, b, c of one spectral point (kd = the wavenumber with an even
+// axis's Nyquist index set to 0, used in the divergence penalty):
+//   OP_A     beta |k|^2 I + gamma kd kd^T
+//   OP_AINV  its inverse by Sherman-Morrison (identity at k = 0)
+//   OP_X1INV scale only; OP_X1FWD nothing
+// each times scale (the 1/N of the inverse transform).
+template <int OP>
+__device__ __forceinline__ void mul_point(float2 &pa, float2 &pb, float2 &pc, float k1, float k1d, float k2,
+                                          float k2d, float k3, float k3d, const SpecParams &sp) {
+    if (OP == OP_X1FWD) {
+    } else if (OP == OP_X1INV) {
+        pa = make_float2(pa.x * sp.scale, pa.y * sp.scale);
+        pb = make_float2(pb.x * sp.scale, pb.y * sp.scale);
+        pc = make_float2(pc.x * sp.scale, pc.y * sp.scale);
+    } else {
+        const float2 a = pa, b = pb, c = pc;
+        const float kk = k1 * k1 + k2 * k2 + k3 * k3;
+        const float kd2 = k1d * k1d + k2d * k2d + k3d * k3d;
+        const float2 kv = make_float2(k1d * a.x + k2d * b.x + k3d * c.x,
+                                      k1d * a.y + k2d * b.y + k3d * c.y);
+        float diag, coup;
+        if (OP == OP_A) {
+            diag = sp.beta * kk;
+            coup = sp.gamma;
+        } else {
+            if (kk == 0.f) {
+                diag = 1.f;
+                coup = 0.f;
+            } else {
+                const float bk = sp.beta * kk;
+                diag = 1.f / bk;
+                coup = -sp.gamma * diag / (bk + sp.gamma * kd2);
+            }
+        }
+        const float s = sp.scale;
+        pa = make_float2((diag * a.x + coup * k1d * kv.x) * s, (diag * a.y + coup * k1d * kv.y) * s);
+        pb = make_float2((diag * b.x + coup * k2d * kv.x) * s, (diag * b.y + coup * k2d * kv.y) * s);
+        pc = make_float2((diag * c.x + coup * k3d * kv.x) * s, (diag * c.y + coup * k3d * kv.y) * s);
+    }
+}
+
 // x1 forward, multiplier, x1 inverse, in place; all three components at once
 // (the divergence penalty couples them).  Persistent blocks walk the items
 // (TK k3 columns at one k2 index); the three component tiles of the next item
@@ -225,38 +321,7 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3, 
             const float k1 = wavenumber(e, n1), k1d = wavenumber_d1(e, n1);
             const float k3 = (float)i3, k3d = ((n3 & 1) == 0 && 2 * i3 == n3) ? 0.f : k3;
             const int id = e * TK + l;
-            if (OP == OP_X1FWD) {
-            } else if (OP == OP_X1INV) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float2 f = cur[c][id];
-                    cur[c][id] = make_float2(f.x * sp.scale, f.y * sp.scale);
-                }
-            } else {
-                const float2 a = cur[0][id], b = cur[1][id], c = cur[2][id];
-                const float kk = k1 * k1 + k2 * k2 + k3 * k3;
-                const float kd2 = k1d * k1d + k2d * k2d + k3d * k3d;
-                const float2 kv = make_float2(k1d * a.x + k2d * b.x + k3d * c.x,
-                                              k1d * a.y + k2d * b.y + k3d * c.y);
-                float diag, coup;
-                if (OP == OP_A) {
-                    diag = sp.beta * kk;
-                    coup = sp.gamma;
-                } else {
-                    if (kk == 0.f) {
-                        diag = 1.f;
-                        coup = 0.f;
-                    } else {
-                        const float bk = sp.beta * kk;
-                        diag = 1.f / bk;
-                        coup = -sp.gamma * diag / (bk + sp.gamma * kd2);
-                    }
-                }
-                const float s = sp.scale;
-                cur[0][id] = make_float2((diag * a.x + coup * k1d * kv.x) * s, (diag * a.y + coup * k1d * kv.y) * s);
-                cur[1][id] = make_float2((diag * b.x + coup * k2d * kv.x) * s, (diag * b.y + coup * k2d * kv.y) * s);
-                cur[2][id] = make_float2((diag * c.x + coup * k3d * kv.x) * s, (diag * c.y + coup * k3d * kv.y) * s);
-            }
+            mul_point<OP>(cur[0][id], cur[1][id], cur[2][id], k1, k1d, k2, k2d, k3, k3d, sp);
         }
         __syncthreads();
         if (INV) {
@@ -282,6 +347,78 @@ k_mul_x1(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3, 
             cur[c] = nxt[c];
             nxt[c] = t;
         }
+    }
+}
+
+// The same pass for lengths with a compile-time plan.  The three component
+// tiles of an item are interleaved line by line -- 3 TK lines of n1 elements,
+// buf[e * 3TK + c * TK + l] -- and transformed together, in place, by MT
+// threads (stage_ip): one barrier pair per radix stage serves all three
+// components, every thread holds a butterfly in every stage (at n1 = 256,
+// TK = 8: 16 x 24 = 384 radix-16 butterflies for 384 threads), and no
+// scratch tile is needed.  Six tiles of n1*TK: current and next item.
+template <int N, int TK, int OP, int MT, int MINB>
+__global__ void __launch_bounds__(MT, MINB)
+k_mul_x1_ip(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p3, long long cstride,
+            SpecParams sp, int ntk, int nitems) {
+    constexpr bool FWD = OP != OP_X1INV, INV = OP != OP_X1FWD;
+    constexpr int LL = 3 * TK, TILE = N * LL, CH = TK / 2;  // CH: 16-byte chunks per row and component
+    extern __shared__ float2 sm[];
+    float2 *cur = sm, *nxt = sm + TILE;
+    const long long rowstride = (long long)n2 * p3;  // between consecutive i1
+    const float2 *__restrict__ tw = p1.tw;
+    auto load = [&](int item, float2 *dst) {
+        const int i2 = item / ntk, k0 = (item - i2 * ntk) * TK;
+        const float2 *base = data + (long long)i2 * p3 + k0;
+        for (int t = threadIdx.x; t < 3 * N * CH; t += MT) {
+            const int c = t / (N * CH), r = t - c * (N * CH);
+            const int e = r / CH, ch = r - e * CH;
+            const int col = k0 + 2 * ch;
+            const int bytes = col + 2 <= h3 ? 16 : (col < h3 ? 8 : 0);
+            cp_async16z(dst + e * LL + c * TK + 2 * ch, base + c * cstride + e * rowstride + (bytes ? 2 * ch : 0),
+                        bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0, cur);
+    for (int item = i0; item < nitems; item += stride) {
+        if (item + stride < nitems) {
+            load(item + stride, nxt);
+            cp_async_wait_n<1>();
+        } else {
+            cp_async_wait_n<0>();
+        }
+        __syncthreads();
+        if (FWD) fft_ip<N, LL, MT>(cur, tw, -1.f);
+        const int i2 = item / ntk, k0 = (item - i2 * ntk) * TK;
+        const float k2 = wavenumber(i2, n2), k2d = wavenumber_d1(i2, n2);
+        for (int t = threadIdx.x; t < N * TK; t += MT) {
+            const int e = t / TK, l = t - e * TK;
+            const int i3 = k0 + l;
+            const float k1 = wavenumber(e, N), k1d = wavenumber_d1(e, N);
+            const float k3 = (float)i3, k3d = ((n3 & 1) == 0 && 2 * i3 == n3) ? 0.f : k3;
+            float2 *q = cur + e * LL + l;
+            mul_point<OP>(q[0], q[TK], q[2 * TK], k1, k1d, k2, k2d, k3, k3d, sp);
+        }
+        __syncthreads();
+        if (INV) fft_ip<N, LL, MT>(cur, tw, +1.f);
+        // back to global memory, two columns (16 bytes) per store
+        float2 *base = data + (long long)i2 * p3 + k0;
+        for (int t = threadIdx.x; t < 3 * N * CH; t += MT) {
+            const int c = t / (N * CH), r = t - c * (N * CH);
+            const int e = r / CH, ch = r - e * CH;
+            const int col = k0 + 2 * ch;
+            const float2 *s = cur + e * LL + c * TK + 2 * ch;
+            float2 *g = base + c * cstride + e * rowstride + 2 * ch;
+            if (col + 2 <= h3) *reinterpret_cast<float4 *>(g) = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+            else if (col < h3) *g = s[0];
+        }
+        __syncthreads();
+        float2 *t = cur;
+        cur = nxt;
+        nxt = t;
     }
 }
 
@@ -338,13 +475,14 @@ k_c2r_x3(const float2 *__restrict__ in, TO *__restrict__ out, const float *__res
 // (one contiguous chunk of 2L*p3 complex values) are fetched by 16-byte
 // cp.async into a staging buffer while the current tile is transformed.
 template <int N, int L, int EPI, typename TO = float>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, fft_in_place(N) ? 3 : 1)
 k_c2r_x3_p(const float2 *__restrict__ in, TO *__restrict__ out, const float *__restrict__ add, long long nlines,
            FftPlan p, int h3, int p3, int nitems) {
     extern __shared__ float2 sm[];
+    constexpr bool IP = fft_in_place(N);  // in-place transform: no scratch tile
     const int n = Fft<N>::size(p), ls = L + 1;
     float2 *A = sm, *B = sm + n * ls;
-    float2 *S = sm + 2 * n * ls;  // staging: 2L lines of p3 complex values
+    float2 *S = sm + (IP ? 1 : 2) * n * ls;  // staging: 2L lines of p3 complex values
     const bool even = (n & 1) == 0;
     auto load = [&](int item) {
         const long long line0 = (long long)item * 2 * L;
@@ -382,7 +520,9 @@ k_c2r_x3_p(const float2 *__restrict__ in, TO *__restrict__ out, const float *__r
         }
         __syncthreads();
         if (item + stride < nitems) load(item + stride);
-        float2 *R = Fft<N>::template run<L>(A, B, p, ls, +1.f);
+        float2 *R = A;
+        if constexpr (IP) fft_ip<N, L, kThreads, L + 1>(A, p.tw, +1.f);
+        else R = Fft<N>::template run<L>(A, B, p, ls, +1.f);
         const long long line0 = (long long)item * 2 * L;
         for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
             const int l = t / n, e = t - l * n;
@@ -429,7 +569,8 @@ void r2c_l(const Dims &d, const FftPlan &p, const TI *in, float2 *out, long long
            cudaStream_t st) {
     if constexpr (std::is_same<TI, float>::value) {
         if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
-            const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2) + (size_t)2 * L * d.n3 * sizeof(float);
+            const size_t smem = (fft_in_place(N) ? 1 : 2) * (size_t)d.n3 * (L + 1) * sizeof(float2) +
+                                (size_t)2 * L * d.n3 * sizeof(float);
             const int nitems = (int)((nlines + 2 * L - 1) / (2 * L));
             set_smem<k_r2c_x3_p<N, L>>(smem);
             k_r2c_x3_p<N, L><<<persistent_grid(nitems, smem), kThreads, smem, st>>>(in, out, nlines, p, d.h3, d.p3,
@@ -478,9 +619,22 @@ void c2c_t(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cu
     k_c2c_x2<N, TK><<<grid, kThreads, smem, st>>>(data, p, d.h3, d.p3, s, ntk, nitems);
 }
 
+template <int N, int TK>
+void c2c_ip(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
+    constexpr int MT = 256;
+    constexpr size_t smem = 2 * (size_t)N * TK * sizeof(float2);
+    constexpr int MINB = smem <= 72 * 1024 ? 3 : 2;
+    const int ntk = (d.h3 + TK - 1) / TK, nitems = ntk * ncomp * d.n1;
+    set_smem<k_c2c_x2_ip<N, TK, MT, MINB>>(smem);
+    k_c2c_x2_ip<N, TK, MT, MINB><<<persistent_grid(nitems, smem), MT, smem, st>>>(data, p, d.h3, d.p3, s, ntk,
+                                                                                  nitems);
+}
+
 template <int N>
 void c2c_n(const Dims &d, const FftPlan &p, float2 *data, int ncomp, float s, cudaStream_t st) {
-    if constexpr (N > 0) {
+    if constexpr (fft_in_place(N)) {
+        c2c_ip<N, tile_cols(N, 1)>(d, p, data, ncomp, s, st);
+    } else if constexpr (N > 0) {
         c2c_t<N, tile_cols(N, 2)>(d, p, data, ncomp, s, st);
     } else {
         switch (tile_cols(d.n2, 2)) {
@@ -510,10 +664,26 @@ void mul_t(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, 
                                                                                 cstride, sp, ntk, nitems);
 }
 
+// compile-time plans: the interleaved in-place form, 384 threads, six tiles
+template <int N, int TK, int OP>
+void mul_ip(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
+    constexpr int MT = 384;
+    constexpr size_t smem = (size_t)6 * N * TK * sizeof(float2);
+    constexpr int MINB = smem <= 112 * 1024 ? 2 : 1;
+    const long long cstride = (long long)d.n1 * d.n2 * d.p3;
+    const int ntk = (d.h3 + TK - 1) / TK, nitems = ntk * d.n2;
+    set_smem<k_mul_x1_ip<N, TK, OP, MT, MINB>>(smem);
+    k_mul_x1_ip<N, TK, OP, MT, MINB><<<persistent_grid(nitems, smem), MT, smem, st>>>(data, p, d.n2, d.n3, d.h3,
+                                                                                       d.p3, cstride, sp, ntk, nitems);
+}
+
 template <int N, int OP>
 void mul_n(const Dims &d, const FftPlan &p, float2 *data, const SpecParams &sp, cudaStream_t st) {
     constexpr int NB = 6;  // three component tiles for the current item, three for the next
-    if constexpr (N > 0) {
+    if constexpr (fft_in_place(N)) {
+        // six tiles in all (no scratch): the column count of five data tiles and one more
+        mul_ip<N, tile_cols(N, NB - 1), OP>(d, p, data, sp, st);
+    } else if constexpr (N > 0) {
         mul_t<N, tile_cols(N, NB), OP>(d, p, data, sp, st);
     } else {
         switch (tile_cols(d.n1, NB)) {
@@ -540,7 +710,8 @@ void c2r_l(const Dims &d, const FftPlan &p, const float2 *in, TO *out, const flo
            long long nlines, cudaStream_t st) {
     if (((uintptr_t)in & 15) == 0) {
         // the persistent form with the next tile staged by cp.async
-        const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2) + (size_t)2 * L * d.p3 * sizeof(float2);
+        const size_t smem = (fft_in_place(N) ? 1 : 2) * (size_t)d.n3 * (L + 1) * sizeof(float2) +
+                            (size_t)2 * L * d.p3 * sizeof(float2);
         const int nitems = (int)((nlines + 2 * L - 1) / (2 * L));
         const int grid = persistent_grid(nitems, smem);
         if (add) {

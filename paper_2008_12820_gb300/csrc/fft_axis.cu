@@ -73,12 +73,13 @@ k_deriv_x3(const float *__restrict__ in, TO *out, const float *add, long long nl
 // transposed from the staging buffer into the transform layout.  Needs n a
 // multiple of 4 and 16-byte aligned fields (the launcher checks).
 template <int N, int L, int EPI, typename TO>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, fft_in_place(N) ? (N >= 256 ? 3 : 2) : 1)
 k_deriv_x3_p(const float *__restrict__ in, TO *out, const float *add, long long nlines, FftPlan p, int nitems) {
     extern __shared__ float2 sm[];
+    constexpr bool IP = fft_in_place(N);  // in-place transforms: no scratch tile
     const int n = Fft<N>::size(p), ls = L + 1;
     float2 *A = sm, *B = sm + n * ls;
-    float *S = reinterpret_cast<float *>(sm + 2 * n * ls);  // staging: 2L lines of n floats
+    float *S = reinterpret_cast<float *>(sm + (IP ? 1 : 2) * n * ls);  // staging: 2L lines of n floats
     auto load = [&](int item) {
         const long long line0 = (long long)item * 2 * L;
         const float *base = in + line0 * n;
@@ -103,7 +104,9 @@ k_deriv_x3_p(const float *__restrict__ in, TO *out, const float *add, long long 
         }
         __syncthreads();
         if (item + stride < nitems) load(item + stride);
-        float2 *R = Fft<N>::template run<L>(A, B, p, ls, -1.f);
+        float2 *R = A;
+        if constexpr (IP) fft_ip<N, L, kThreads, L + 1>(A, p.tw, -1.f);
+        else R = Fft<N>::template run<L>(A, B, p, ls, -1.f);
         for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
             const int e = t / L, l = t - e * L;
             const float k = wavenumber_d1(e, n) * sc;
@@ -111,7 +114,9 @@ k_deriv_x3_p(const float *__restrict__ in, TO *out, const float *add, long long 
             R[e * ls + l] = make_float2(-k * z.y, k * z.x);
         }
         __syncthreads();
-        float2 *Q = Fft<N>::template run<L>(R, R == A ? B : A, p, ls, +1.f);
+        float2 *Q = R;
+        if constexpr (IP) fft_ip<N, L, kThreads, L + 1>(R, p.tw, +1.f);
+        else Q = Fft<N>::template run<L>(R, R == A ? B : A, p, ls, +1.f);
         const long long line0 = (long long)item * 2 * L;
         for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
             const int l = t / n, e = t - l * n;
@@ -250,6 +255,75 @@ k_deriv_strided_p(const float *__restrict__ in, TO *out, const float *add, int n
     }
 }
 
+// The strided derivative for lengths with an in-place plan (stage_ip): no
+// scratch tile, so a block holds only the current and the next tile (three
+// blocks per SM at n = 256).  Same transforms and multiplier per line as
+// k_deriv_strided_p.
+template <int N, int TKC, int EPI, typename TO, int MT, int MINB>
+__global__ void __launch_bounds__(MT, MINB)
+k_deriv_strided_ip(const float *__restrict__ in, TO *out, const float *add, int n3, long long estride,
+                   long long pstride, FftPlan p, int ntk, int nitems) {
+    extern __shared__ float2 sm[];
+    float2 *cur = sm, *nxt = sm + N * TKC;
+    constexpr int CH = TKC / 2;  // 16-byte chunks per row
+    const float2 *__restrict__ tw = p.tw;
+    auto load = [&](int item, float2 *dst) {
+        const int plane = item / ntk, k0 = (item - plane * ntk) * 2 * TKC;
+        const float *base = in + (long long)plane * pstride + k0;
+        for (int t = threadIdx.x; t < N * CH; t += MT) {
+            const int e = t / CH, ch = t - e * CH;
+            const int i3 = k0 + 4 * ch;
+            const int bytes = i3 + 4 <= n3 ? 16 : 0;
+            cp_async16z(dst + e * TKC + 2 * ch, base + e * estride + (bytes ? 4 * ch : 0), bytes);
+        }
+        cp_async_commit_all();
+    };
+    const int i0 = blockIdx.x, stride = gridDim.x;
+    if (i0 >= nitems) return;
+    load(i0, cur);
+    const float sc = 1.f / (float)N;
+    for (int item = i0; item < nitems; item += stride) {
+        if (item + stride < nitems) {
+            load(item + stride, nxt);
+            cp_async_wait_n<1>();
+        } else {
+            cp_async_wait_n<0>();
+        }
+        __syncthreads();
+        fft_ip<N, TKC, MT>(cur, tw, -1.f);
+        for (int t = threadIdx.x; t < N * TKC; t += MT) {
+            const int e = t / TKC;
+            const float k = wavenumber_d1(e, N) * sc;
+            const float2 z = cur[t];
+            cur[t] = make_float2(-k * z.y, k * z.x);
+        }
+        __syncthreads();
+        fft_ip<N, TKC, MT>(cur, tw, +1.f);
+        const int plane = item / ntk, k0 = (item - plane * ntk) * 2 * TKC;
+        const long long base = (long long)plane * pstride;
+        for (int t = threadIdx.x; t < N * TKC; t += MT) {
+            const int e = t / TKC, c = t - e * TKC;
+            const int i3 = k0 + 2 * c;
+            const long long o = base + e * estride + i3;
+            const float2 z = cur[t];
+            if (i3 < n3) {
+                float val = z.x;
+                if (EPI == EPI_ADD) val += add[o];
+                str(out + o, val);
+            }
+            if (i3 + 1 < n3) {
+                float val = z.y;
+                if (EPI == EPI_ADD) val += add[o + 1];
+                str(out + o + 1, val);
+            }
+        }
+        __syncthreads();
+        float2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+}
+
 // ---- axis derivatives: launchers ------------------------------------------
 constexpr int deriv_cols(int n) { return n <= 256 ? 16 : (n <= 512 ? 8 : 4); }
 
@@ -260,7 +334,8 @@ void deriv_x3_l(const Dims &d, const FftPlan &p, const float *in, TO *out, const
     const long long nlines = (long long)d.n1 * d.n2;
     if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
         // the persistent form with the next tile staged by cp.async
-        const size_t smem = 2 * (size_t)d.n3 * (L + 1) * sizeof(float2) + (size_t)2 * L * d.n3 * sizeof(float);
+        const size_t smem = (fft_in_place(N) ? 1 : 2) * (size_t)d.n3 * (L + 1) * sizeof(float2) +
+                            (size_t)2 * L * d.n3 * sizeof(float);
         const int nitems = (int)((nlines + 2 * L - 1) / (2 * L));
         const int grid = persistent_grid(nitems, smem);
         if constexpr (std::is_same<TO, float>::value) {
@@ -303,6 +378,29 @@ void deriv_x3_n(const Dims &d, const FftPlan &p, const float *in, TO *out, const
 template <int N, int TKC, typename TO>
 void deriv_strided_t(const Dims &d, const FftPlan &p, int n, const float *in, TO *out, const float *add,
                      long long estride, long long pstride, int nplanes, cudaStream_t st) {
+    if constexpr (fft_in_place(N)) {
+        if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
+            // the in-place double-buffered persistent form
+            constexpr int MT = 256;
+            constexpr size_t smem = 2 * (size_t)N * TKC * sizeof(float2);
+            // three blocks per SM where the registers allow it without spills (n = 128 spills at 85)
+            constexpr int MINB = smem <= 72 * 1024 && N >= 256 ? 3 : 2;
+            const int ntk = (d.n3 + 2 * TKC - 1) / (2 * TKC), nitems = ntk * nplanes;
+            const int grid = persistent_grid(nitems, smem);
+            if constexpr (std::is_same<TO, float>::value) {
+                if (add) {
+                    set_smem<k_deriv_strided_ip<N, TKC, EPI_ADD, TO, MT, MINB>>(smem);
+                    k_deriv_strided_ip<N, TKC, EPI_ADD, TO, MT, MINB><<<grid, MT, smem, st>>>(
+                        in, out, add, d.n3, estride, pstride, p, ntk, nitems);
+                    return;
+                }
+            }
+            set_smem<k_deriv_strided_ip<N, TKC, EPI_STORE, TO, MT, MINB>>(smem);
+            k_deriv_strided_ip<N, TKC, EPI_STORE, TO, MT, MINB><<<grid, MT, smem, st>>>(
+                in, out, add, d.n3, estride, pstride, p, ntk, nitems);
+            return;
+        }
+    }
     if (d.n3 % 4 == 0 && ((uintptr_t)in & 15) == 0) {
         // the double-buffered persistent form
         const size_t smem = 3 * (size_t)n * TKC * sizeof(float2);

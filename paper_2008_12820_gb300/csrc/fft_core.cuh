@@ -249,6 +249,68 @@ __device__ __forceinline__ float2 *fft_ct(float2 *A, float2 *B, const float2 *__
     }
 }
 
+// In-place form of the compile-time plan for NT threads: each thread reads all
+// of its butterflies of a stage into registers (IT of them), the block waits,
+// and the results go back into the same buffer.  No scratch buffer, so a
+// block can hold more lines in the same shared memory, and with WORK a
+// multiple of NT every thread has work in every stage.  Same butterflies,
+// twiddles and order of operations per line as stage_ct.
+template <int N, int R, int NS, int L, int NT, int LS = L>
+__device__ __forceinline__ void stage_ip(float2 *__restrict__ A, const float2 *__restrict__ tw, float s) {
+    constexpr int NB = N / R, WORK = NB * L, TSTRIDE = N / (NS * R), IT = (WORK + NT - 1) / NT;
+    float2 a[IT][R];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int t = threadIdx.x + i * NT;
+        if (WORK % NT == 0 || t < WORK) {
+            const int l = t % L;
+            const int j = t / L;
+            const int k = j % NS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[i][r] = A[(j + r * NB) * LS + l];
+            if (NS > 1 && k != 0) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(tw + r * k * TSTRIDE);
+                    w.y *= -s;
+                    a[i][r] = cmul(a[i][r], w);
+                }
+            }
+            dft<R>(a[i], s);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int t = threadIdx.x + i * NT;
+        if (WORK % NT == 0 || t < WORK) {
+            const int l = t % L;
+            const int j = t / L;
+            const int k = j % NS;
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) A[(base + r * NS) * LS + l] = a[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+// FFT of L lines of length N stored as A[e * LS + l] (LS >= L; an odd LS
+// keeps the transposing loads of the x3 passes free of bank conflicts), in
+// place, NT threads; ends behind a barrier
+template <int N, int L, int NT, int LS = L, int S = 0>
+__device__ __forceinline__ void fft_ip(float2 *A, const float2 *__restrict__ tw, float s) {
+    if constexpr (S < num_stages(N)) {
+        stage_ip<N, radix_at(N, S), ns_before(N, S), L, NT, LS>(A, tw, s);
+        fft_ip<N, L, NT, LS, S + 1>(A, tw, s);
+    }
+}
+
+// The lengths whose passes use the in-place plan: powers of two from 128 on
+// (radix-16 stages with one or two butterflies a thread, no register spills);
+// the other lengths keep the out-of-place stages with a scratch tile.
+__host__ __device__ constexpr bool fft_in_place(int n) { return n >= 128 && (n & (n - 1)) == 0; }
+
 // N > 0: compile-time plan of that length; N == 0: the runtime plan p
 template <int N>
 struct Fft {
