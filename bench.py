@@ -746,6 +746,45 @@ def run_pcstudy(args):
                       "nt": 4, "gamma": 1.0, "eps_n": 5e-2, "eps_h0": 1e-3, "rows": rows}), flush=True)
 
 
+def run_oracle_study(args):
+    """The FP64 oracle timed at the sizes the measurement plan names, on the
+    host cores (OpenMP over all of them): gradient and one Hessian matvec at
+    128^3 and 256^3 (v = half the generating velocity, a smooth direction),
+    full solves from v = 0 at 32^3 and 128^3.  One JSON line; about half a
+    minute of CPU work.  Context for the GPU numbers, not a bench line."""
+    import numpy as np
+
+    import oracle
+    from paper_2008_12820_gb300 import synth
+    oracle.build()
+    rows = []
+    for n in (128, 256):
+        w = synth.workload(WORKLOAD, shape=(n, n, n))
+        P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
+        v = (0.5 * w["v_true"]).astype(np.float64)
+        vt = synth.smooth_direction((n, n, n), 7).astype(np.float64)
+        t0 = time.perf_counter()
+        P.gradient(v)
+        t1 = time.perf_counter()
+        P.matvec(vt)
+        t2 = time.perf_counter()
+        P.close()
+        rows.append({"what": "gradient + matvec", "n": n, "gradient_s": round(t1 - t0, 3),
+                     "matvec_s": round(t2 - t1, 3), "matvec_gvoxel_s": round(n ** 3 / (t2 - t1) / 1e9, 6)})
+    for n in (32, 128):
+        w = synth.workload("sin32" if n == 32 else WORKLOAD, shape=None if n == 32 else (n, n, n))
+        P = oracle.Problem(w["m0"], w["m1"], w["nt"], w["beta"], w["gamma"])
+        t0 = time.perf_counter()
+        _, rep = P.solve(np.zeros((3,) + tuple(w["shape"])))
+        t1 = time.perf_counter()
+        P.close()
+        rows.append({"what": "full solve from v = 0", "n": n, "workload": "sin32" if n == 32 else WORKLOAD,
+                     "n_gn": rep.n_gn, "n_pcg": rep.n_pcg, "solve_s": round(t1 - t0, 3),
+                     "gvoxel_s": round(n ** 3 / (t1 - t0) / 1e9, 7)})
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    print(json.dumps({"study": "FP64 oracle on the host cores", "cores": cores, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -754,6 +793,8 @@ def main():
         run_batch(args)
     elif args.workload == "pcstudy":
         run_pcstudy(args)
+    elif args.workload == "oracle-study":
+        run_oracle_study(args)
     else:
         run_ours(args)
 
