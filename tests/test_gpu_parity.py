@@ -67,6 +67,27 @@ def test_spectral_operators(claire, shape):
         assert rel(host(t), O.apply_Ainv(v, beta, gamma)) < TOL
 
 
+# grids whose axes take the in-place transform plans (powers of two from 128
+# on) in every pass: x1 lengths 128 and 512 (the interleaved x1 multiplier
+# pass, the x1 derivative), x2 lengths 128 and 512 (the x2 pass, the x2
+# derivative), x3 lengths 256 and 512 (the x3 forward, inverse and derivative
+# passes); the other axes take the out-of-place plans beside them
+IN_PLACE_SHAPES = [(128, 16, 512), (512, 128, 32), (16, 512, 256)]
+
+
+@pytest.mark.parametrize("shape", IN_PLACE_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_spectral_operators_in_place_lengths(claire, shape):
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal(shape).astype(np.float32)
+    v = rng.standard_normal((3,) + shape).astype(np.float32)
+    beta, gamma = 1e-2, 1.0
+    with claire.Registration(shape, 4, beta, gamma) as reg:
+        assert rel(host(reg.grad(dev(f))), O.grad(f)) < TOL
+        assert rel(host(reg.div(dev(v))), O.div(v)) < TOL
+        assert rel(host(reg.apply_A(dev(v))), O.apply_A(v, beta, gamma)) < TOL
+        assert rel(host(reg.precond(dev(v))), O.apply_Ainv(v, beta, gamma)) < TOL
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_interpolation(claire, shape):
     rng = np.random.default_rng(1)
