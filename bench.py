@@ -77,6 +77,8 @@ KNAMES = {"footpoint": "k_footpoints_box, k_footpoints, k_tile_ranges, k_sl_pipe
 # 60% of the HBM peak); the others are streaming vector work and reductions
 TRANSPORT_FFT = ("footpoint", "state", "adjoint", "incstate", "incadj", "fft_r2c", "fft_c2c", "fft_mul",
                  "fft_c2r", "deriv")
+# one cubic SL interpolation per voxel and launch (the bench's solves use cubic interpolation)
+SL_STEP_CLASSES = ("state", "adjoint", "incstate", "incadj")
 
 
 def parse():
@@ -299,6 +301,18 @@ def run_ours(args):
                      "GBps": round(b_ / (t_ * 1e-3) / 1e9, 1) if t_ > 0 else None,
                      "frac": round(b_ / (t_ * 1e-3) / 1e9 / peak, 4) if t_ > 0 else None}
                  for k, (n_, t_, b_) in prof.items() if n_}
+    # The SL step classes are bound by the shared-memory data pipe, not by HBM:
+    # each voxel of a step reads its 64 cubic stencil taps there, one 128-byte
+    # wavefront per warp and tap, so a step over N voxels needs at least
+    # 64 N / 32 wavefront-cycles spread over the SMs.  That bound at the SM
+    # clock sampled during the timed region, and the class's fraction of it.
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    f_sm = (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0) * 1e6 if isinstance(clk, dict) else 2070e6
+    for k in SL_STEP_CLASSES:
+        e = breakdown.get(k)
+        if e and e["ms_per_step"] > 0:
+            bound_ms = e["launches"] * N * 64 / 32 / sms / f_sm * 1e3
+            e["smem_pipe"] = {"bound_ms": round(bound_ms, 4), "frac": round(bound_ms / e["ms_per_step"], 4)}
     tf = {k: e["frac"] for k, e in breakdown.items() if k in TRANSPORT_FFT and e["frac"] is not None}
     min_tf = min(tf, key=tf.get) if tf else None
     roofline = {"bound": "hbm", "kernel": dom, "kernels": KNAMES[dom],
