@@ -60,10 +60,12 @@ def body_force_bound(total, reg_part):
     return TOL + 2 * U16 * np.linalg.norm(total - reg_part) / np.linalg.norm(total)
 
 
-@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((64, 64, 64), 8)])
+@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((64, 64, 64), 8), ((128, 24, 256), 2)])
 def test_fp16_storage_operators_vs_oracle(claire, shape, nt):
     """state, grad m, adjoint, gradient, objective and matvec of one
-    linearization (rows a3, a4, a6, a7-a9) in the FP16-storage form"""
+    linearization (rows a3, a4, a6, a7-a9) in the FP16-storage form; the
+    128 x 24 x 256 grid takes the in-place transform plans along x1 and x3
+    for the FP16 outputs of grad m^j"""
     beta, gamma = 1e-2, 1.0
     d = synth.sinusoid_pair(shape, 1000)
     m0, m1, v = d["m0"], d["m1"], (0.8 * d["v_true"]).astype(np.float32)
