@@ -60,12 +60,10 @@ def body_force_bound(total, reg_part):
     return TOL + 2 * U16 * np.linalg.norm(total - reg_part) / np.linalg.norm(total)
 
 
-@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((64, 64, 64), 8), ((128, 24, 256), 2)])
+@pytest.mark.parametrize("shape,nt", [((32, 32, 32), 4), ((48, 40, 36), 3), ((64, 64, 64), 8)])
 def test_fp16_storage_operators_vs_oracle(claire, shape, nt):
     """state, grad m, adjoint, gradient, objective and matvec of one
-    linearization (rows a3, a4, a6, a7-a9) in the FP16-storage form; the
-    128 x 24 x 256 grid takes the in-place transform plans along x1 and x3
-    for the FP16 outputs of grad m^j"""
+    linearization (rows a3, a4, a6, a7-a9) in the FP16-storage form"""
     beta, gamma = 1e-2, 1.0
     d = synth.sinusoid_pair(shape, 1000)
     m0, m1, v = d["m0"], d["m1"], (0.8 * d["v_true"]).astype(np.float32)
@@ -88,6 +86,43 @@ def test_fp16_storage_operators_vs_oracle(claire, shape, nt):
         assert abs(J - Jo) / abs(Jo) < TOL
         H = reg.hess_matvec(dev(v), dev(vt))
         assert rel(host(H), Ho) < tol_h
+
+
+def test_fp16_storage_in_place_lengths(claire):
+    """A 128 x 24 x 256 grid, whose x1 and x3 axes take the in-place transform
+    plans (FP16 outputs of grad m^j there).  The stored fields against the
+    oracle within u; the gradient and the matvec against the FP32 form on the
+    same grid, within 2u of the body force: on this grid the FP32 rounding
+    of beta A v itself (|k|^2 up to 128^2 along x3) is above 1e-5 of ||g||, so
+    the oracle comparison of g would measure the FFT floor, not the FP16
+    storage."""
+    shape, nt, beta, gamma = (128, 24, 256), 2, 1e-2, 1.0
+    d = synth.sinusoid_pair(shape, 1000)
+    m0, m1, v = d["m0"], d["m1"], (0.8 * d["v_true"]).astype(np.float32)
+    vt = synth.smooth_direction(shape, 7).astype(np.float32)
+    P = O.Problem(m0, m1, nt, beta, gamma)
+    P.linearize(v)
+    mh, gmh = P.state_history(), P.grad_state_history()
+    go, Jo, lh = P.gradient(v, want_adjoint=True)
+    Ho = P.matvec(vt)
+    b = go - O.apply_A(v, beta, gamma)
+    bt = Ho - O.apply_A(vt, beta, gamma)
+    out = {}
+    for prec in ("fp32", "fp16"):
+        with claire.Registration(shape, nt, beta, gamma, precision=prec) as reg:
+            reg.set_images(dev(m0), dev(m1))
+            g, J = reg.gradient(dev(v))
+            if prec == "fp16":
+                for j in range(nt + 1):
+                    assert rel(host(reg.field("state", j)), mh[j]) < U16 + TOL, j
+                    assert rel(host(reg.field("gradm", j)), gmh[j]) < U16 + TOL, j
+                    assert rel(host(reg.field("adj", j)), lh[j]) < U16 + TOL, j
+            H = reg.hess_matvec(dev(v), dev(vt))
+            out[prec] = (host(g), J, host(H))
+    (g32, J32, H32), (g16, J16, H16) = out["fp32"], out["fp16"]
+    assert abs(J16 - Jo) / abs(Jo) < TOL and abs(J32 - Jo) / abs(Jo) < TOL
+    assert np.linalg.norm(g16 - g32) <= 2 * U16 * np.linalg.norm(b) + 1e-6 * np.linalg.norm(g32)
+    assert np.linalg.norm(H16 - H32) <= 2 * U16 * np.linalg.norm(bt) + 1e-6 * np.linalg.norm(H32)
 
 
 def test_fp16_storage_fixed_work_step_vs_oracle(claire):
