@@ -292,9 +292,10 @@ int claire_solve_host(claire_ctx *ctx, const float *m0, const float *m1, const f
 /* Batched form (no counterpart in the paper, which registers one pair at a
  * time): solve n independent registrations together, one per context, each
  * exactly as claire_solve would (same options for all; contexts may differ
- * in grid size, nt, beta, gamma and precision).  Each context runs on a CUDA
- * stream created for the call and is driven by a host thread of its own, so
- * the kernels of different pairs overlap on the GPU; the results are bitwise
+ * in grid size, nt, beta, gamma and precision).  Up to eight host threads,
+ * each with a CUDA stream created for the call, take the contexts largest
+ * grid first and solve them one after the other on their stream, so the
+ * kernels of different pairs overlap on the GPU; the results are bitwise
  * those of n claire_solve calls.  ctxs[i] (distinct, on the current device)
  * with velocity v[i] (float[3][N_i], device, in/out); reports may be NULL,
  * else n entries.  The call first synchronizes each context's stream and
