@@ -215,8 +215,9 @@ def precond_noalloc(r, s, beta, gamma, stream=None):
 def solve_batch(regs, vs, check=True, **opts):
     """Solve the registrations ``regs`` (Registration objects, distinct) with
     velocities ``vs`` (float32 CUDA tensors, in/out) together through
-    claire_solve_batch: one CUDA stream and host thread per pair, results
-    bitwise those of ``reg.solve(v)`` one by one.  Returns the reports."""
+    claire_solve_batch: up to eight host threads with a CUDA stream each take
+    the pairs largest grid first; results bitwise those of ``reg.solve(v)``
+    one by one.  Returns the reports."""
     n = len(regs)
     if n != len(vs) or n == 0:
         raise ValueError("need as many velocities as registrations (>= 1)")
