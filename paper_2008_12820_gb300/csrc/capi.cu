@@ -701,6 +701,30 @@ struct claire_ctx {
             }
             grad(m1f, gm1f);
             launch_f2h(gm1f, hist(gmhist_h, nt, 3), 3 * (long long)N, st, &prof);
+        } else if (!prof.on) {
+            // X+, div v and c on the second stream while X-, the state and
+            // grad m^j run on the context's (the same kernels as below, side
+            // by side; joined before returning)
+            ensure_side();
+            CK(cudaEventRecord(ev_fork, st));
+            CK(cudaStreamWaitEvent(side, ev_fork, 0));
+            launch_footpoints(d, nt, vlin, nullptr, dispp, nullptr, rng_p(), side, &prof);
+            div_on(vlin, divv, side);
+            launch_adjoint_factor(d, nt, divv, dispp, rng_p(), cfac, side, &prof);
+            CK(cudaEventRecord(ev_join, side));
+            launch_footpoints(d, nt, vlin, dispm, nullptr, rng_m(), nullptr, st, &prof);
+            wait_images();
+            CK(cudaMemcpyAsync(mhist, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            for (int j = 0; j < nt; ++j)
+                launch_state_step(d, hist(mhist, j), dispm, rng_m(), hist(mhist, j + 1), st, &prof);
+            for (int j = gm0_valid ? 1 : 0; j <= nt; ++j) grad(hist(mhist, j), hist(gmhist, j, 3));
+            gm0_valid = true;
+            CK(cudaStreamWaitEvent(st, ev_join, 0));
+            check_launch("linearize");
+            ++lin_epoch;
+            have_lin = true;
+            co.gm_valid = false;
+            return;
         } else {
             launch_footpoints(d, nt, vlin, dispm, dispp, rng_m(), rng_p(), st, &prof);
             wait_images();
