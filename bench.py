@@ -339,7 +339,12 @@ def run_ours(args):
                   "phases_of_profiled_solve_ms": {"hess": round(rep_prof.t_hess_ms, 3),
                                                   "grad": round(rep_prof.t_grad_ms, 3),
                                                   "pc": round(rep_prof.t_pc_ms, 3),
-                                                  "obj": round(rep_prof.t_obj_ms, 3)}},
+                                                  "obj": round(rep_prof.t_obj_ms, 3)},
+                  # the Gauss-Newton matvec as the solver applies it inside PCG,
+                  # beta A p carried by the recurrence instead of a transform
+                  # (events around each launch group: a slight overestimate)
+                  "pcg_matvec_ms_profiled": round(rep_prof.t_hess_ms / rep_prof.n_matvec, 4)
+                  if rep_prof.n_matvec else None},
         "roofline": roofline, "kernel_breakdown": breakdown,
         "min_frac_transport_fft": {"class": min_tf, "frac": tf.get(min_tf)} if min_tf else None,
         "gpu_launches": int(launches), "clocks": clk,
