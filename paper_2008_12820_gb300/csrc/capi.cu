@@ -648,9 +648,21 @@ struct claire_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void ensure_side() {
         if (side) return;
-        CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        // all three or none: a failure leaves the context as it was
+        cudaStream_t s = nullptr;
+        cudaEvent_t f = nullptr, j = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (j) cudaEventDestroy(j);
+            if (f) cudaEventDestroy(f);
+            if (s) cudaStreamDestroy(s);
+            CK(e);
+        }
+        side = s;
+        ev_fork = f;
+        ev_join = j;
     }
 
     // With state_ready, mhist and dispm already hold the state and the X- foot
