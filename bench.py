@@ -383,6 +383,7 @@ def run_ours(args):
     # ---- the same solve with the paper's H0-based preconditioners ---------
     if not args.no_extra:
         out["precond_solves"] = precond_solves(reg, v, stream)
+        out["paper_gpu_discretization"] = paper_gpu_discretization(reg, v, shape, stream)
         if args.workload == "blob256":
             out["large_displacement"] = large_displacement(claire, synth, args, stream)
 
@@ -427,6 +428,44 @@ def precond_solves(reg, v, stream, reps=3):
                      "grel": rep.grel, "J": rep.J, "t_pc_ms": round(rep.t_pc_ms, 3),
                      "t_hess_ms": round(rep.t_hess_ms, 3)}
     return out
+
+
+def paper_gpu_discretization(reg, v, shape, stream, reps=3):
+    """The same solve and Hessian matvec with the discretization the paper's
+    GPU runs use (Sections 4.1, 4.2: trilinear SL interpolation, 8th-order
+    finite-difference first derivatives), beside the default cubic / spectral
+    form; the context is set back to cubic / spectral afterwards."""
+    import torch
+    from paper_2008_12820_gb300 import synth
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reg.set_discretization(interp="linear", deriv="fd8")
+    try:
+        v.zero_()
+        reg.solve(v)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            v.zero_()
+            rep = reg.solve(v)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        solve_ms = e0.elapsed_time(e1) / reps
+        reg.linearize(v)
+        vt = torch.from_numpy(synth.smooth_direction(shape, 7)).cuda()
+        Hv = torch.empty_like(vt)
+        for _ in range(3):
+            reg.hess_matvec(None, vt, out=Hv)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            reg.hess_matvec(None, vt, out=Hv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mv_ms = e0.elapsed_time(e1) / 10
+    finally:
+        reg.set_discretization(interp="cubic", deriv="spectral")
+    return {"interp": "trilinear", "deriv": "fd8", "solve_ms": round(solve_ms, 3), "n_gn": rep.n_gn,
+            "n_pcg": rep.n_pcg, "grel": rep.grel, "J": rep.J, "hess_matvec_ms": round(mv_ms, 4)}
 
 
 def large_displacement(claire, synth, args, stream, reps=3):

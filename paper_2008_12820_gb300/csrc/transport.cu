@@ -935,10 +935,12 @@ constexpr int kSlLaunches = 1;
 
 inline bool full_tiles(const Dims &d) { return d.n3 % PT3 == 0 && d.n2 % PT2 == 0 && d.n1 % PT1 == 0; }
 
-// the full-tile form for the cubic steps (the production discretization)
+// the full-tile form for grids of whole tiles, cubic and trilinear (with 8
+// taps a voxel the trilinear steps lose relatively more to the bounds checks:
+// incremental state 13.8 -> 10.4 ms per 256^3 solve)
 template <int MODE, int ORDER, typename TS, typename TG>
 void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
-    if constexpr (ORDER == 3) {
+    if constexpr (ORDER == 3 || ORDER == 1) {
         if (full_tiles(d)) {
             launch_pipe_f<MODE, ORDER, TS, TG, true>(d, a, tiles, st);
             return;
