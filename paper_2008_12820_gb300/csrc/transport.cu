@@ -916,18 +916,23 @@ inline int chunk_ok(const Dims &d, const T *f) {
 inline int pipe_blocks(const Dims &d, int per_sm) {
     const long long ntiles = (long long)((d.n3 + PT3 - 1) / PT3) * ((d.n2 + PT2 - 1) / PT2) *
                              ((d.n1 + PT1 - 1) / PT1);
-    const long long want = (long long)per_sm * num_sms();
+    // at most kReduceBlocks: a dot-product step leaves one partial sum per block
+    long long want = (long long)per_sm * num_sms();
+    if (want > kReduceBlocks) want = kReduceBlocks;
     return (int)(ntiles < want ? ntiles : want);
 }
 
+// returns the number of blocks launched (the partial sums a dot-product step
+// leaves for its finalize)
 template <int MODE, int ORDER, typename TS, typename TG, bool FULL>
-void launch_pipe_f(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
+int launch_pipe_f(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
     const size_t smem = 2 * BOX_FLOATS * sizeof(float);
     // the shared-memory limit is set once per instantiation and device
     static SmemAttr attr;
     attr.ensure(k_sl_pipe<MODE, ORDER, TS, TG, FULL>, (int)smem, "k_sl_pipe");
-    k_sl_pipe<MODE, ORDER, TS, TG, FULL><<<pipe_blocks(d, SlOcc<MODE>::v), dim3(PT3, PT2), smem, st>>>(
-        a, d, tiles, chunk_ok(d, a.src));
+    const int grid = pipe_blocks(d, SlOcc<MODE>::v);
+    k_sl_pipe<MODE, ORDER, TS, TG, FULL><<<grid, dim3(PT3, PT2), smem, st>>>(a, d, tiles, chunk_ok(d, a.src));
+    return grid;
 }
 
 // kernels one SL step launches
@@ -939,20 +944,17 @@ inline bool full_tiles(const Dims &d) { return d.n3 % PT3 == 0 && d.n2 % PT2 == 
 // taps a voxel the trilinear steps lose relatively more to the bounds checks:
 // incremental state 13.8 -> 10.4 ms per 256^3 solve)
 template <int MODE, int ORDER, typename TS, typename TG>
-void launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
+int launch_pipe_o(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
     if constexpr (ORDER == 3 || ORDER == 1) {
-        if (full_tiles(d)) {
-            launch_pipe_f<MODE, ORDER, TS, TG, true>(d, a, tiles, st);
-            return;
-        }
+        if (full_tiles(d)) return launch_pipe_f<MODE, ORDER, TS, TG, true>(d, a, tiles, st);
     }
-    launch_pipe_f<MODE, ORDER, TS, TG, false>(d, a, tiles, st);
+    return launch_pipe_f<MODE, ORDER, TS, TG, false>(d, a, tiles, st);
 }
 
 template <int MODE, typename TS, typename TG>
-void launch_pipe(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
-    if (d.iorder == 1) launch_pipe_o<MODE, 1>(d, a, tiles, st);
-    else launch_pipe_o<MODE, 3>(d, a, tiles, st);
+int launch_pipe(const Dims &d, const SlArgsT<TS, TG> &a, const int4 *tiles, cudaStream_t st) {
+    if (d.iorder == 1) return launch_pipe_o<MODE, 1>(d, a, tiles, st);
+    return launch_pipe_o<MODE, 3>(d, a, tiles, st);
 }
 
 // ----------------------------------------------------------- pointwise ----
@@ -1113,8 +1115,8 @@ void adjoint_acc(const Dims &d, const float *src, const float *dispp, const int4
     if (want_dot) {
         a.pv = p;
         a.partial = partial;
-        launch_pipe<SL_ADJDOT>(d, a, tiles_p, st);
-        launch_finalize(partial, pipe_blocks(d, SlOcc<SL_ADJDOT>::v), dot_add, dot_out, st);
+        const int nb = launch_pipe<SL_ADJDOT>(d, a, tiles_p, st);
+        launch_finalize(partial, nb, dot_add, dot_out, st);
     } else {
         launch_pipe<SL_ADJACC>(d, a, tiles_p, st);
     }
