@@ -1,8 +1,9 @@
 // fft_core.cuh -- the shared-memory Stockham FFT building blocks of the
 // pencil transforms (fft.cu) and the axis derivatives (fft_axis.cu): in-register
-// DFTs of radix 2, 3, 4, 5, 8, 16, the Stockham stages, compile-time plans for
-// the common lengths and a runtime plan for the others, wavenumbers, and the
-// launch helpers.  Internal linkage: each translation unit instantiates what
+// DFTs of radix 2, 3, 4, 5, 8, 16, the Stockham stages (out of place with a
+// scratch tile, and in place for power-of-two lengths from 128), compile-time
+// plans for the common lengths and a runtime plan for the others, wavenumbers,
+// and the launch helpers.  Internal linkage: each translation unit instantiates what
 // it uses.
 #pragma once
 
