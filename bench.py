@@ -804,6 +804,50 @@ def run_pcstudy(args):
                       "nt": 4, "gamma": 1.0, "eps_n": 5e-2, "eps_h0": 1e-3, "rows": rows}), flush=True)
 
 
+def run_precond(args):
+    """(beta A)^-1 of a 3-component field alone (the five pencil passes of the
+    inverse-A preconditioner, Section 3 "Preconditioning") on an n^3 grid
+    (--grid, default 256), in a context with N_t = 1 so that little else is
+    allocated: device time per application and the algorithmic bytes of the
+    passes over it.  For profiling captures of the transform kernels at full
+    size; not a bench line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2008_12820_gb300 import claire
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n = args.grid or 256
+    shape = (n, n, n)
+    rng = np.random.default_rng(5)
+    r = torch.from_numpy(rng.standard_normal((3,) + shape).astype(np.float32)).cuda()
+    s = torch.empty_like(r)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with claire.Registration(shape, 1, 1e-2, 1.0) as reg:
+        for _ in range(args.warmup):
+            reg.precond(r, out=s)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            reg.precond(r, out=s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        h3 = n // 2 + 1
+        # r2c: real in, half spectrum out; two c2c x2 passes and the x1 pass:
+        # half spectrum in and out; c2r: half spectrum in, real out
+        spec = 3 * n * n * h3 * 8
+        real = 3 * n ** 3 * 4
+        byts = (real + spec) + 2 * (2 * spec) + 2 * spec + (spec + real)
+        print(json.dumps({"what": "(beta A)^-1 of a 3-component field, five pencil passes", "grid": list(shape),
+                          "ms": round(ms, 4), "algorithmic_bytes": byts,
+                          "workspace_gb": round(reg.workspace_bytes() / 1e9, 2),
+                          "GBps": round(byts / (ms * 1e-3) / 1e9, 1)}), flush=True)
+
+
 def run_oracle_study(args):
     """The FP64 oracle timed at the sizes the measurement plan names, on the
     host cores (OpenMP over all of them): gradient and one Hessian matvec at
@@ -853,6 +897,8 @@ def main():
         run_pcstudy(args)
     elif args.workload == "oracle-study":
         run_oracle_study(args)
+    elif args.workload == "precond":
+        run_precond(args)
     else:
         run_ours(args)
 
