@@ -208,10 +208,12 @@ k_c2c_x2_ip(float2 *__restrict__ data, FftPlan p, int h3, int p3, float s, int n
         for (int t = threadIdx.x; t < N * CH; t += MT) {
             const int e = t / CH, ch = t - e * CH;
             const int col = k0 + 2 * ch;
-            const float2 *q = cur + e * TK + 2 * ch;
+            // one 16-byte shared load per two columns (two 8-byte loads at a
+            // 16-byte lane stride would conflict in pairs of banks)
+            const float4 q = *reinterpret_cast<const float4 *>(cur + e * TK + 2 * ch);
             float2 *g = base + (long long)e * p3 + 2 * ch;
-            if (col + 2 <= h3) *reinterpret_cast<float4 *>(g) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
-            else if (col < h3) *g = q[0];
+            if (col + 2 <= h3) *reinterpret_cast<float4 *>(g) = q;
+            else if (col < h3) *g = make_float2(q.x, q.y);
         }
         __syncthreads();
         float2 *t = cur;
@@ -410,10 +412,10 @@ k_mul_x1_ip(float2 *__restrict__ data, FftPlan p1, int n2, int n3, int h3, int p
             const int c = t / (N * CH), r = t - c * (N * CH);
             const int e = r / CH, ch = r - e * CH;
             const int col = k0 + 2 * ch;
-            const float2 *s = cur + e * LL + c * TK + 2 * ch;
+            const float4 q = *reinterpret_cast<const float4 *>(cur + e * LL + c * TK + 2 * ch);
             float2 *g = base + c * cstride + e * rowstride + 2 * ch;
-            if (col + 2 <= h3) *reinterpret_cast<float4 *>(g) = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
-            else if (col < h3) *g = s[0];
+            if (col + 2 <= h3) *reinterpret_cast<float4 *>(g) = q;
+            else if (col < h3) *g = make_float2(q.x, q.y);
         }
         __syncthreads();
         float2 *t = cur;
