@@ -74,6 +74,35 @@ def test_batch_equals_one_by_one(claire):
         r.close()
 
 
+def test_batch_more_pairs_than_workers(claire):
+    """Twelve pairs: more than the batch's eight worker threads, so workers
+    take several pairs in turn on their stream (largest grid first); every
+    result equals the one-by-one solve bit for bit."""
+    shapes = [(32, 32, 32), (24, 40, 32), (40, 24, 36), (32, 48, 24), (28, 28, 44), (36, 36, 36),
+              (20, 27, 45), (48, 32, 32), (32, 32, 40), (44, 24, 28), (24, 24, 24), (40, 40, 24)]
+    ws = []
+    for i, shape in enumerate(shapes):
+        d = synth.blob_pair(shape, 3000 + i, max_disp_vox=2.0)
+        ws.append(dict(d, shape=shape, nt=2 + i % 3, beta=1e-2, gamma=1.0, precision="fp32"))
+    seq = []
+    for w in ws:
+        with make(claire, w) as reg:
+            v = torch.zeros((3,) + w["shape"], device="cuda")
+            rep = reg.solve(v)
+            seq.append((rep, v.clone()))
+    regs = [make(claire, w) for w in ws]
+    vs = [torch.zeros((3,) + w["shape"], device="cuda") for w in ws]
+    reps = claire.solve_batch(regs, vs)
+    torch.cuda.synchronize()
+    for (r1, v1), r2, v2 in zip(seq, reps, vs):
+        assert r2.status == 0
+        assert (r1.n_gn, r1.n_pcg, r1.n_ls) == (r2.n_gn, r2.n_pcg, r2.n_ls)
+        assert r1.J == r2.J and r1.grel == r2.grel
+        assert torch.equal(v1, v2)
+    for r in regs:
+        r.close()
+
+
 def test_batch_reports_a_failing_pair(claire):
     ws = pairs()[:3]
     regs = [make(claire, w) for w in ws]
