@@ -486,6 +486,7 @@ k_c2r_x3_p(const float2 *__restrict__ in, TO *__restrict__ out, const float *__r
     float2 *A = sm, *B = sm + n * ls;
     float2 *S = sm + (IP ? 1 : 2) * n * ls;  // staging: 2L lines of p3 complex values
     const bool even = (n & 1) == 0;
+    if (N > 0) h3 = N / 2 + 1;
     auto load = [&](int item) {
         const long long line0 = (long long)item * 2 * L;
         const float2 *base = in + line0 * p3;
@@ -503,22 +504,20 @@ k_c2r_x3_p(const float2 *__restrict__ in, TO *__restrict__ out, const float *__r
     for (int item = i0; item < nitems; item += stride) {
         cp_async_wait_n<0>();
         __syncthreads();
-        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
-            const int l = t / n, k = t - l * n;
-            const bool lo = k < h3;
-            const int kk = lo ? k : n - k;
-            float2 a = S[(2 * l) * p3 + kk];
-            float2 b = S[(2 * l + 1) * p3 + kk];
-            if (k == 0 || (even && 2 * k == n)) {
+        // each stored coefficient k < h3 gives Z_k = A_k + i B_k and, by
+        // Hermitian symmetry, Z_{n-k} = conj(A_k) + i conj(B_k): one read of
+        // the staged lines for both
+        for (int t = threadIdx.x; t < L * h3; t += blockDim.x) {
+            const int l = t / h3, k = t - l * h3;
+            float2 a = S[(2 * l) * p3 + k];
+            float2 b = S[(2 * l + 1) * p3 + k];
+            const bool self = k == 0 || (even && 2 * k == n);
+            if (self) {
                 a.y = 0.f;
                 b.y = 0.f;
             }
-            if (!lo) {
-                a.y = -a.y;
-                b.y = -b.y;
-            }
-            // Z = A + i B
             A[k * ls + l] = make_float2(a.x - b.y, a.y + b.x);
+            if (!self) A[(n - k) * ls + l] = make_float2(a.x + b.y, -a.y + b.x);
         }
         __syncthreads();
         if (item + stride < nitems) load(item + stride);
