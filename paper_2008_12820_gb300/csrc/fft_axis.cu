@@ -105,15 +105,23 @@ k_deriv_x3_p(const float *__restrict__ in, TO *out, const float *add, long long 
         __syncthreads();
         if (item + stride < nitems) load(item + stride);
         float2 *R = A;
-        if constexpr (IP) fft_ip<N, L, kThreads, L + 1>(A, p.tw, -1.f);
-        else R = Fft<N>::template run<L>(A, B, p, ls, -1.f);
-        for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
-            const int e = t / L, l = t - e * L;
-            const float k = wavenumber_d1(e, n) * sc;
-            const float2 z = R[e * ls + l];
-            R[e * ls + l] = make_float2(-k * z.y, k * z.x);
+        if constexpr (IP) {
+            // the multiplier i k / n applied as the last forward stage stores
+            const auto deriv = [sc](int e, float2 &z) {
+                const float k = wavenumber_d1(e, N) * sc;
+                z = make_float2(-k * z.y, k * z.x);
+            };
+            fft_ip<N, L, kThreads, L + 1, 0>(A, p.tw, -1.f, deriv);
+        } else {
+            R = Fft<N>::template run<L>(A, B, p, ls, -1.f);
+            for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+                const int e = t / L, l = t - e * L;
+                const float k = wavenumber_d1(e, n) * sc;
+                const float2 z = R[e * ls + l];
+                R[e * ls + l] = make_float2(-k * z.y, k * z.x);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         float2 *Q = R;
         if constexpr (IP) fft_ip<N, L, kThreads, L + 1>(R, p.tw, +1.f);
         else Q = Fft<N>::template run<L>(R, R == A ? B : A, p, ls, +1.f);
@@ -290,14 +298,13 @@ k_deriv_strided_ip(const float *__restrict__ in, TO *out, const float *add, int 
             cp_async_wait_n<0>();
         }
         __syncthreads();
-        fft_ip<N, TKC, MT>(cur, tw, -1.f);
-        for (int t = threadIdx.x; t < N * TKC; t += MT) {
-            const int e = t / TKC;
+        // forward transform with the multiplier i k / n applied as its last
+        // stage stores, then the inverse transform
+        const auto deriv = [sc](int e, float2 &z) {
             const float k = wavenumber_d1(e, N) * sc;
-            const float2 z = cur[t];
-            cur[t] = make_float2(-k * z.y, k * z.x);
-        }
-        __syncthreads();
+            z = make_float2(-k * z.y, k * z.x);
+        };
+        fft_ip<N, TKC, MT, TKC, 0>(cur, tw, -1.f, deriv);
         fft_ip<N, TKC, MT>(cur, tw, +1.f);
         const int plane = item / ntk, k0 = (item - plane * ntk) * 2 * TKC;
         const long long base = (long long)plane * pstride;

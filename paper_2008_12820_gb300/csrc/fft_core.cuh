@@ -256,8 +256,14 @@ __device__ __forceinline__ float2 *fft_ct(float2 *A, float2 *B, const float2 *__
 // block can hold more lines in the same shared memory, and with WORK a
 // multiple of NT every thread has work in every stage.  Same butterflies,
 // twiddles and order of operations per line as stage_ct.
-template <int N, int R, int NS, int L, int NT, int LS = L>
-__device__ __forceinline__ void stage_ip(float2 *__restrict__ A, const float2 *__restrict__ tw, float s) {
+// no pointwise step after the last stage
+struct NoPost {
+    __device__ __forceinline__ void operator()(int, float2 &) const {}
+};
+
+template <int N, int R, int NS, int L, int NT, int LS = L, class Post = NoPost>
+__device__ __forceinline__ void stage_ip(float2 *__restrict__ A, const float2 *__restrict__ tw, float s,
+                                         const Post &post = Post()) {
     constexpr int NB = N / R, WORK = NB * L, TSTRIDE = N / (NS * R), IT = (WORK + NT - 1) / NT;
     float2 a[IT][R];
 #pragma unroll
@@ -290,7 +296,10 @@ __device__ __forceinline__ void stage_ip(float2 *__restrict__ A, const float2 *_
             const int k = j % NS;
             const int base = (j / NS) * NS * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) A[(base + r * NS) * LS + l] = a[i][r];
+            for (int r = 0; r < R; ++r) {
+                post(base + r * NS, a[i][r]);
+                A[(base + r * NS) * LS + l] = a[i][r];
+            }
         }
     }
     __syncthreads();
@@ -298,12 +307,17 @@ __device__ __forceinline__ void stage_ip(float2 *__restrict__ A, const float2 *_
 
 // FFT of L lines of length N stored as A[e * LS + l] (LS >= L; an odd LS
 // keeps the transposing loads of the x3 passes free of bank conflicts), in
-// place, NT threads; ends behind a barrier
-template <int N, int L, int NT, int LS = L, int S = 0>
-__device__ __forceinline__ void fft_ip(float2 *A, const float2 *__restrict__ tw, float s) {
-    if constexpr (S < num_stages(N)) {
+// place, NT threads; ends behind a barrier.  post(e, v) is applied to every
+// output element (e = its index along the line) before the last stage
+// stores it: a pointwise multiplier without another pass over the tile.
+template <int N, int L, int NT, int LS = L, int S = 0, class Post = NoPost>
+__device__ __forceinline__ void fft_ip(float2 *A, const float2 *__restrict__ tw, float s,
+                                       const Post &post = Post()) {
+    if constexpr (S + 1 == num_stages(N)) {
+        stage_ip<N, radix_at(N, S), ns_before(N, S), L, NT, LS, Post>(A, tw, s, post);
+    } else if constexpr (S < num_stages(N)) {
         stage_ip<N, radix_at(N, S), ns_before(N, S), L, NT, LS>(A, tw, s);
-        fft_ip<N, L, NT, LS, S + 1>(A, tw, s);
+        fft_ip<N, L, NT, LS, S + 1, Post>(A, tw, s, post);
     }
 }
 
